@@ -1,0 +1,150 @@
+"""Long oracle simulations behind the physics pins.
+
+Each function runs one plain-FP64 oracle case and returns plain numbers.  They
+are module-level so a ``spawn`` process pool can run them side by side; the
+test session starts that pool once and shares the results.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+
+def _oracle():
+    import oracle
+    return oracle
+
+
+def _W():
+    from paper_2410_06657_gb300 import workloads
+    return workloads
+
+
+def layer_psi(nx, ny, h0, W):
+    """Planar liquid layer of thickness h0 on the bottom wall (y = -1/2)."""
+    y = np.arange(ny, dtype=np.float64)[:, None] + 0.5 + np.zeros((1, nx))
+    return 0.5 + 0.5 * np.tanh(2.0 * (h0 - y) / W)
+
+
+def laplace(R, W=4.0, N=64, steps=5000):
+    """Static drop in the middle of an N x N box, no freezing, no field."""
+    o = _oracle().Oracle(_W().params(nx=N, ny=N, T_w=0.0, CaE=0.0, R0=R, theta_deg=90.0, W=W))
+    o.init_droplet(R, N / 2, N / 2, 0)
+    o.step(steps)
+    p, psi = o.get("p"), o.get("psi")
+    dp = float(p[psi > 0.99].mean() - p[psi < 0.01].mean())
+    R_eff = float(math.sqrt(psi.sum() / math.pi))
+    return dict(R=R, W=W, dp=dp, R_eff=R_eff, gamma=0.01)
+
+
+def contact_angle(theta, R=16.0, nx=96, ny=48, steps=5000):
+    W = _W()
+    o = _oracle().Oracle(W.params(nx=nx, ny=ny, T_w=0.0, CaE=0.0, R0=R, theta_deg=theta))
+    xc, yc = W.sessile_center(nx, R, theta)
+    o.init_droplet(R, xc, yc, 0)
+    o.step(steps)
+    ob = o.observables()
+    return dict(theta=theta, height=ob["height"], base_half=ob["R_tr"])
+
+
+def stefan(Ste=0.1, alpha=0.1, h0=56.0, ny=64, steps=20000, samples=8):
+    """One-phase Stefan problem: liquid layer at T_m, cold wall below."""
+    o = _oracle().Oracle(_W().params(nx=4, ny=ny, rho_sl=1.0, Ste=Ste, alpha_l=alpha,
+                                     CaE=0.0, R0=h0, theta_deg=90.0))
+    o.init_psi(layer_psi(4, ny, h0, 4.0))
+    ts, fronts = [], []
+    for _ in range(samples):
+        o.step(steps // samples)
+        ts.append(o.t)
+        fronts.append(o.observables()["front"])
+    return dict(Ste=Ste, alpha=alpha, t=ts, front=fronts)
+
+
+def volume_change(rho_sl, h0=20.0, ny=48, steps=8000):
+    o = _oracle().Oracle(_W().params(nx=4, ny=ny, rho_sl=rho_sl, Ste=0.5, alpha_l=0.1,
+                                     CaE=0.0, R0=h0, theta_deg=90.0))
+    o.init_psi(layer_psi(4, ny, h0, 4.0))
+    o.step(steps)
+    ob = o.observables()
+    return dict(rho_sl=rho_sl, h0=h0, height=ob["height"], frozen=ob["frozen_fraction"])
+
+
+def deformation(R_sigma, S_eps, CaE=0.2, N=80, R=16.0, steps=5000, presolve=12000):
+    """Suspended drop between the electrodes, viscosity and density ratio 1."""
+    o = _oracle().Oracle(_W().params(nx=N, ny=N, T_w=0.0, CaE=CaE, R_sigma=R_sigma, S_eps=S_eps,
+                                     R0=R, rho_lg=1.0, mu_lg=1.0, k_e=5))
+    o.init_droplet(R, N / 2, N / 2, presolve)
+    o.step(steps)
+    psi = o.get("psi")
+
+    def extent(v):
+        idx = np.where(v >= 0.5)[0]
+        a, b = idx[0], idx[-1]
+        lo = (a - 1) + (0.5 - v[a - 1]) / (v[a] - v[a - 1])
+        hi = b + (v[b] - 0.5) / (v[b] - v[b + 1])
+        return float(hi - lo)
+
+    L_along = extent(psi[:, N // 2])      # along E (vertical)
+    H_perp = extent(psi[N // 2, :])       # perpendicular to E
+    return dict(R=R_sigma, S=S_eps, CaE=CaE, D=(L_along - H_perp) / (L_along + H_perp))
+
+
+def droplet_front(Fo, Ste=0.2, rho_sl=0.9, theta=120.0, alpha_lg=0.2, R=16.0, nx=96, ny=48):
+    W = _W()
+    p = W.params(nx=nx, ny=ny, Ste=Ste, rho_sl=rho_sl, theta_deg=theta, alpha_lg=alpha_lg,
+                 CaE=0.0, R0=R)
+    o = _oracle().Oracle(p)
+    xc, yc = W.sessile_center(nx, R, theta)
+    o.init_droplet(R, xc, yc, 0)
+    o.step(int(round(Fo * R * R / p["alpha_l"])))
+    ob = o.observables()
+    return dict(Fo=ob["Fo"], front_over_R0=ob["front"] / R)
+
+
+def mass_conservation(steps=1000):
+    """Sessile drop with the field on and no freezing (T_w = T_m)."""
+    W = _W()
+    p = W.params(nx=128, ny=64, T_w=0.0, k_e=2)
+    o = _oracle().Oracle(p)
+    xc, yc = W.sessile_center(128, 20.0, 90.0)
+    o.init_droplet(20.0, xc, yc, 50)
+    m0 = o.observables()["mass"]
+    o.step(steps)
+    ob = o.observables()
+    return dict(m0=m0, m1=ob["mass"], solid=ob["solid"])
+
+
+JOBS = {
+    "laplace_10": (laplace, (10.0,)),
+    "laplace_14": (laplace, (14.0,)),
+    "laplace_18": (laplace, (18.0,)),
+    "laplace_14_W5": (laplace, (14.0, 5.0)),
+    "angle_60": (contact_angle, (60.0,)),
+    "angle_90": (contact_angle, (90.0,)),
+    "angle_120": (contact_angle, (120.0,)),
+    "stefan": (stefan, ()),
+    "volume_0.9": (volume_change, (0.9,)),
+    "volume_1.1": (volume_change, (1.1,)),
+    "deform_5_2": (deformation, (5.0, 2.0)),
+    "deform_2_5": (deformation, (2.0, 5.0)),
+    "front_paper": (droplet_front, (0.62,)),
+    "mass": (mass_conservation, ()),
+}
+
+
+def _run(name):
+    fn, args = JOBS[name]
+    return name, fn(*args)
+
+
+def run_all(processes=None):
+    import multiprocessing as mp
+    import os
+    ctx = mp.get_context("spawn")
+    procs = processes or min(len(JOBS), max(1, os.cpu_count() or 1))
+    # longest jobs first so the pool drains evenly
+    order = ["deform_5_2", "deform_2_5", "laplace_10", "laplace_14", "laplace_18",
+             "laplace_14_W5", "angle_60", "angle_90", "angle_120", "front_paper",
+             "mass", "stefan", "volume_0.9", "volume_1.1"]
+    with ctx.Pool(procs) as pool:
+        return dict(pool.map(_run, order, chunksize=1))

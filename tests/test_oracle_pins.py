@@ -1,0 +1,321 @@
+"""Pins for the FP64 CPU oracle: the paper's printed numbers, closed forms,
+invariants and textbook special cases.  CPU only.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign or index, a transposed operand) breaks at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_06657_gb300 import workloads as W
+from tests import oracle_runs
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+@pytest.fixture(scope="session")
+def runs():
+    return oracle_runs.run_all()
+
+
+# --------------------------------------------------------------------------
+# Lattice and pointwise pieces
+# --------------------------------------------------------------------------
+
+def test_d2q9_lattice_isotropy():
+    """Sec. 3.1: the velocity set built from the paper's cos/sin formula has
+    the D2Q9 moment isotropy up to fourth order with c_s^2 = 1/3."""
+    cx, cy, w = oracle.lattice()
+    c = np.stack([cx, cy], 1).astype(float)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.allclose(w @ c, 0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), np.eye(2) / 3, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, c, c, c), 0, atol=1e-16)
+    d = np.eye(2)
+    iso4 = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+            + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso4, atol=1e-16)
+    speeds = sorted(set(np.round(np.hypot(cx, cy), 12)))
+    assert speeds == [0.0, 1.0, round(math.sqrt(2), 12)]
+    # rest, axis E N W S, then the diagonals in angular order (Sec. 3.1)
+    assert (cx[0], cy[0]) == (0, 0)
+    angles = np.degrees(np.arctan2(cy[1:], cx[1:])) % 360
+    assert np.allclose(angles, [0, 90, 180, 270, 45, 135, 225, 315])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_equilibrium_and_source_moments(seed):
+    """Moments fixed by Secs. 3.1-3.4: sum f_eq = psi, sum c f_eq = psi u;
+    sum h_eq = 0, sum c h_eq = rho u, sum c c h_eq = p I + rho u u;
+    sum g_eq = H, sum c g_eq = C_p T u; sum l_eq = 0, sum_{1..4} l_eq/(1-w_0) = phi;
+    sum R_i = S, sum c R_i = F + rho f; sum F_i = psi div u,
+    sum c F_i = d_t(psi u) + c_s^2 lambda n."""
+    r = np.random.default_rng(seed)
+    v = {k: float(r.uniform(-1, 1)) for k in
+         ["ux", "uy", "p", "H", "T", "phi", "S", "Fx", "Fy", "rfx", "rfy", "Ftx", "Fty",
+          "dtx", "dty", "divu"]}
+    v.update(psi=float(r.uniform(0, 1)), rho=float(r.uniform(0.1, 1)),
+             cp=float(r.uniform(0.5, 2)), Cref=float(r.uniform(0.5, 2)),
+             lam=float(r.uniform(0, 1)))
+    th = r.uniform(0, 2 * np.pi)
+    v.update(nxv=math.cos(th), nyv=math.sin(th))
+    out = oracle.pointwise(**v)
+    cx, cy, w = oracle.lattice()
+    c = np.stack([cx, cy], 1).astype(float)
+    u = np.array([v["ux"], v["uy"]])
+    tol = 1e-14
+    assert abs(out["feq"].sum() - v["psi"]) < tol
+    assert np.allclose(c.T @ out["feq"], v["psi"] * u, atol=tol)
+    assert abs(out["heq"].sum()) < tol
+    assert np.allclose(c.T @ out["heq"], v["rho"] * u, atol=tol)
+    assert np.allclose(np.einsum("i,ia,ib->ab", out["heq"], c, c),
+                       v["p"] * np.eye(2) + v["rho"] * np.outer(u, u), atol=tol)
+    assert abs(out["geq"].sum() - v["H"]) < tol
+    assert np.allclose(c.T @ out["geq"], v["cp"] * v["T"] * u, atol=tol)
+    assert abs(out["leq"].sum()) < tol
+    assert abs(out["leq"][1:].sum() / (1 - 1 / 3) - v["phi"]) < tol
+    assert abs(out["hsrc"].sum() - v["S"]) < tol
+    assert np.allclose(c.T @ out["hsrc"], [v["Fx"] + v["rfx"], v["Fy"] + v["rfy"]], atol=tol)
+    # second moment of R_i: S c_s^2 I + (u Ft + Ft u)  (Sec. 3.2)
+    Ft = np.array([v["Ftx"], v["Fty"]])
+    assert np.allclose(np.einsum("i,ia,ib->ab", out["hsrc"], c, c),
+                       v["S"] / 3 * np.eye(2) + np.outer(u, Ft) + np.outer(Ft, u), atol=tol)
+    assert abs(out["fsrc"].sum() - v["psi"] * v["divu"]) < tol
+    assert np.allclose(c.T @ out["fsrc"],
+                       [v["dtx"] + v["lam"] * v["nxv"] / 3, v["dty"] + v["lam"] * v["nyv"] / 3],
+                       atol=tol)
+
+
+def test_stencils_exact_on_polynomials():
+    """Eqs. (eqtidi1)-(eqtidi2): the isotropic gradient is exact for quadratics
+    and the Laplacian for cubics (interior rows; x periodic needs a periodic
+    field, so check away from the wrap)."""
+    ny, nx = 12, 16
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    z = 0.3 * x - 0.7 * y + 0.05 * x * x - 0.02 * y * y + 0.03 * x * y
+    gx, gy, lp = oracle.stencils(z)
+    sl = (slice(1, ny - 1), slice(1, nx - 1))
+    assert np.allclose(gx[sl], (0.3 + 0.1 * x + 0.03 * y)[sl], atol=1e-12)
+    assert np.allclose(gy[sl], (-0.7 - 0.04 * y + 0.03 * x)[sl], atol=1e-12)
+    assert np.allclose(lp[sl], 0.1 - 0.04, atol=1e-12)
+    z3 = 0.001 * x ** 3 - 0.002 * y ** 3 + 0.003 * x * x * y
+    _, _, lp3 = oracle.stencils(z3)
+    assert np.allclose(lp3[sl], (0.006 * x - 0.012 * y + 0.006 * y)[sl], atol=1e-11)
+    # periodic x: a single Fourier mode keeps its shape (the stencil is a
+    # symmetric convolution), so the gradient is proportional to the
+    # analytic one with one common factor
+    zp = np.sin(2 * np.pi * x / nx)
+    gxp, _, _ = oracle.stencils(zp)
+    exact = 2 * np.pi / nx * np.cos(2 * np.pi * x / nx)
+    ratio = gxp[sl][np.abs(exact[sl]) > 0.1] / exact[sl][np.abs(exact[sl]) > 0.1]
+    assert np.ptp(ratio) < 1e-12 and abs(ratio.mean() - 1) < 0.03
+
+
+def test_potential_ghost_keeps_linear_fields_exact():
+    """R19: the mirrored phi ghost makes a linear potential's gradient and
+    Laplacian exact on the wall rows too (Dirichlet value at y = -1/2)."""
+    ny, nx = 10, 8
+    y = np.arange(ny, dtype=float)[:, None] + np.zeros((1, nx))
+    E = 0.37
+    z = 0.2 + E * (y + 0.5)
+    gx, gy, lp = oracle.stencils(z, kind=2, phi_bot=0.2, phi_top=0.2 + E * ny)
+    assert np.allclose(gy, E, atol=1e-14)
+    assert np.allclose(gx, 0, atol=1e-14)
+    assert np.allclose(lp, 0, atol=1e-13)
+
+
+def test_enthalpy_inversion_branches_and_continuity():
+    """Eq. (Hfl) under readings R5-R6: solid, mushy and liquid branches;
+    T(H) continuous and non-decreasing; f_l ramps over exactly psi*L."""
+    cp, Tm, L = 1.3, 0.25, 2.0
+    Hs = cp * Tm
+    fl, T = oracle.enthalpy_inversion(Hs - 0.65, 1.0, cp, Tm, L)
+    assert fl == 0.0 and abs(T - (Hs - 0.65) / cp) < 1e-15
+    fl, T = oracle.enthalpy_inversion(Hs + 0.5, 1.0, cp, Tm, L)
+    assert abs(fl - 0.25) < 1e-15 and T == Tm
+    fl, T = oracle.enthalpy_inversion(Hs + L + 1.3, 1.0, cp, Tm, L)
+    assert fl == 1.0 and abs(T - (Tm + 1.0)) < 1e-15
+    # latent heat scaled by psi: half-liquid cell melts over L/2
+    fl, _ = oracle.enthalpy_inversion(Hs + 0.5, 0.5, cp, Tm, L)
+    assert abs(fl - 0.5) < 1e-15
+    # gas never solidifies
+    fl, T = oracle.enthalpy_inversion(Hs - 1.0, 0.0, cp, Tm, L)
+    assert fl == 1.0 and abs(T - (Hs - 1.0) / cp) < 1e-15
+    Hs_grid = np.linspace(Hs - 1, Hs + L + 1, 2001)
+    Ts = np.array([oracle.enthalpy_inversion(h, 1.0, cp, Tm, L)[1] for h in Hs_grid])
+    assert np.all(np.diff(Ts) >= -1e-15)
+    assert np.max(np.abs(np.diff(Ts))) < 2 * (Hs_grid[1] - Hs_grid[0]) / cp
+
+
+def test_derived_constants_invert_the_dimensionless_numbers():
+    """Sec. 4-5 definitions: Ca_E = eps_e E0^2 R0 / gamma and
+    Ste = C_p (T_m - T_w) / L recovered from the derived lattice constants;
+    Eq. (Computed) end members; tau_f = M/c_s^2 + 1/2."""
+    p = W.params(CaE=0.37, Ste=0.23, R0=21.0, gamma=0.013, eps_g=1.7)
+    d = oracle.derive(p)
+    assert abs(p["eps_g"] * d["E0"] ** 2 * p["R0"] / p["gamma"] - 0.37) < 1e-14
+    assert abs(p["cp_l"] * (p["T_m"] - p["T_w"]) / d["L"] - 0.23) < 1e-14
+    assert abs(d["phi_top"] - d["phi_bot"] - d["E0"] * p["ny"]) < 1e-14
+    assert d["rho"][1] / d["rho"][2] == pytest.approx(10.0)
+    assert d["rho"][0] / d["rho"][1] == pytest.approx(0.9)
+    assert d["eps"][1] / d["eps"][2] == pytest.approx(p["S_eps"])
+    assert d["sig"][1] / d["sig"][2] == pytest.approx(p["R_sigma"])
+    assert d["tau_f"] == pytest.approx(0.8)
+    # thermal diffusivity ratio alpha_l / alpha_g = 0.2 (Sec. 5.1)
+    al = d["kth"][1] / (d["rho"][1] * d["cp"][1])
+    ag = d["kth"][2] / (d["rho"][2] * d["cp"][2])
+    assert al / ag == pytest.approx(0.2)
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(theta_deg=0.0), dict(theta_deg=180.0),
+                                 dict(M=0.0), dict(mu_l=0.0), dict(k_e=0), dict(Ste=0.0)])
+def test_invalid_parameters_rejected(bad):
+    with pytest.raises(ValueError):
+        oracle.Oracle(W.params(**bad))
+
+
+# --------------------------------------------------------------------------
+# Whole-scheme invariants and physics
+# --------------------------------------------------------------------------
+
+def test_uniform_field_is_exact_fixed_point_and_attractor():
+    """Sec. 3.4 with no droplet: the linear potential between the electrodes
+    is the steady state (anti-bounce-back at y = -1/2 and ny - 1/2), E is
+    uniform and the free charge vanishes."""
+    ny = 16
+    o = oracle.Oracle(W.params(nx=4, ny=ny, CaE=0.2, R0=10.0, T_w=0.0, k_e=10))
+    o.init_psi(np.zeros((ny, 4)))
+    d = o.derived()
+    y = np.arange(ny)[:, None] + 0.5
+    lin = d["phi_bot"] + (d["phi_top"] - d["phi_bot"]) * y / ny
+    o.step(100)
+    assert np.abs(o.get("phi") - lin).max() < 1e-12 * d["phi_top"]
+    o.set("l", np.zeros((5, ny, 4)))
+    o.step(600)
+    assert np.abs(o.get("phi") - lin).max() < 1e-10 * d["phi_top"]
+    assert abs(o.observables()["charge"]) < 1e-12
+
+
+def test_mass_conserved_without_freezing(runs):
+    """Sec. 3.1: with no phase change the phase-field LB conserves sum psi
+    (walls bounce back, x periodic, sum F_i = psi div u = 0)."""
+    r = runs["mass"]
+    assert r["solid"] == 0.0
+    assert abs(r["m1"] - r["m0"]) / r["m0"] < 1e-13
+
+
+def test_laplace_law(runs):
+    """Laplace law in 2D, dp = gamma / R (the paper's surface-tension model,
+    Eqs. Fs and the chemical potential).  At W = 4 lattice units the diffuse
+    interface carries a discretisation error of a few per cent that shrinks
+    as the interface is resolved (W = 5 closer than W = 4)."""
+    pts = [runs[f"laplace_{R}"] for R in (10, 14, 18)]
+    inv_R = np.array([1 / p["R_eff"] for p in pts])
+    dp = np.array([p["dp"] for p in pts])
+    slope, icpt = np.polyfit(inv_R, dp, 1)
+    gamma = pts[0]["gamma"]
+    assert abs(slope / gamma - 1) < 0.08
+    assert abs(icpt) < 0.10 * gamma / 18
+    prod = dp / inv_R
+    assert np.ptp(prod) / prod.mean() < 0.03
+    err4 = abs(runs["laplace_14"]["dp"] * runs["laplace_14"]["R_eff"] / gamma - 1)
+    err5 = abs(runs["laplace_14_W5"]["dp"] * runs["laplace_14_W5"]["R_eff"] / gamma - 1)
+    assert err5 < err4
+
+
+@pytest.mark.parametrize("theta", [60, 90, 120])
+def test_static_contact_angle(runs, theta):
+    """Wetting boundary (Algorithm 1, reading R17): a sessile drop relaxes to
+    the prescribed static angle; circular-cap geometry gives
+    theta = 2 atan(h / a) from height h and base half-width a."""
+    r = runs[f"angle_{theta}"]
+    meas = math.degrees(2 * math.atan(r["height"] / r["base_half"]))
+    assert abs(meas - theta) < 3.0
+
+
+def test_stefan_front_follows_neumann_solution(runs):
+    """One-phase Stefan problem (Sec. 4, Sec. 5.3): the front advances as
+    h = 2 lam sqrt(alpha t) with lam exp(lam^2) erf(lam) = Ste / sqrt(pi)
+    (the textbook Neumann root); fitted slope within 3 %."""
+    from scipy.optimize import brentq
+    from scipy.special import erf
+    r = runs["stefan"]
+    lam = brentq(lambda l: l * math.exp(l * l) * erf(l) - r["Ste"] / math.sqrt(math.pi), 1e-9, 5)
+    t = np.array(r["t"], float)
+    h = np.array(r["front"])
+    slope, icpt = np.polyfit(np.sqrt(t), h, 1)
+    assert abs(slope / (2 * lam * math.sqrt(r["alpha"])) - 1) < 0.03
+    # small-Ste limit printed in Sec. 5.2: h = sqrt(2 Ste Fo) (lengths in R0)
+    assert abs(lam - math.sqrt(r["Ste"] / 2)) / lam < 0.02
+
+
+@pytest.mark.parametrize("rho_sl", GOLDEN["volume_change"]["rho_sl"])
+def test_volume_change_on_freezing(runs, rho_sl):
+    """Three-phase Stefan problem (Sec. 4): a fully frozen layer has height
+    h_f = rho_l h_0 / rho_s (mass conservation)."""
+    r = runs[f"volume_{rho_sl}"]
+    assert r["frozen"] > 0.99
+    assert abs(r["height"] / (r["h0"] / rho_sl) - 1) < 0.02
+
+
+@pytest.mark.parametrize("case", GOLDEN["deformation"]["cases"], ids=lambda c: f"R{c['R']}_S{c['S']}")
+def test_leaky_dielectric_deformation(runs, case):
+    """Sec. 4 (Fig. 5): the steady deformation lies with the small-deformation
+    theories: Feng (2D) D = Ca f_F / (3 (1+R)^2), f_F = R^2 + R + 1 - 3S, and
+    Taylor D = 9 Ca f_T / (16 (2+R)^2).  The sign (prolate/oblate) is exact."""
+    R, S, Ca, B = case["R"], case["S"], case["CaE"], case["B"]
+    r = runs[f"deform_{int(R)}_{int(S)}"]
+    fF = R * R + R + 1 - 3 * S
+    fT = R * R + 1 - 2 * S + 0.6 * (R - S) * (2 + 3 * B) / (1 + B)
+    D_feng = Ca * fF / (3 * (1 + R) ** 2)
+    D_taylor = 9 * Ca / 16 * fT / (2 + R) ** 2
+    assert np.sign(r["D"]) == np.sign(fF) == np.sign(fT)
+    lo, hi = sorted([abs(D_feng), abs(D_taylor)])
+    assert 0.85 * lo <= abs(r["D"]) <= 1.15 * hi
+
+
+def test_regime_table_matches_feng_discriminant():
+    """Sec. 5 (Fig. 6): OB- is oblate, PR+ and PR- are prolate, by the sign of
+    f_F(R, S) = R^2 + R + 1 - 3S."""
+    for name in ("OB-", "PR+", "PR-"):
+        g = GOLDEN["regimes"][name]
+        fF = g["R"] ** 2 + g["R"] + 1 - 3 * g["S"]
+        assert (fF > 0) == (g["shape"] == "prolate")
+        assert W.REGIMES[name] == (g["R"], g["S"])
+
+
+def test_droplet_front_matches_paper(runs):
+    """Sec. 5.2: the centreline front of the freezing droplet is close to the
+    1D relation sqrt(2 Ste Fo) = 0.498 at Ste = 0.2 (the paper measured
+    0.477, a 4.3 % gap).  Pin: within 10 % of 0.498."""
+    g = GOLDEN["droplet_front"]
+    r = runs["front_paper"]
+    assert abs(r["Fo"] - g["Fo"]) < 0.01
+    assert abs(math.sqrt(2 * g["Ste"] * g["Fo"]) - g["h_analytical"]) < 1e-3
+    assert abs(r["front_over_R0"] / g["h_analytical"] - 1) < 0.10
+    assert abs(g["h_numerical"] / g["h_analytical"] - 1) < 0.10
+
+
+@pytest.mark.parametrize("theta", [60.0, 90.0, 120.0])
+def test_observables_geometry_of_initial_cap(theta):
+    """The observable definitions on the initial circular cap: height
+    R (1 - cos theta) above the wall, half-width of row 0 (cell centres at
+    y = 0) equal to the circle's chord there, widest extent 2R (theta >= 90)
+    or row 0's chord (theta < 90), nothing frozen yet."""
+    R, nx, ny = 18.0, 96, 48
+    o = oracle.Oracle(W.params(nx=nx, ny=ny, R0=R, theta_deg=theta))
+    xc, yc = W.sessile_center(nx, R, theta)
+    o.init_droplet(R, xc, yc, 0)
+    ob = o.observables()
+    t = math.radians(theta)
+    chord0 = math.sqrt(R * R - yc * yc)
+    assert abs(ob["height"] - R * (1 - math.cos(t))) < 0.15
+    assert abs(ob["R_tr"] - chord0) < 0.15
+    assert abs(ob["width"] - (2 * R if theta >= 90 else 2 * chord0)) < 0.3
+    assert ob["frozen_fraction"] < 1e-12 and ob["front"] == 0.0 and ob["t_fre"] == -1
+    assert ob["aspect"] == pytest.approx(ob["height"] / ob["width"])
