@@ -1,0 +1,269 @@
+/*
+ * lbm.h -- C ABI of the GB300 phase-field lattice Boltzmann library for the
+ * freezing of a wetting droplet under a uniform electric field
+ * (Huang, Li, Che, Chai, Wang, Shi, arXiv 2410.06657).
+ *
+ * One time step advances four coupled lattice Boltzmann systems on an
+ * nx x ny lattice (Sec. 3, Algorithm 1):
+ *   f  D2Q9 Allen-Cahn phase field psi            (Sec. 3.1, Eq. LB-PF)
+ *   h  D2Q9 incompressible flow with a mass source (Sec. 3.2, Eq. LB_flow)
+ *   g  D2Q9 total enthalpy H -> T, solid fraction  (Sec. 3.3, Eqs. LB_H, Hfl)
+ *   l  D2Q5 electric potential phi                 (Sec. 3.4, Eq. LB_phi)
+ * with the isotropic gradient/Laplacian stencils (Eqs. eqtidi1-2), the
+ * surface-tension and leaky-dielectric forces (Eqs. Fs, Fe), and the wall
+ * treatments of Algorithm 1.  x is periodic; walls sit at y = -1/2 (cold
+ * substrate at T_w, bottom electrode phi = 0, wetting at angle theta) and at
+ * y = ny - 1/2 (adiabatic, top electrode phi = E0 * ny, neutral wetting).
+ *
+ * Conventions for every call:
+ *   - Returns LBM_OK (0) or a negative LBM_ERR_* code; nothing throws.
+ *   - The library owns all device memory of a handle; callers own every
+ *     host buffer they pass (it is only read or written during the call).
+ *   - A handle is bound to one CUDA stream and is not thread-safe.  Calls
+ *     that only enqueue work (lbm_step) return before the GPU finishes;
+ *     calls that return data to the host synchronise that stream.
+ *   - All arithmetic runs in the library's CUDA kernels; there is no CPU
+ *     path.  A call made without a usable GPU returns LBM_ERR_CUDA.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Storage / arithmetic precision of a handle. */
+enum {
+    LBM_FP64 = 0,  /* populations and arithmetic in double                      */
+    LBM_FP32 = 1,  /* populations and arithmetic in float                       */
+    LBM_FP16S = 2  /* populations stored as half after subtracting a reference  */
+                   /* state (weight-shifted), arithmetic in float               */
+};
+
+/* Return codes. */
+enum {
+    LBM_OK = 0,
+    LBM_ERR_BADPARAM = -1,   /* a parameter is out of range (see lbm_params)   */
+    LBM_ERR_OOM = -2,        /* device allocation failed                       */
+    LBM_ERR_DIVERGED = -3,   /* a non-finite psi or H was seen; the handle     */
+                             /* refuses further steps                          */
+    LBM_ERR_CUDA = -4,       /* a CUDA call failed (message: lbm_last_error)   */
+    LBM_ERR_STATE = -5       /* call out of order (e.g. step before init)      */
+};
+
+/*
+ * Problem parameters: the paper's dimensionless numbers plus the lattice
+ * choices it leaves open.  All quantities are in lattice units
+ * (dx = dt = 1, Sec. 3.1).  Derived quantities (Sec. 2 and Sec. 4):
+ *   rho_g = rho_l / rho_lg, rho_s = rho_l * rho_sl, mu_g = mu_l / mu_lg,
+ *   mu_s = mu_l; L = cp_l (T_m - T_w) / Ste; k_phase = rho C_p alpha with
+ *   alpha_g = alpha_l / alpha_lg and alpha_s = alpha_l;
+ *   eps_l = eps_s = S_eps * eps_g; sigma_l = sigma_s = R_sigma * sigma_g;
+ *   E0 = sqrt(CaE * gamma / (eps_g * R0)) (CaE = eps_e E0^2 R / gamma, Sec. 4);
+ *   kappa = 3 gamma W / 2, beta = 12 gamma / W (Sec. 2);
+ *   C_p,ref = 2 cp_s cp_l / (cp_s + cp_l) (Sec. 3.3).
+ * Validity (else LBM_ERR_BADPARAM): nx, ny > 0; k_e >= 1; precision one of
+ * LBM_FP*; W, M, rho_l, rho_lg, rho_sl, mu_l, mu_lg, Ste, alpha_l, alpha_lg,
+ * cp_*, R_sigma, S_eps, eps_g, sigma_g, R0 > 0; gamma, CaE >= 0;
+ * 0 < theta_deg < 180; T_m >= T_w.  These keep every relaxation time above
+ * 1/2 in every phase and every mixture.
+ */
+typedef struct lbm_params {
+    int32_t nx, ny;      /* lattice size                                     */
+    int32_t k_e;         /* potential sweeps per time step (>= 1)            */
+    int32_t precision;   /* LBM_FP64 | LBM_FP32 | LBM_FP16S                  */
+    double W;            /* interface width                                  */
+    double M;            /* phase-field mobility (tau_f = M / c_s^2 + 1/2)   */
+    double gamma;        /* liquid-gas surface tension                       */
+    double rho_l;        /* liquid density                                   */
+    double rho_lg;       /* rho_l / rho_g                                    */
+    double rho_sl;       /* rho_s / rho_l                                    */
+    double mu_l;         /* liquid dynamic viscosity                         */
+    double mu_lg;        /* mu_l / mu_g (the paper's viscosity ratio)        */
+    double Ste;          /* Stefan number cp_l (T_m - T_w) / L               */
+    double alpha_l;      /* liquid thermal diffusivity                       */
+    double alpha_lg;     /* alpha_l / alpha_g                                */
+    double cp_l, cp_s, cp_g;   /* specific heats                             */
+    double T_m;          /* melting temperature                              */
+    double T_w;          /* cold-wall temperature                            */
+    double T_init;       /* initial temperature of the whole domain          */
+    double CaE;          /* electric capillary number                        */
+    double R_sigma;      /* conductivity ratio R = sigma_l / sigma_g         */
+    double S_eps;        /* permittivity ratio S = eps_l / eps_g             */
+    double eps_g;        /* gas permittivity                                 */
+    double sigma_g;      /* gas conductivity (tau_l = sigma / c_s^2 + 1/2)   */
+    double R0;           /* reference radius in CaE and Fo = alpha_l t / R0^2 */
+    double theta_deg;    /* static contact angle on the bottom wall          */
+} lbm_params;
+
+/*
+ * Observables of one instance (row a10).  The paper measures these from
+ * its fields but gives no discrete definition; the library's are:
+ *   mass = sum psi, enthalpy = sum H, solid = sum f_s, charge = sum q_v with
+ *   q_v = div(eps E) by the product rule (all FP64 reductions);
+ *   frozen_fraction = solid / mass;
+ *   height = highest interpolated psi = 1/2 crossing of any column,
+ *            measured from the wall at y = -1/2;
+ *   width  = widest interpolated psi = 1/2 extent of any row;
+ *   aspect = height / width; R_tr = half of row 0's extent (contact line);
+ *   front  = lowest interpolated f_s = 1/2 crossing on column nx/2 above a
+ *            frozen bottom cell (0 if that cell is not frozen);
+ *   t_fre  = first step at which an observables call saw
+ *            frozen_fraction >= 0.99 (-1 until then), Fo_fre its Fourier number;
+ *   status = LBM_OK or LBM_ERR_DIVERGED (non-finite psi or H anywhere).
+ */
+typedef struct lbm_obs {
+    int64_t step;
+    double Fo;
+    double mass, enthalpy, charge, solid, frozen_fraction;
+    double height, width, aspect, R_tr, front;
+    int64_t t_fre;
+    double Fo_fre;
+    int32_t status;
+    int32_t reserved;
+} lbm_obs;
+
+/* Field ids for lbm_get_field / lbm_set_field.  Arrays are host doubles,
+ * row-major [plane][y][x] with x fastest, planes as stated. */
+enum {
+    LBM_FIELD_F = 0,        /* 9 planes: phase-field populations f_i at time n   */
+    LBM_FIELD_H = 1,        /* 9 planes: flow populations h_i                    */
+    LBM_FIELD_G = 2,        /* 9 planes: enthalpy populations g_i                */
+    LBM_FIELD_L = 3,        /* 5 planes: potential populations l_i               */
+    LBM_FIELD_FS_PREV = 4,  /* solid fraction of the previous step               */
+    LBM_FIELD_MDOT_PREV = 5,/* mass source (1 - rho_s/rho_l) d f_s/dt, previous  */
+    LBM_FIELD_Q_PREV = 6,   /* rho C_p T mdot, previous step                     */
+    LBM_FIELD_PSIUX = 7,    /* psi u_x of the previous step (Euler d_t(psi u))   */
+    LBM_FIELD_PSIUY = 8,    /* psi u_y of the previous step                      */
+    LBM_FIELD_P = 9,        /* pressure p of the previous step                   */
+    LBM_FIELD_S = 10,       /* S = rho mdot + u . grad rho of the previous step  */
+    LBM_FIELD_PSI = 11,     /* order parameter psi at time n        (read only)  */
+    LBM_FIELD_FSOLID = 12,  /* solid fraction f_s at time n         (read only)  */
+    LBM_FIELD_T = 13,       /* temperature T at time n              (read only)  */
+    LBM_FIELD_PHI = 14,     /* electric potential phi at time n     (read only)  */
+    LBM_FIELD_HTOT = 15,    /* total enthalpy H at time n           (read only)  */
+    LBM_FIELD_SIGMA = 16    /* conductivity used by the extra potential sweeps   */
+};
+
+/* Message of the last failing call on this thread (static storage). */
+const char *lbm_last_error(void);
+
+/*
+ * Create an instance.  Validates `p` (see lbm_params), derives the lattice
+ * constants of Secs. 2-3, and allocates the device state: two copies of the
+ * 32 populations per cell (f 9, h 9, g 9, l 5) in the precision's storage
+ * type and two copies of 7 per-cell auxiliary fields (previous-step f_s,
+ * mdot, rho C_p T mdot, psi u_x, psi u_y, p, S), plus sigma and a small
+ * reduction workspace.  `stream` is a cudaStream_t (NULL: the legacy
+ * default stream); all work of the handle is enqueued there.
+ * On success *out owns the memory until lbm_destroy.
+ * Errors: BADPARAM, OOM, CUDA.
+ */
+int lbm_create(const lbm_params *p, void *stream, struct lbm_handle **out);
+
+/*
+ * Initial state (Sec. 2; Algorithm 1 "Initialization"): a circular droplet
+ * of radius R centred at (xc, yc) in cell coordinates (cell (x, y) sits at
+ * (x, y); the bottom wall is y = -1/2), psi = 1/2 + 1/2 tanh(2 (R - r) / W);
+ * fluid at rest, p = 0, T = T_init, no solid, all latent heat held
+ * (H = C_p T + psi L); phi linear between the electrodes; every population
+ * at its equilibrium.  Then `presolve` sweeps of the potential LB relax phi
+ * around the droplet before t = 0 (the field and the cold wall act from
+ * t = 0, Sec. 2).  A sessile cap at contact angle theta has
+ * yc = -1/2 - R cos(theta).  Resets the step counter and t_fre.
+ * Errors: BADPARAM (R <= 0, presolve < 0), CUDA.
+ */
+int lbm_init_droplet(struct lbm_handle *h, double R, double xc, double yc, int32_t presolve);
+
+/*
+ * Same initial state from an arbitrary order-parameter field: `psi` is a
+ * host array of ny * nx doubles (row-major, x fastest), copied during the
+ * call.  Errors: BADPARAM (NULL psi, presolve < 0), CUDA.
+ */
+int lbm_init_psi(struct lbm_handle *h, const double *psi, int32_t presolve);
+
+/*
+ * Advance n >= 0 time steps (Algorithm 1 under a Jacobi reading: every
+ * system collides with time-n fields, then all stream, then the walls act).
+ * Each step is one fused kernel launch over the lattice plus k_e - 1
+ * potential-only sweeps (sigma frozen at time n).  Enqueues asynchronously
+ * on the handle's stream (long runs replay a captured CUDA graph).
+ * Errors: STATE (not initialised), DIVERGED (an earlier observables call
+ * saw non-finite values), BADPARAM (n < 0), CUDA.
+ */
+int lbm_step(struct lbm_handle *h, int64_t n);
+
+/*
+ * Observables at the current time (see lbm_obs), reduced on the GPU in
+ * FP64 and copied to *out.  Synchronises the stream.  Updates t_fre.
+ * Returns LBM_ERR_DIVERGED (and sets out->status) if a non-finite psi or H
+ * was found.  Errors: BADPARAM (NULL out), STATE, CUDA.
+ */
+int lbm_observables(struct lbm_handle *h, lbm_obs *out);
+
+/*
+ * Enqueue the observables reduction without waiting; the result stays on
+ * the device until lbm_observables_fetch copies it (synchronising).
+ * Errors: STATE, CUDA.
+ */
+int lbm_observables_async(struct lbm_handle *h);
+int lbm_observables_fetch(struct lbm_handle *h, lbm_obs *out);
+
+/*
+ * Copy one field to the host as doubles (layout: see the field ids).
+ * Synchronises the stream.  Errors: BADPARAM (unknown id, NULL), STATE, CUDA.
+ */
+int lbm_get_field(struct lbm_handle *h, int32_t field, double *host_out);
+
+/*
+ * Overwrite one stored field (ids 0-10 and 16) from host doubles, converting
+ * to the storage precision.  Synchronises.  Errors: BADPARAM (read-only id,
+ * NULL), STATE, CUDA.
+ */
+int lbm_set_field(struct lbm_handle *h, int32_t field, const double *host_in);
+
+/*
+ * Whole-state snapshot for checkpoint/resume and host hand-over: the step
+ * counter, t_fre and every stored array in the handle's storage precision.
+ * lbm_state_bytes gives the size; export copies device -> host (synchronous),
+ * import copies host -> device (enqueued on the stream; from pinned host
+ * memory it is asynchronous, and the caller must keep the buffer alive and
+ * unchanged until the stream reaches that point).  A snapshot only imports
+ * into a handle created with identical lbm_params.
+ * Errors: BADPARAM (NULL, size mismatch), STATE, CUDA.
+ */
+size_t lbm_state_bytes(const struct lbm_handle *h);
+int lbm_export_state(struct lbm_handle *h, void *host, size_t bytes);
+int lbm_import_state(struct lbm_handle *h, const void *host, size_t bytes);
+
+/* Steps taken since the last init.  */
+int64_t lbm_step_count(const struct lbm_handle *h);
+
+/* Free the device state.  NULL is ignored. */
+void lbm_destroy(struct lbm_handle *h);
+
+/*
+ * Batched form: many instances of one precision advance together, one
+ * persistent kernel launch per time step over a work list of (instance,
+ * tile) pairs, so small and uneven lattices fill the GPU.  Members stay
+ * owned by the caller, keep their own state and stay usable alone (their
+ * results are the same as stepping them one by one); the batch holds only
+ * the work list and its launch configuration.  Every member must be
+ * initialised, share the precision, and use the stream the batch was given.
+ * tile_rows picks the tile height (0: autotuned once at creation by timing
+ * the candidate shapes on the members).
+ * Errors: BADPARAM (n < 1, mixed precision, NULL), STATE, OOM, CUDA.
+ */
+int lbm_batch_create(struct lbm_handle *const *members, int32_t n, void *stream,
+                     int32_t tile_rows, struct lbm_batch **out);
+int lbm_batch_step(struct lbm_batch *b, int64_t n);
+int32_t lbm_batch_tile_rows(const struct lbm_batch *b);
+void lbm_batch_destroy(struct lbm_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

@@ -1,0 +1,823 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation,
+// derived lattice constants, device memory, stepping (with CUDA-graph
+// replay of long runs), observables, field access, snapshots and batches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return LBM_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t storage_bytes(int precision) {
+    return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
+}
+size_t aux_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+
+// Lattice constants from the dimensionless parameters (Secs. 2-4).
+void derive(const lbm_params &p, Consts<double> &c) {
+    c.rho[1] = p.rho_l;
+    c.rho[2] = p.rho_l / p.rho_lg;
+    c.rho[0] = p.rho_l * p.rho_sl;
+    c.mu[1] = p.mu_l;
+    c.mu[2] = p.mu_l / p.mu_lg;
+    c.mu[0] = p.mu_l;
+    c.cp[0] = p.cp_s;
+    c.cp[1] = p.cp_l;
+    c.cp[2] = p.cp_g;
+    c.kth[1] = c.rho[1] * c.cp[1] * p.alpha_l;                  // k = rho C_p alpha
+    c.kth[2] = c.rho[2] * c.cp[2] * (p.alpha_l / p.alpha_lg);
+    c.kth[0] = c.rho[0] * c.cp[0] * p.alpha_l;                  // alpha_s = alpha_l
+    c.eps[2] = p.eps_g;
+    c.eps[1] = p.S_eps * p.eps_g;
+    c.eps[0] = c.eps[1];
+    c.sig[2] = p.sigma_g;
+    c.sig[1] = p.R_sigma * p.sigma_g;
+    c.sig[0] = c.sig[1];
+    c.L = p.cp_l * (p.T_m - p.T_w) / p.Ste;
+    c.Cref = 2.0 * p.cp_s * p.cp_l / (p.cp_s + p.cp_l);
+    c.kappa = 1.5 * p.gamma * p.W;
+    c.beta = 12.0 * p.gamma / p.W;
+    c.tau_f = p.M / (1.0 / 3.0) + 0.5;
+    const double E0 = std::sqrt(p.CaE * p.gamma / (p.eps_g * p.R0));
+    c.phi_bot = 0.0;
+    c.phi_top = E0 * p.ny;
+    c.wet = 4.0 / p.W * std::cos(p.theta_deg * 3.14159265358979323846 / 180.0);
+    c.T_m = p.T_m;
+    c.W = p.W;
+    c.one_m_rsl = 1.0 - c.rho[0] / c.rho[1];
+    c.Cref_Tw = c.Cref * p.T_w;
+    c.T_init = p.T_init;
+}
+
+template <typename T>
+Consts<T> cast_consts(const Consts<double> &d) {
+    Consts<T> c;
+    for (int i = 0; i < 3; i++) {
+        c.rho[i] = T(d.rho[i]);
+        c.mu[i] = T(d.mu[i]);
+        c.kth[i] = T(d.kth[i]);
+        c.cp[i] = T(d.cp[i]);
+        c.eps[i] = T(d.eps[i]);
+        c.sig[i] = T(d.sig[i]);
+    }
+    c.L = T(d.L); c.Cref = T(d.Cref); c.kappa = T(d.kappa); c.beta = T(d.beta);
+    c.tau_f = T(d.tau_f); c.phi_bot = T(d.phi_bot); c.phi_top = T(d.phi_top); c.wet = T(d.wet);
+    c.T_m = T(d.T_m); c.W = T(d.W); c.one_m_rsl = T(d.one_m_rsl); c.Cref_Tw = T(d.Cref_Tw);
+    c.T_init = T(d.T_init);
+    return c;
+}
+
+bool pos(double v) { return v > 0.0; }   // false for NaN
+
+const char *validate(const lbm_params &p) {
+    if (p.nx <= 0 || p.ny <= 0) return "nx and ny must be positive";
+    if ((long long)p.nx * p.ny > (1LL << 28)) return "lattice too large";
+    if (p.k_e < 1) return "k_e must be >= 1";
+    if (p.precision < LBM_FP64 || p.precision > LBM_FP16S) return "unknown precision";
+    if (!pos(p.W) || !pos(p.M)) return "W and M must be positive";
+    if (!(p.gamma >= 0.0) || !(p.CaE >= 0.0)) return "gamma and CaE must be >= 0";
+    if (!pos(p.rho_l) || !pos(p.rho_lg) || !pos(p.rho_sl)) return "densities must be positive";
+    if (!pos(p.mu_l) || !pos(p.mu_lg)) return "viscosities must be positive";
+    if (!pos(p.Ste) || !pos(p.alpha_l) || !pos(p.alpha_lg)) return "Ste and diffusivities must be positive";
+    if (!pos(p.cp_l) || !pos(p.cp_s) || !pos(p.cp_g)) return "heat capacities must be positive";
+    if (!pos(p.R_sigma) || !pos(p.S_eps) || !pos(p.eps_g) || !pos(p.sigma_g)) return "electric properties must be positive";
+    if (!pos(p.R0)) return "R0 must be positive";
+    if (!(p.theta_deg > 0.0 && p.theta_deg < 180.0)) return "theta must lie in (0, 180)";
+    if (!(p.T_m >= p.T_w)) return "T_m must be >= T_w";
+    if (!std::isfinite(p.T_init)) return "T_init must be finite";
+    return nullptr;
+}
+
+// Half-precision storage references and scales (weight-shifted form).
+Shift make_shift(const lbm_params &p, const Consts<double> &c) {
+    Shift s;
+    s.f_ref = 0.5f;                        // f_i - w_i / 2: psi in [0, 1] maps to +-w_i / 2
+    s.g_ref = float(c.Cref * p.T_m);       // g_i ~ w_i C_p,ref T near the melting point
+    s.g0_ref = float(0.5 * c.L - c.Cref * p.T_m + (4.0 / 9.0) * c.Cref * p.T_m);
+    s.h_scale = 1.0f;
+    s.l_scale = 1.0f;
+    s.f_scale = 1.0f;
+    s.g_scale = 1.0f;
+    return s;
+}
+
+int obs_grid_blocks(int nx, int ny) { return ((nx + 31) / 32) * ((ny + 7) / 8); }
+
+}  // namespace
+
+int lbm::obs_blocks(int nx, int ny) { return obs_grid_blocks(nx, ny); }
+
+struct lbm_handle {
+    lbm_params P;
+    Consts<double> cd;
+    Consts<float> cf;
+    Shift sh;
+    DevState s;
+    cudaStream_t st;
+    cudaStream_t cap;          // private stream used only to capture graphs
+    void *mem = nullptr;
+    size_t mem_bytes = 0;
+    void *ws_mem = nullptr;
+    ObsScratch ws;
+    size_t ws_max_bytes = 0, ws_min_bytes = 0, ws_u32_bytes = 0;
+    unsigned long long *ws_max_base = nullptr, *ws_min_base = nullptr;
+    unsigned int *ws_u32_base = nullptr;
+    double *staging = nullptr;
+    int cur = 0, lcur = 0;
+    int64_t step = 0;
+    bool inited = false, diverged = false;
+    int tile_rows = 8;
+    // graph cache: one per starting parity (cur, lcur)
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int gsteps = 0;
+};
+
+struct lbm_batch {
+    std::vector<lbm_handle *> m;
+    int precision = LBM_FP32;
+    int k_e = 1;
+    cudaStream_t st = nullptr;
+    BatchItem *items_dev = nullptr;
+    void *consts_dev = nullptr;
+    int total_tiles = 0, total_sweep_tiles = 0, tile_rows = 8, grid = 0, sweep_grid = 0;
+    int flips = 0;                 // steps since the list was built (mod 2 matters)
+    int lflips = 0;                // potential sweeps since then
+    std::vector<int> cur0, lcur0;  // member parities when the list was built
+    cudaStream_t cap = nullptr;    // private capture stream
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+};
+
+namespace {
+
+const void *consts_for(const lbm_handle *h) {
+    return h->P.precision == LBM_FP64 ? static_cast<const void *>(&h->cd) : static_cast<const void *>(&h->cf);
+}
+
+cudaError_t do_step(lbm_handle *h, cudaStream_t st) {
+    const int ws = h->P.k_e > 1 ? 1 : 0;
+    const void *c = consts_for(h);
+    cudaError_t e;
+    switch (h->P.precision) {
+    case LBM_FP64: e = launch_step_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
+    case LBM_FP32: e = launch_step_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
+    default: e = launch_step_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    h->cur ^= 1;
+    h->lcur ^= 1;
+    for (int j = 1; j < h->P.k_e; j++) {
+        switch (h->P.precision) {
+        case LBM_FP64: e = launch_sweep_f64(h->s, h->lcur, c, h->sh, st); break;
+        case LBM_FP32: e = launch_sweep_f32(h->s, h->lcur, c, h->sh, st); break;
+        default: e = launch_sweep_f16s(h->s, h->lcur, c, h->sh, st); break;
+        }
+        if (e != cudaSuccess) return e;
+        h->lcur ^= 1;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t do_sweep(lbm_handle *h, cudaStream_t st) {
+    const void *c = consts_for(h);
+    cudaError_t e;
+    switch (h->P.precision) {
+    case LBM_FP64: e = launch_sweep_f64(h->s, h->lcur, c, h->sh, st); break;
+    case LBM_FP32: e = launch_sweep_f32(h->s, h->lcur, c, h->sh, st); break;
+    default: e = launch_sweep_f16s(h->s, h->lcur, c, h->sh, st); break;
+    }
+    if (e == cudaSuccess) h->lcur ^= 1;
+    return e;
+}
+
+void drop_graphs(lbm_handle *h) {
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            if (h->gexec[a][b]) {
+                cudaGraphExecDestroy(h->gexec[a][b]);
+                h->gexec[a][b] = nullptr;
+            }
+}
+
+int ensure_staging(lbm_handle *h) {
+    if (h->staging) return LBM_OK;
+    const size_t n = (size_t)9 * h->P.nx * h->P.ny;
+    if (cudaMalloc(&h->staging, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        h->staging = nullptr;
+        return fail(LBM_ERR_OOM, "staging allocation failed");
+    }
+    return LBM_OK;
+}
+
+int finish_init(lbm_handle *h, const double *psi_dev, double R, double xc, double yc, int presolve) {
+    h->cur = 0;
+    h->lcur = 0;
+    const void *c = consts_for(h);
+    cudaError_t e;
+    switch (h->P.precision) {
+    case LBM_FP64: e = launch_init_f64(h->s, psi_dev, R, xc, yc, c, h->sh, h->st); break;
+    case LBM_FP32: e = launch_init_f32(h->s, psi_dev, R, xc, yc, c, h->sh, h->st); break;
+    default: e = launch_init_f16s(h->s, psi_dev, R, xc, yc, c, h->sh, h->st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    for (int j = 0; j < presolve; j++) {
+        e = do_sweep(h, h->st);
+        if (e != cudaSuccess) return cuda_fail(e, "pre-solve sweep");
+    }
+    lbm_obs o;
+    std::memset(&o, 0, sizeof o);
+    o.t_fre = -1;
+    o.Fo_fre = -1.0;
+    CK(cudaMemcpyAsync(h->ws.obs, &o, sizeof o, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->step = 0;
+    h->inited = true;
+    h->diverged = false;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err.c_str(); }
+
+int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
+    if (!p || !out) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    *out = nullptr;
+    if (const char *why = validate(*p)) return fail(LBM_ERR_BADPARAM, why);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(LBM_ERR_CUDA, "no CUDA device");
+    }
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(LBM_ERR_OOM, "host allocation failed");
+    h->P = *p;
+    derive(*p, h->cd);
+    h->cf = cast_consts<float>(h->cd);
+    h->sh = make_shift(*p, h->cd);
+    h->st = static_cast<cudaStream_t>(stream);
+    const int nx = p->nx, ny = p->ny;
+    const int pitch = (int)round_up(nx, 32);
+    const long long plane = (long long)pitch * ny;
+    const size_t sb = storage_bytes(p->precision), ab = aux_bytes(p->precision);
+    const size_t pop_b = round_up((size_t)NPOP * plane * sb, 256);
+    const size_t aux_b = round_up((size_t)NAUX * plane * ab, 256);
+    const size_t sig_b = round_up((size_t)plane * ab, 256);
+    h->mem_bytes = 2 * pop_b + 2 * aux_b + sig_b;
+    if (cudaMalloc(&h->mem, h->mem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(LBM_ERR_OOM, "device allocation of the state failed");
+    }
+    char *b = static_cast<char *>(h->mem);
+    h->s.pop[0] = b;
+    h->s.pop[1] = b + pop_b;
+    h->s.aux[0] = b + 2 * pop_b;
+    h->s.aux[1] = b + 2 * pop_b + aux_b;
+    h->s.sigma = b + 2 * pop_b + 2 * aux_b;
+    h->s.nx = nx;
+    h->s.ny = ny;
+    h->s.pitch = pitch;
+    h->s.plane = plane;
+    // observables workspace
+    const int nb = obs_grid_blocks(nx, ny);
+    const size_t part_b = round_up((size_t)nb * 4 * sizeof(double), 256);
+    h->ws_max_bytes = round_up((size_t)(2 + ny) * 8, 256);
+    h->ws_min_bytes = round_up((size_t)(1 + ny) * 8, 256);
+    h->ws_u32_bytes = round_up((size_t)(ny + 2) * 4, 256);
+    const size_t obs_b = round_up(sizeof(lbm_obs), 256);
+    if (cudaMalloc(&h->ws_mem, part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->mem);
+        delete h;
+        return fail(LBM_ERR_OOM, "device allocation of the reduction workspace failed");
+    }
+    char *w = static_cast<char *>(h->ws_mem);
+    h->ws.partials = reinterpret_cast<double *>(w);
+    h->ws_max_base = reinterpret_cast<unsigned long long *>(w + part_b);
+    h->ws_min_base = reinterpret_cast<unsigned long long *>(w + part_b + h->ws_max_bytes);
+    h->ws_u32_base = reinterpret_cast<unsigned int *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes);
+    h->ws.maxv = h->ws_max_base;
+    h->ws.minv = h->ws_min_base;
+    h->ws.rowany = h->ws_u32_base;
+    h->ws.bad = h->ws_u32_base + ny;
+    h->ws.obs = reinterpret_cast<lbm_obs *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes);
+    h->ws.nblocks = nb;
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->ws_mem);
+        cudaFree(h->mem);
+        delete h;
+        return fail(LBM_ERR_CUDA, "stream creation failed");
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->st);
+    drop_graphs(h);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    cudaFree(h->staging);
+    cudaFree(h->ws_mem);
+    cudaFree(h->mem);
+    delete h;
+}
+
+int lbm_init_droplet(lbm_handle *h, double R, double xc, double yc, int32_t presolve) {
+    if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    if (!(R > 0.0) || presolve < 0 || !std::isfinite(xc) || !std::isfinite(yc))
+        return fail(LBM_ERR_BADPARAM, "R must be positive, presolve >= 0, centre finite");
+    return finish_init(h, nullptr, R, xc, yc, presolve);
+}
+
+int lbm_init_psi(lbm_handle *h, const double *psi, int32_t presolve) {
+    if (!h || !psi) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (presolve < 0) return fail(LBM_ERR_BADPARAM, "presolve must be >= 0");
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->staging, psi, sizeof(double) * h->P.nx * h->P.ny, cudaMemcpyHostToDevice, h->st));
+    return finish_init(h, h->staging, 0.0, 0.0, 0.0, presolve);
+}
+
+int lbm_step(lbm_handle *h, int64_t n) {
+    if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    if (n < 0) return fail(LBM_ERR_BADPARAM, "n must be >= 0");
+    if (!h->inited) return fail(LBM_ERR_STATE, "step before init");
+    if (h->diverged) return fail(LBM_ERR_DIVERGED, "instance diverged earlier");
+    // Long runs replay a captured graph of G steps (G even, so both parities
+    // return to their starting values and the graph can be reused).
+    const int G = 32;
+    while (n >= G) {
+        cudaGraphExec_t &ex = h->gexec[h->cur][h->lcur];
+        if (!ex) {
+            const int c0 = h->cur, l0 = h->lcur;
+            CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int j = 0; j < G && e == cudaSuccess; j++) e = do_step(h, h->cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+            h->cur = c0;
+            h->lcur = l0;
+            if (e != cudaSuccess) return cuda_fail(e, "graph capture of the step");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ex = nullptr;
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+        }
+        CK(cudaGraphLaunch(ex, h->st));
+        // G steps flip cur G times and lcur G * k_e times: both even.
+        h->step += G;
+        n -= G;
+    }
+    for (int64_t j = 0; j < n; j++) {
+        cudaError_t e = do_step(h, h->st);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel");
+        h->step += 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_observables_async(lbm_handle *h) {
+    if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    if (!h->inited) return fail(LBM_ERR_STATE, "observables before init");
+    CK(cudaMemsetAsync(h->ws_max_base, 0x00, h->ws_max_bytes, h->st));
+    CK(cudaMemsetAsync(h->ws_min_base, 0xFF, h->ws_min_bytes, h->st));
+    CK(cudaMemsetAsync(h->ws_u32_base, 0x00, h->ws_u32_bytes, h->st));
+    Scalars sc;
+    sc.step = h->step;
+    sc.alpha_l = h->P.alpha_l;
+    sc.R0 = h->P.R0;
+    cudaError_t e;
+    switch (h->P.precision) {
+    case LBM_FP64: e = launch_obs_f64(h->s, h->cur, h->lcur, &h->cd, h->sh, h->ws, sc, h->st); break;
+    case LBM_FP32: e = launch_obs_f32(h->s, h->cur, h->lcur, &h->cd, h->sh, h->ws, sc, h->st); break;
+    default: e = launch_obs_f16s(h->s, h->cur, h->lcur, &h->cd, h->sh, h->ws, sc, h->st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "observables kernels");
+    return LBM_OK;
+}
+
+int lbm_observables_fetch(lbm_handle *h, lbm_obs *out) {
+    if (!h || !out) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (!h->inited) return fail(LBM_ERR_STATE, "observables before init");
+    CK(cudaMemcpyAsync(out, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (out->status == LBM_ERR_DIVERGED) {
+        h->diverged = true;
+        return fail(LBM_ERR_DIVERGED, "non-finite psi or H");
+    }
+    return LBM_OK;
+}
+
+int lbm_observables(lbm_handle *h, lbm_obs *out) {
+    if (!out) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    int rc = lbm_observables_async(h);
+    if (rc) return rc;
+    return lbm_observables_fetch(h, out);
+}
+
+static int field_planes(int field) {
+    if (field == LBM_FIELD_F || field == LBM_FIELD_H || field == LBM_FIELD_G) return 9;
+    if (field == LBM_FIELD_L) return 5;
+    if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_SIGMA) return 1;
+    return 0;
+}
+
+int lbm_get_field(lbm_handle *h, int32_t field, double *host_out) {
+    if (!h || !host_out) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    const int planes = field_planes(field);
+    if (!planes) return fail(LBM_ERR_BADPARAM, "unknown field id");
+    if (!h->inited) return fail(LBM_ERR_STATE, "field access before init");
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+    cudaError_t e;
+    switch (h->P.precision) {
+    case LBM_FP64: e = launch_get_f64(h->s, h->cur, h->lcur, field, &h->cd, h->sh, h->staging, h->st); break;
+    case LBM_FP32: e = launch_get_f32(h->s, h->cur, h->lcur, field, &h->cd, h->sh, h->staging, h->st); break;
+    default: e = launch_get_f16s(h->s, h->cur, h->lcur, field, &h->cd, h->sh, h->staging, h->st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "field gather kernel");
+    CK(cudaMemcpyAsync(host_out, h->staging, sizeof(double) * planes * h->P.nx * h->P.ny,
+                       cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+}
+
+int lbm_set_field(lbm_handle *h, int32_t field, const double *host_in) {
+    if (!h || !host_in) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    const int planes = field_planes(field);
+    if (!planes || (field >= LBM_FIELD_PSI && field <= LBM_FIELD_HTOT))
+        return fail(LBM_ERR_BADPARAM, "field id is not writable");
+    if (!h->inited) return fail(LBM_ERR_STATE, "field access before init");
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->staging, host_in, sizeof(double) * planes * h->P.nx * h->P.ny,
+                       cudaMemcpyHostToDevice, h->st));
+    const void *c = consts_for(h);
+    cudaError_t e;
+    switch (h->P.precision) {
+    case LBM_FP64: e = launch_set_f64(h->s, h->cur, h->lcur, field, c, h->sh, h->staging, h->st); break;
+    case LBM_FP32: e = launch_set_f32(h->s, h->cur, h->lcur, field, c, h->sh, h->staging, h->st); break;
+    default: e = launch_set_f16s(h->s, h->cur, h->lcur, field, c, h->sh, h->staging, h->st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "field scatter kernel");
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+}
+
+// Snapshot layout: header | f,h,g planes | l planes | aux planes | sigma | lbm_obs
+struct SnapHeader {
+    char magic[8];
+    int64_t step;
+    int32_t nx, ny, precision, k_e;
+    int64_t body_bytes;
+    char pad[24];
+};
+
+static void snap_sizes(const lbm_handle *h, size_t &fhg, size_t &l, size_t &aux, size_t &sig) {
+    const size_t sb = storage_bytes(h->P.precision), ab = aux_bytes(h->P.precision);
+    fhg = (size_t)NFHG * h->s.plane * sb;
+    l = (size_t)(NPOP - NFHG) * h->s.plane * sb;
+    aux = (size_t)NAUX * h->s.plane * ab;
+    sig = (size_t)h->s.plane * ab;
+}
+
+size_t lbm_state_bytes(const lbm_handle *h) {
+    if (!h) return 0;
+    size_t a, b, c, d;
+    snap_sizes(h, a, b, c, d);
+    return sizeof(SnapHeader) + a + b + c + d + sizeof(lbm_obs);
+}
+
+int lbm_export_state(lbm_handle *h, void *host, size_t bytes) {
+    if (!h || !host) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (bytes != lbm_state_bytes(h)) return fail(LBM_ERR_BADPARAM, "snapshot size mismatch");
+    if (!h->inited) return fail(LBM_ERR_STATE, "export before init");
+    size_t a, b, c, d;
+    snap_sizes(h, a, b, c, d);
+    SnapHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, "LBMGB300", 8);
+    hd.step = h->step;
+    hd.nx = h->P.nx;
+    hd.ny = h->P.ny;
+    hd.precision = h->P.precision;
+    hd.k_e = h->P.k_e;
+    hd.body_bytes = (int64_t)(a + b + c + d + sizeof(lbm_obs));
+    char *o = static_cast<char *>(host);
+    std::memcpy(o, &hd, sizeof hd);
+    o += sizeof hd;
+    const size_t sb = storage_bytes(h->P.precision);
+    CK(cudaMemcpyAsync(o, h->s.pop[h->cur], a, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(o + a, static_cast<char *>(h->s.pop[h->lcur]) + (size_t)NFHG * h->s.plane * sb, b,
+                       cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(o + a + b, h->s.aux[h->cur], c, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(o + a + b + c, h->s.sigma, d, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(o + a + b + c + d, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+}
+
+int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
+    if (!h || !host) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (bytes != lbm_state_bytes(h)) return fail(LBM_ERR_BADPARAM, "snapshot size mismatch");
+    SnapHeader hd;
+    std::memcpy(&hd, host, sizeof hd);
+    if (std::memcmp(hd.magic, "LBMGB300", 8) != 0 || hd.nx != h->P.nx || hd.ny != h->P.ny ||
+        hd.precision != h->P.precision || hd.k_e != h->P.k_e)
+        return fail(LBM_ERR_BADPARAM, "snapshot does not match this handle");
+    size_t a, b, c, d;
+    snap_sizes(h, a, b, c, d);
+    const char *o = static_cast<const char *>(host) + sizeof hd;
+    const size_t sb = storage_bytes(h->P.precision);
+    CK(cudaMemcpyAsync(h->s.pop[h->cur], o, a, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(static_cast<char *>(h->s.pop[h->lcur]) + (size_t)NFHG * h->s.plane * sb, o + a, b,
+                       cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->s.aux[h->cur], o + a + b, c, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->s.sigma, o + a + b + c, d, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->ws.obs, o + a + b + c + d, sizeof(lbm_obs), cudaMemcpyHostToDevice, h->st));
+    h->step = hd.step;
+    h->inited = true;
+    h->diverged = false;
+    return LBM_OK;
+}
+
+int64_t lbm_step_count(const lbm_handle *h) { return h ? h->step : -1; }
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+
+static cudaError_t batch_launch_steps(lbm_batch *b, int64_t n, cudaStream_t st) {
+    for (int64_t j = 0; j < n; j++) {
+        const int fc = b->flips & 1, fl = b->lflips & 1;
+        cudaError_t e;
+        switch (b->precision) {
+        case LBM_FP64:
+            e = launch_batch_step_f64(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_tiles, b->tile_rows,
+                                      b->grid, fc, fl, st);
+            break;
+        case LBM_FP32:
+            e = launch_batch_step_f32(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_tiles, b->tile_rows,
+                                      b->grid, fc, fl, st);
+            break;
+        default:
+            e = launch_batch_step_f16s(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_tiles,
+                                       b->tile_rows, b->grid, fc, fl, st);
+            break;
+        }
+        if (e != cudaSuccess) return e;
+        b->flips++;
+        b->lflips++;
+        for (int s = 1; s < b->k_e; s++) {
+            const int fl2 = b->lflips & 1;
+            switch (b->precision) {
+            case LBM_FP64:
+                e = launch_batch_sweep_f64(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_sweep_tiles,
+                                           b->sweep_grid, fl2, st);
+                break;
+            case LBM_FP32:
+                e = launch_batch_sweep_f32(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_sweep_tiles,
+                                           b->sweep_grid, fl2, st);
+                break;
+            default:
+                e = launch_batch_sweep_f16s(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_sweep_tiles,
+                                            b->sweep_grid, fl2, st);
+                break;
+            }
+            if (e != cudaSuccess) return e;
+            b->lflips++;
+        }
+    }
+    return cudaSuccess;
+}
+
+static int batch_build(lbm_batch *b, int tile_rows) {
+    std::vector<BatchItem> items(b->m.size());
+    int tiles = 0, sweeps = 0;
+    for (size_t i = 0; i < b->m.size(); i++) {
+        lbm_handle *h = b->m[i];
+        BatchItem &it = items[i];
+        it.s = h->s;
+        it.cur = h->cur;
+        it.lcur = h->lcur;
+        it.write_sigma = h->P.k_e > 1 ? 1 : 0;
+        it.tiles_x = (h->P.nx + 31) / 32;
+        it.tiles_y = (h->P.ny + tile_rows - 1) / tile_rows;
+        it.tile_begin = tiles;
+        tiles += it.tiles_x * it.tiles_y;
+        it.sweep_tiles_x = it.tiles_x;
+        it.sweep_begin = sweeps;
+        sweeps += it.tiles_x * ((h->P.ny + 7) / 8);
+        it.sh = h->sh;
+    }
+    b->cur0.resize(b->m.size());
+    b->lcur0.resize(b->m.size());
+    for (size_t i = 0; i < b->m.size(); i++) {
+        b->cur0[i] = b->m[i]->cur;
+        b->lcur0[i] = b->m[i]->lcur;
+    }
+    for (int a = 0; a < 2; a++)
+        for (int c = 0; c < 2; c++)
+            if (b->gexec[a][c]) {
+                cudaGraphExecDestroy(b->gexec[a][c]);
+                b->gexec[a][c] = nullptr;
+            }
+    b->total_tiles = tiles;
+    b->total_sweep_tiles = sweeps;
+    b->tile_rows = tile_rows;
+    cudaFree(b->items_dev);
+    b->items_dev = nullptr;
+    CK(cudaMalloc(&b->items_dev, items.size() * sizeof(BatchItem)));
+    CK(cudaMemcpyAsync(b->items_dev, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, b->st));
+    CK(cudaStreamSynchronize(b->st));
+    b->flips = 0;
+    b->lflips = 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    per_sm = tile_rows == 16 ? 2 : (tile_rows == 8 ? 4 : 8);
+    b->grid = std::min(tiles, sms * per_sm);
+    b->sweep_grid = std::min(sweeps, sms * 8);
+    return LBM_OK;
+}
+
+int lbm_batch_create(lbm_handle *const *members, int32_t n, void *stream, int32_t tile_rows, lbm_batch **out) {
+    if (!members || !out || n < 1) return fail(LBM_ERR_BADPARAM, "need at least one member");
+    *out = nullptr;
+    if (tile_rows != 0 && tile_rows != 4 && tile_rows != 8 && tile_rows != 16)
+        return fail(LBM_ERR_BADPARAM, "tile_rows must be 0, 4, 8 or 16");
+    for (int i = 0; i < n; i++) {
+        if (!members[i]) return fail(LBM_ERR_BADPARAM, "NULL member");
+        if (!members[i]->inited) return fail(LBM_ERR_STATE, "member not initialised");
+        if (members[i]->P.precision != members[0]->P.precision)
+            return fail(LBM_ERR_BADPARAM, "members must share the precision");
+        if (members[i]->P.k_e != members[0]->P.k_e) return fail(LBM_ERR_BADPARAM, "members must share k_e");
+        if (members[i]->diverged) return fail(LBM_ERR_DIVERGED, "member diverged earlier");
+    }
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return fail(LBM_ERR_OOM, "host allocation failed");
+    b->m.assign(members, members + n);
+    b->precision = members[0]->P.precision;
+    b->k_e = members[0]->P.k_e;
+    b->st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(LBM_ERR_CUDA, "stream creation failed");
+    }
+    // per-member constants in the arithmetic type
+    const size_t csz = b->precision == LBM_FP64 ? sizeof(Consts<double>) : sizeof(Consts<float>);
+    std::vector<char> cs(csz * n);
+    for (int i = 0; i < n; i++) std::memcpy(cs.data() + csz * i, consts_for(members[i]), csz);
+    if (cudaMalloc(&b->consts_dev, cs.size()) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(LBM_ERR_OOM, "batch constants allocation failed");
+    }
+    int rc = LBM_OK;
+    if (cudaMemcpy(b->consts_dev, cs.data(), cs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(LBM_ERR_CUDA, "batch constants copy failed");
+    if (!rc && tile_rows == 0) {
+        // Autotune: time each tile height on the members' own data.  The step
+        // reads one copy and writes the other, so re-running it without
+        // flipping parities leaves every member's state unchanged.
+        float best = 1e30f;
+        int best_rows = 8;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int rows : {4, 8, 16}) {
+            if ((rc = batch_build(b, rows))) break;
+            const int k_e = b->k_e;
+            b->k_e = 1;
+            cudaError_t e = batch_launch_steps(b, 1, b->st);          // warm-up
+            b->flips = 0; b->lflips = 0;
+            cudaEventRecord(e0, b->st);
+            for (int r = 0; r < 5 && e == cudaSuccess; r++) {
+                e = batch_launch_steps(b, 1, b->st);
+                b->flips = 0; b->lflips = 0;
+            }
+            cudaEventRecord(e1, b->st);
+            b->k_e = k_e;
+            if (e != cudaSuccess) { rc = cuda_fail(e, "autotune launch"); break; }
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(LBM_ERR_CUDA, "autotune sync"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_rows = rows; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        tile_rows = best_rows;
+    }
+    if (!rc) rc = batch_build(b, tile_rows);
+    if (rc) {
+        lbm_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *b, int64_t n) {
+    if (!b) return fail(LBM_ERR_BADPARAM, "NULL batch");
+    if (n < 0) return fail(LBM_ERR_BADPARAM, "n must be >= 0");
+    for (lbm_handle *h : b->m)
+        if (h->diverged) return fail(LBM_ERR_DIVERGED, "a member diverged earlier");
+    // A member stepped alone since the list was built has other parities:
+    // rebuild the list from the members' current state.
+    for (size_t i = 0; i < b->m.size(); i++) {
+        if (b->m[i]->cur != (b->cur0[i] ^ (b->flips & 1)) || b->m[i]->lcur != (b->lcur0[i] ^ (b->lflips & 1))) {
+            int rc = batch_build(b, b->tile_rows);
+            if (rc) return rc;
+            break;
+        }
+    }
+    const int64_t total = n;
+    const int G = 32;   // graph length: even, so every parity returns to its start
+    while (n >= G) {
+        cudaGraphExec_t &ex = b->gexec[b->flips & 1][b->lflips & 1];
+        if (!ex) {
+            const int f0 = b->flips, l0 = b->lflips;
+            CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = batch_launch_steps(b, G, b->cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+            b->flips = f0;
+            b->lflips = l0;
+            if (e != cudaSuccess) return cuda_fail(e, "graph capture of the batch step");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ex = nullptr;
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+        }
+        CK(cudaGraphLaunch(ex, b->st));
+        b->flips += G;
+        b->lflips += G * b->k_e;
+        n -= G;
+    }
+    cudaError_t e = batch_launch_steps(b, n, b->st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch step");
+    for (lbm_handle *h : b->m) {
+        h->cur ^= (int)(total & 1);
+        h->lcur ^= (int)((total * h->P.k_e) & 1);
+        h->step += total;
+    }
+    return LBM_OK;
+}
+
+int32_t lbm_batch_tile_rows(const lbm_batch *b) { return b ? b->tile_rows : 0; }
+
+void lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->st);
+    for (int a = 0; a < 2; a++)
+        for (int c = 0; c < 2; c++)
+            if (b->gexec[a][c]) cudaGraphExecDestroy(b->gexec[a][c]);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->items_dev);
+    cudaFree(b->consts_dev);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,1025 @@
+// Fused sm_103a kernels of the phase-field LB electrofreezing step
+// (arXiv 2410.06657, Secs. 2-3 and Algorithm 1), templated on
+//   S  storage type of the populations (double, float, __half),
+//   T  arithmetic type (double or float),
+//   A  type of the auxiliary per-cell fields (double or float).
+// Included once by each precision's translation unit.
+//
+// Memory layout (all structure-of-arrays, x fastest, rows padded to `pitch`):
+//   pop[b]  : 32 planes  f_0..8 | h_0..8 | g_0..8 | l_0..4
+//   aux[b]  : 7 planes   f_s, mdot, rho C_p T mdot, psi u_x, psi u_y, p, S
+//             of the previous step (read by the next step's stencils, so the
+//             step reads copy b and writes copy 1-b)
+//   sigma   : conductivity at time n for the extra potential sweeps.
+// f, h, g swap copies every step; l swaps on every potential sweep, so it
+// keeps its own parity.
+//
+// One step is one launch.  A thread block owns a 32 x BY tile.  Phase 1
+// computes the local macroscopic fields (row a1) of the tile and of its
+// one-cell halo (recomputed from the halo's own populations, so no second
+// pass over HBM is needed) into shared memory; phase 2 applies the
+// radius-1 stencils (a2), forces (a3), flow macros (a4), the four
+// collisions (a5-a8) and pushes the post-collision populations to their
+// destinations in the other copy, applying the wall rules (a9).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// D2Q9 (Sec. 3.1): rest; E, N, W, S; NE, NW, SW, SE.
+__device__ constexpr int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ constexpr int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__device__ constexpr int OPP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+// D2Q5 (Sec. 3.4): rest; E, N, W, S.
+__device__ constexpr int CX5[5] = {0, 1, 0, -1, 0};
+__device__ constexpr int CY5[5] = {0, 0, 1, 0, -1};
+__device__ constexpr int OPP5[5] = {0, 3, 4, 1, 2};
+
+template <typename T>
+__device__ __forceinline__ constexpr T w9(int i) {
+    return i == 0 ? T(4.0 / 9.0) : (i < 5 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+}
+template <typename T>
+__device__ __forceinline__ constexpr T w5(int i) {
+    return i == 0 ? T(1.0 / 3.0) : T(1.0 / 6.0);
+}
+template <typename T>
+__device__ __forceinline__ constexpr T cs2() { return T(1.0 / 3.0); }
+
+// ---------------------------------------------------------------------------
+// Storage policies: how a population of arithmetic type T is kept in S.
+// ---------------------------------------------------------------------------
+template <typename S, typename T>
+struct Pol {
+    static constexpr bool shifted = false;
+    __device__ static __forceinline__ T ld(const S *p, T, float) { return T(*p); }
+    __device__ static __forceinline__ void st(S *p, T v, T, float) { *p = S(v); }
+};
+template <>
+struct Pol<__half, float> {
+    static constexpr bool shifted = true;
+    __device__ static __forceinline__ float ld(const __half *p, float ref, float inv_scale) {
+        return __half2float(*p) * inv_scale + ref;
+    }
+    __device__ static __forceinline__ void st(__half *p, float v, float ref, float scale) {
+        *p = __float2half_rn((v - ref) * scale);
+    }
+};
+
+// Per-cell reference values of the weight-shifted half storage.
+template <typename T>
+struct Refs {
+    T f[9], g[9], l[5];
+};
+
+template <typename S, typename T>
+__device__ __forceinline__ void make_refs(Refs<T> &r, const Shift &sh, const Consts<T> &c, int y,
+                                          int ny) {
+    if constexpr (Pol<S, T>::shifted) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            r.f[i] = w9<T>(i) * T(sh.f_ref);
+            r.g[i] = (i == 0) ? T(sh.g0_ref) : w9<T>(i) * T(sh.g_ref);
+        }
+        // linear potential between the electrodes
+        T phil = c.phi_bot + (c.phi_top - c.phi_bot) * (T(y) + T(0.5)) / T(ny);
+#pragma unroll
+        for (int i = 0; i < 5; i++) r.l[i] = (i == 0) ? (w5<T>(0) - T(1)) * phil : w5<T>(i) * phil;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise physics (shared by the step, observables and field kernels).
+// ---------------------------------------------------------------------------
+
+// Eq. (Computed): three-phase property law.
+template <typename T>
+__device__ __forceinline__ T chi(T fs, T psi, const T v[3]) {
+    return fs * v[0] + (T(1) - fs) * psi * v[1] + (T(1) - fs) * (T(1) - psi) * v[2];
+}
+
+// Eq. (Hfl) with H_s = C_p T_m, latent heat carried by the liquid part
+// (L_eff = psi L): liquid fraction and temperature from total enthalpy.
+template <typename T>
+__device__ __forceinline__ void enthalpy_inversion(T H, T psi, T cp, T Tm, T L, T &fl, T &Tt) {
+    T Hs = cp * Tm;
+    T Leff = psi * L;
+    T Hl = Hs + Leff;
+    if (H < Hs)
+        Tt = H / cp;
+    else if (H <= Hl)
+        Tt = Tm;
+    else
+        Tt = Tm + (H - Hl) / cp;
+    if (Leff < T(1e-12)) {
+        fl = T(1);
+    } else {
+        T r = (H - Hs) / Leff;
+        fl = r < T(0) ? T(0) : (r > T(1) ? T(1) : r);
+    }
+}
+
+template <typename T>
+struct Macro {
+    T psi, H, T_, fs, rho, eps, phi;
+};
+
+// Row a1: local macroscopic quantities from the populations at time n
+// (psi and H use the previous step's mdot and rho C_p T mdot).
+template <typename T>
+__device__ __forceinline__ void local_macros(const T f[9], const T g[9], T l1234, T fs_prev,
+                                             T mdot_prev, T Q_prev, const Consts<T> &c,
+                                             Macro<T> &m) {
+    T sf = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; i++) sf += f[i];
+    m.psi = sf / (T(1) - T(0.5) * mdot_prev);             // Eq. (Computed_psi)
+    T sg = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; i++) sg += g[i];
+    m.H = sg + T(0.5) * Q_prev;                           // Sec. 3.3
+    T cp_lev = chi(fs_prev, m.psi, c.cp);
+    T fl;
+    enthalpy_inversion(m.H, m.psi, cp_lev, c.T_m, c.L, fl, m.T_);
+    m.fs = m.psi * (T(1) - fl);
+    m.rho = chi(m.fs, m.psi, c.rho);
+    m.eps = chi(m.fs, m.psi, c.eps);
+    m.phi = l1234 / (T(1) - w5<T>(0));                    // Eq. (Computed_phi)
+}
+
+// Isotropic stencils (Eqs. eqtidi1-2) on a shared-memory tile.
+template <typename T, int W>
+__device__ __forceinline__ void grad_s(const T (*z)[W], int ex, int ey, T &gx, T &gy) {
+    T sx = T(0), sy = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+        T v = z[ey + CY[i]][ex + CX[i]];
+        sx += w9<T>(i) * T(CX[i]) * v;
+        sy += w9<T>(i) * T(CY[i]) * v;
+    }
+    gx = sx / cs2<T>();
+    gy = sy / cs2<T>();
+}
+template <typename T, int W>
+__device__ __forceinline__ T lap_s(const T (*z)[W], int ex, int ey) {
+    T z0 = z[ey][ex];
+    T acc = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; i++) acc += T(2) * w9<T>(i) * (z[ey + CY[i]][ex + CX[i]] - z0);
+    return acc / cs2<T>();
+}
+
+// s_i(u) of Sec. 3.2.
+template <typename T>
+__device__ __forceinline__ T s_i(int i, T ux, T uy) {
+    T cu = T(CX[i]) * ux + T(CY[i]) * uy;
+    T uu = ux * ux + uy * uy;
+    return w9<T>(i) * (cu / cs2<T>() + cu * cu / (T(2) * cs2<T>() * cs2<T>()) - uu / (T(2) * cs2<T>()));
+}
+
+template <typename T>
+__device__ __forceinline__ int wrapx(int x, int nx) {
+    return x < 0 ? x + nx : (x >= nx ? x - nx : x);
+}
+
+// ---------------------------------------------------------------------------
+// The fused step (rows a1-a9) for one 32 x BY tile.
+// ---------------------------------------------------------------------------
+template <typename T, int BY>
+struct TileSmem {
+    T psi[BY + 2][34];
+    T rho[BY + 2][34];
+    T eps[BY + 2][34];
+    T phi[BY + 2][34];
+    T p[BY + 2][34];
+    T S[BY + 2][34];
+};
+
+template <typename S, typename T, typename A>
+struct StepIO {
+    const S *fhg_in;
+    S *fhg_out;
+    const S *l_in;
+    S *l_out;
+    const A *aux_in;
+    A *aux_out;
+    A *sigma;
+    int nx, ny, pitch, write_sigma;
+    long long plane;
+};
+
+template <typename S, typename T, typename A>
+__device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, int lcur, int write_sigma) {
+    StepIO<S, T, A> io;
+    io.fhg_in = reinterpret_cast<const S *>(s.pop[cur]);
+    io.fhg_out = reinterpret_cast<S *>(s.pop[1 - cur]);
+    io.l_in = reinterpret_cast<const S *>(s.pop[lcur]) + (long long)NFHG * s.plane;
+    io.l_out = reinterpret_cast<S *>(s.pop[1 - lcur]) + (long long)NFHG * s.plane;
+    io.aux_in = reinterpret_cast<const A *>(s.aux[cur]);
+    io.aux_out = reinterpret_cast<A *>(s.aux[1 - cur]);
+    io.sigma = reinterpret_cast<A *>(s.sigma);
+    io.nx = s.nx;
+    io.ny = s.ny;
+    io.pitch = s.pitch;
+    io.write_sigma = write_sigma;
+    io.plane = s.plane;
+    return io;
+}
+
+// Halo/own macro evaluation of one cell into shared memory.
+template <typename S, typename T, typename A, int BY>
+__device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Consts<T> &c,
+                                             const Shift &sh, TileSmem<T, BY> &sm, int ex, int ey,
+                                             int x, int y) {
+    const long long P = io.plane;
+    const long long k = (long long)y * io.pitch + x;
+    Refs<T> rf;
+    make_refs<S, T>(rf, sh, c, y, io.ny);
+    const float fi = 1.0f / sh.f_scale, gi = 1.0f / sh.g_scale, li = 1.0f / sh.l_scale;
+    T f[9], g[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        f[i] = Pol<S, T>::ld(io.fhg_in + i * P + k, rf.f[i], fi);
+        g[i] = Pol<S, T>::ld(io.fhg_in + (18 + i) * P + k, rf.g[i], gi);
+    }
+    T l1234 = T(0);
+#pragma unroll
+    for (int i = 1; i < 5; i++) l1234 += Pol<S, T>::ld(io.l_in + i * P + k, rf.l[i], li);
+    Macro<T> m;
+    local_macros(f, g, l1234, T(io.aux_in[AUX_FS * P + k]), T(io.aux_in[AUX_MDOT * P + k]),
+                 T(io.aux_in[AUX_Q * P + k]), c, m);
+    sm.psi[ey][ex] = m.psi;
+    sm.rho[ey][ex] = m.rho;
+    sm.eps[ey][ex] = m.eps;
+    sm.phi[ey][ex] = m.phi;
+    sm.p[ey][ex] = T(io.aux_in[AUX_P * P + k]);
+    sm.S[ey][ex] = T(io.aux_in[AUX_S * P + k]);
+}
+
+template <typename S, typename T, typename A, int BY>
+__device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Consts<T> &c,
+                                          const Shift &sh, TileSmem<T, BY> &sm, int x0, int y0) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    const int nx = io.nx, ny = io.ny;
+    const long long P = io.plane;
+
+    // ---- phase 1: own cell (kept in registers) -------------------------
+    const int xg = x0 + tx, y = y0 + ty;
+    const bool own = (xg < nx) && (y < ny);
+    const int x = xg < nx ? xg : xg % nx;       // wrapped slot of a ragged tile
+    const long long k = (long long)y * io.pitch + x;
+    Refs<T> rf;
+    T f[9], g[9], l[5];
+    Macro<T> m;
+    T fs_prev = T(0), mdot_prev = T(0), Q_prev = T(0), pux_prev = T(0), puy_prev = T(0);
+    const float fsc = 1.0f / sh.f_scale, gsc = 1.0f / sh.g_scale, lsc = 1.0f / sh.l_scale;
+    const float hsc = 1.0f / sh.h_scale;
+    if (y < ny) {
+        make_refs<S, T>(rf, sh, c, y, ny);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            f[i] = Pol<S, T>::ld(io.fhg_in + i * P + k, rf.f[i], fsc);
+            g[i] = Pol<S, T>::ld(io.fhg_in + (18 + i) * P + k, rf.g[i], gsc);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(io.l_in + i * P + k, rf.l[i], lsc);
+        fs_prev = T(io.aux_in[AUX_FS * P + k]);
+        mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
+        Q_prev = T(io.aux_in[AUX_Q * P + k]);
+        T l1234 = T(0);
+#pragma unroll
+        for (int i = 1; i < 5; i++) l1234 += l[i];
+        local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
+        sm.psi[ty + 1][tx + 1] = m.psi;
+        sm.rho[ty + 1][tx + 1] = m.rho;
+        sm.eps[ty + 1][tx + 1] = m.eps;
+        sm.phi[ty + 1][tx + 1] = m.phi;
+        sm.p[ty + 1][tx + 1] = T(io.aux_in[AUX_P * P + k]);
+        sm.S[ty + 1][tx + 1] = T(io.aux_in[AUX_S * P + k]);
+    }
+
+    // ---- phase 1: halo ring, recomputed from the neighbours' populations
+    constexpr int NRING = 2 * 34 + 2 * BY;
+    for (int r = tid; r < NRING; r += 32 * BY) {
+        int ex, ey;
+        if (r < 34) {
+            ex = r; ey = 0;
+        } else if (r < 68) {
+            ex = r - 34; ey = BY + 1;
+        } else if (r < 68 + BY) {
+            ex = 0; ey = r - 68 + 1;
+        } else {
+            ex = 33; ey = r - 68 - BY + 1;
+        }
+        const int hy = y0 - 1 + ey;
+        if (hy < 0 || hy >= ny) continue;
+        int hx = (x0 - 1 + ex) % nx;
+        if (hx < 0) hx += nx;
+        cell_to_smem<S, T, A, BY>(io, c, sh, sm, ex, ey, hx, hy);
+    }
+    __syncthreads();
+
+    // ---- wall ghost rows for the stencils (readings R17, R19) ----------
+    if (y0 == 0 && tid < 34) {              // bottom wall: wetting, copy, mirror
+        const T z = sm.psi[1][tid];
+        sm.psi[0][tid] = z + c.wet * z * (T(1) - z);
+        sm.rho[0][tid] = sm.rho[1][tid];
+        sm.eps[0][tid] = sm.eps[1][tid];
+        sm.phi[0][tid] = T(2) * c.phi_bot - sm.phi[1][tid];
+        sm.p[0][tid] = sm.p[1][tid];
+        sm.S[0][tid] = sm.S[1][tid];
+    }
+    const int et = ny - y0 + 1;              // ext row of y = ny, if inside the tile
+    if (et >= 1 && et <= BY + 1 && tid >= 64 && tid < 98) {
+        const int e = tid - 64;              // top wall: neutral wetting, copy, mirror
+        sm.psi[et][e] = sm.psi[et - 1][e];
+        sm.rho[et][e] = sm.rho[et - 1][e];
+        sm.eps[et][e] = sm.eps[et - 1][e];
+        sm.phi[et][e] = T(2) * c.phi_top - sm.phi[et - 1][e];
+        sm.p[et][e] = sm.p[et - 1][e];
+        sm.S[et][e] = sm.S[et - 1][e];
+    }
+    __syncthreads();
+    if (!own) return;
+
+    const int ex = tx + 1, ey = ty + 1;
+    // ---- a2: stencils ----------------------------------------------------
+    T gpsix, gpsiy, grhox, grhoy, gepsx, gepsy, gphix, gphiy, gpx, gpy, gSx, gSy;
+    grad_s<T, 34>(sm.psi, ex, ey, gpsix, gpsiy);
+    const T lpsi = lap_s<T, 34>(sm.psi, ex, ey);
+    grad_s<T, 34>(sm.rho, ex, ey, grhox, grhoy);
+    grad_s<T, 34>(sm.eps, ex, ey, gepsx, gepsy);
+    grad_s<T, 34>(sm.phi, ex, ey, gphix, gphiy);
+    const T lphi = lap_s<T, 34>(sm.phi, ex, ey);
+    grad_s<T, 34>(sm.p, ex, ey, gpx, gpy);
+    grad_s<T, 34>(sm.S, ex, ey, gSx, gSy);
+
+    // ---- a3: forces (Eq. Fs with the chemical potential of Sec. 2; Eq. Fe)
+    const T ps = m.psi;
+    const T muc = T(4) * c.beta * (ps - T(1)) * (ps - T(0)) * (ps - T(0.5)) - c.kappa * lpsi;
+    const T Fsx = muc * gpsix, Fsy = muc * gpsiy;
+    const T Ex = -gphix, Ey = -gphiy;
+    const T qv = -(gepsx * gphix + gepsy * gphiy + m.eps * lphi);
+    const T E2 = Ex * Ex + Ey * Ey;
+    const T Fex = qv * Ex - T(0.5) * E2 * gepsx;
+    const T Fey = qv * Ey - T(0.5) * E2 * gepsy;
+    const T Fx = Fsx + Fex, Fy = Fsy + Fey;
+
+    // ---- a4: flow macros (Sec. 3.2) ---------------------------------------
+    T h[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.fhg_in + (9 + i) * P + k, T(0), hsc);
+    T jx = T(0), jy = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        jx += T(CX[i]) * h[i];
+        jy += T(CY[i]) * h[i];
+    }
+    const T r = m.rho;
+    const T mu = chi(m.fs, ps, c.mu), kth = chi(m.fs, ps, c.kth);
+    const T sig = chi(m.fs, ps, c.sig), cp = chi(m.fs, ps, c.cp);
+    const T mdot = c.one_m_rsl * (m.fs - fs_prev);                 // Eq. (ns1)
+    const T usx = (jx + T(0.5) * Fx) / r, usy = (jy + T(0.5) * Fy) / r;
+    const T fx = m.fs * (T(0) - usx), fy = m.fs * (T(0) - usy);    // u_s = 0
+    const T ux = usx + T(0.5) * fx, uy = usy + T(0.5) * fy;        // Eq. (Computed_u)
+    const T rfx = r * fx, rfy = r * fy;
+    const T Sn = r * mdot + (ux * grhox + uy * grhoy);
+    const T Ftx = Fx - gpx + cs2<T>() * grhox + cs2<T>() * gSx;
+    const T Fty = Fy - gpy + cs2<T>() * grhoy + cs2<T>() * gSy;
+    const T uF = ux * Ftx + uy * Fty;
+    const T R0 = w9<T>(0) * (Sn - uF / cs2<T>());
+    const T tau_h = mu / r / cs2<T>() + T(0.5);
+    T sh_ = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; i++) sh_ += h[i];
+    const T p = cs2<T>() / (T(1) - w9<T>(0)) * (sh_ + T(0.5) * Sn + tau_h * R0 + r * s_i<T>(0, ux, uy));
+
+    // ---- collisions + push streaming (a5-a9) -------------------------------
+    const int xl = x;                         // own column
+    const bool bot = (y == 0), top = (y == ny - 1);
+    auto dest = [&](int i, int cxv, int cyv) -> long long {
+        return (long long)(y + cyv) * io.pitch + wrapx<T>(xl + cxv, nx);
+    };
+    Refs<T> ro;                               // destination references (half storage)
+
+    // a7: flow
+    {
+        const T pre = T(1) - T(1) / (T(2) * tau_h);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const T cu = T(CX[i]) * ux + T(CY[i]) * uy;
+            const T cF = T(CX[i]) * Ftx + T(CY[i]) * Fty;
+            const T Ri = w9<T>(i) * (Sn + (T(CX[i]) * (Fx + rfx) + T(CY[i]) * (Fy + rfy)) / cs2<T>() +
+                                     (cu * cF - cs2<T>() * uF) / (cs2<T>() * cs2<T>()));
+            const T heq = ((i == 0) ? p / cs2<T>() * (w9<T>(0) - T(1)) : p / cs2<T>() * w9<T>(i)) +
+                          r * s_i<T>(i, ux, uy);
+            const T post = h[i] - (h[i] - heq) / tau_h + pre * Ri;
+            const int yt = y + CY[i];
+            if (yt < 0 || yt >= ny)
+                Pol<S, T>::st(io.fhg_out + (9 + OPP9[i]) * P + k, post, T(0), sh.h_scale);
+            else
+                Pol<S, T>::st(io.fhg_out + (9 + i) * P + dest(i, CX[i], CY[i]), post, T(0), sh.h_scale);
+        }
+    }
+    // a5: phase field
+    {
+        const T pux = ps * ux, puy = ps * uy;
+        const T dtx = pux - T(io.aux_in[AUX_PUX * P + k]);
+        const T dty = puy - T(io.aux_in[AUX_PUY * P + k]);
+        pux_prev = pux;
+        puy_prev = puy;
+        const T gn = sqrt(gpsix * gpsix + gpsiy * gpsiy);
+        T nxv = T(0), nyv = T(0);
+        if (!(gn < T(1e-12))) {
+            nxv = gpsix / gn;
+            nyv = gpsiy / gn;
+        }
+        const T lam = T(4) * ps * (T(1) - ps) / c.W;
+        const T inv = T(1) / c.tau_f;
+        const T pre = T(1) - T(1) / (T(2) * c.tau_f);
+        (void)inv;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const T cu = T(CX[i]) * ux + T(CY[i]) * uy;
+            const T feq = w9<T>(i) * ps * (T(1) + cu / cs2<T>());
+            const T ax = dtx + cs2<T>() * lam * nxv;
+            const T ay = dty + cs2<T>() * lam * nyv;
+            const T Fi = w9<T>(i) * (T(CX[i]) * ax + T(CY[i]) * ay) / cs2<T>() + w9<T>(i) * ps * mdot;
+            const T post = f[i] - (f[i] - feq) / c.tau_f + pre * Fi;
+            const int yt = y + CY[i];
+            if (yt < 0 || yt >= ny) {
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+                Pol<S, T>::st(io.fhg_out + OPP9[i] * P + k, post, ro.f[OPP9[i]], sh.f_scale);
+            } else {
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
+                Pol<S, T>::st(io.fhg_out + i * P + dest(i, CX[i], CY[i]), post, ro.f[i], sh.f_scale);
+            }
+        }
+    }
+    // a8: enthalpy (Sec. 3.3)
+    T Qn;
+    {
+        const T tau_g = kth / (r * c.Cref * cs2<T>()) + T(0.5);
+        Qn = r * cp * m.T_ * mdot;
+        const T uu = ux * ux + uy * uy;
+        const T pre = T(1) - T(1) / (T(2) * tau_g);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const T cu = T(CX[i]) * ux + T(CY[i]) * uy;
+            T geq;
+            if (i == 0)
+                geq = m.H - c.Cref * m.T_ + w9<T>(0) * cp * m.T_ * (c.Cref / cp - uu / (T(2) * cs2<T>()));
+            else
+                geq = w9<T>(i) * cp * m.T_ *
+                      (c.Cref / cp + cu / cs2<T>() + (cu * cu - cs2<T>() * uu) / (T(2) * cs2<T>() * cs2<T>()));
+            const T post = g[i] - (g[i] - geq) / tau_g + pre * (w9<T>(i) * Qn);
+            const int yt = y + CY[i];
+            if (yt < 0) {            // cold wall: anti-bounce-back to C_p,ref T_w
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+                Pol<S, T>::st(io.fhg_out + (18 + OPP9[i]) * P + k,
+                              -post + T(2) * w9<T>(i) * c.Cref_Tw, ro.g[OPP9[i]], sh.g_scale);
+            } else if (yt >= ny) {   // top wall: adiabatic bounce-back
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+                Pol<S, T>::st(io.fhg_out + (18 + OPP9[i]) * P + k, post, ro.g[OPP9[i]], sh.g_scale);
+            } else {
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
+                Pol<S, T>::st(io.fhg_out + (18 + i) * P + dest(i, CX[i], CY[i]), post, ro.g[i], sh.g_scale);
+            }
+        }
+    }
+    // a6: potential (Sec. 3.4), one sweep inside the fused step
+    {
+        const T tau_l = sig / cs2<T>() + T(0.5);
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            const T leq = (i == 0) ? (w5<T>(0) - T(1)) * m.phi : w5<T>(i) * m.phi;
+            const T post = l[i] - (l[i] - leq) / tau_l;
+            const int yt = y + CY5[i];
+            if (yt < 0 || yt >= ny) {   // electrodes: anti-bounce-back
+                const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+                Pol<S, T>::st(io.l_out + OPP5[i] * P + k, -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]],
+                              sh.l_scale);
+            } else {
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
+                Pol<S, T>::st(io.l_out + i * P + (long long)yt * io.pitch + wrapx<T>(xl + CX5[i], nx), post,
+                              ro.l[i], sh.l_scale);
+            }
+        }
+    }
+    (void)bot;
+    (void)top;
+    // previous-step fields for the next step
+    io.aux_out[AUX_FS * P + k] = A(m.fs);
+    io.aux_out[AUX_MDOT * P + k] = A(mdot);
+    io.aux_out[AUX_Q * P + k] = A(Qn);
+    io.aux_out[AUX_PUX * P + k] = A(pux_prev);
+    io.aux_out[AUX_PUY * P + k] = A(puy_prev);
+    io.aux_out[AUX_P * P + k] = A(p);
+    io.aux_out[AUX_S * P + k] = A(Sn);
+    if (io.write_sigma) io.sigma[k] = A(sig);
+}
+
+template <typename S, typename T, typename A, int BY>
+__global__ void __launch_bounds__(32 * BY) k_step(DevState s, int cur, int lcur, int write_sigma,
+                                                  Consts<T> c, Shift sh) {
+    __shared__ TileSmem<T, BY> sm;
+    const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
+    step_tile<S, T, A, BY>(io, c, sh, sm, blockIdx.x * 32, blockIdx.y * BY);
+}
+
+// Batched form: blocks walk a flat list of tiles of many instances.  The
+// parities of every member flip together, so the list keeps each member's
+// parity at the start and the launch passes the flips since then.
+template <bool SWEEP>
+__device__ __forceinline__ int find_item(const BatchItem *__restrict__ items, int n_items, int t) {
+    int lo = 0, hi = n_items - 1;      // last item whose first tile is <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int b = SWEEP ? items[mid].sweep_begin : items[mid].tile_begin;
+        if (b <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename S, typename T, typename A, int BY>
+__global__ void __launch_bounds__(32 * BY) k_batch_step(const BatchItem *__restrict__ items,
+                                                        const Consts<T> *__restrict__ consts,
+                                                        int n_items, int total_tiles, int flip_cur,
+                                                        int flip_l) {
+    __shared__ TileSmem<T, BY> sm;
+    __shared__ int s_item;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) s_item = find_item<false>(items, n_items, t);
+        __syncthreads();
+        const BatchItem &it = items[s_item];
+        const int local = t - it.tile_begin;
+        const int bx = local % it.tiles_x, by = local / it.tiles_x;
+        const StepIO<S, T, A> io = make_io<S, T, A>(it.s, it.cur ^ flip_cur, it.lcur ^ flip_l, it.write_sigma);
+        step_tile<S, T, A, BY>(io, consts[s_item], it.sh, sm, bx * 32, by * BY);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Extra potential sweeps (k_e > 1 and the pre-solve): D2Q5 collide with sigma
+// frozen at time n, push-stream, anti-bounce-back at the electrodes.
+// ---------------------------------------------------------------------------
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void sweep_cell(const S *l_in, S *l_out, const A *sigma, int nx, int ny,
+                                           int pitch, long long P, const Consts<T> &c, const Shift &sh,
+                                           int x, int y) {
+    const long long k = (long long)y * pitch + x;
+    Refs<T> rf, ro;
+    make_refs<S, T>(rf, sh, c, y, ny);
+    const float lsc = 1.0f / sh.l_scale;
+    T l[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(l_in + i * P + k, rf.l[i], lsc);
+    T sl = T(0);
+#pragma unroll
+    for (int i = 1; i < 5; i++) sl += l[i];
+    const T phi = sl / (T(1) - w5<T>(0));
+    const T tau_l = T(sigma[k]) / cs2<T>() + T(0.5);
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const T leq = (i == 0) ? (w5<T>(0) - T(1)) * phi : w5<T>(i) * phi;
+        const T post = l[i] - (l[i] - leq) / tau_l;
+        const int yt = y + CY5[i];
+        if (yt < 0 || yt >= ny) {
+            const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
+            if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+            Pol<S, T>::st(l_out + OPP5[i] * P + k, -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]], sh.l_scale);
+        } else {
+            if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
+            Pol<S, T>::st(l_out + i * P + (long long)yt * pitch + wrapx<T>(x + CX5[i], nx), post, ro.l[i],
+                          sh.l_scale);
+        }
+    }
+}
+
+template <typename S, typename T, typename A>
+__global__ void k_sweep(DevState s, int lcur, Consts<T> c, Shift sh) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= s.nx || y >= s.ny) return;
+    const S *l_in = reinterpret_cast<const S *>(s.pop[lcur]) + (long long)NFHG * s.plane;
+    S *l_out = reinterpret_cast<S *>(s.pop[1 - lcur]) + (long long)NFHG * s.plane;
+    sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(s.sigma), s.nx, s.ny, s.pitch, s.plane, c,
+                        sh, x, y);
+}
+
+// Batched potential sweep over the same work list (32 x 8 cells per tile).
+template <typename S, typename T, typename A>
+__global__ void __launch_bounds__(256) k_batch_sweep(const BatchItem *__restrict__ items,
+                                                     const Consts<T> *__restrict__ consts, int n_items,
+                                                     int total_tiles, int flip_l) {
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const int ii = find_item<true>(items, n_items, t);
+        const BatchItem &it = items[ii];
+        const int local = t - it.sweep_begin;
+        const int x = (local % it.sweep_tiles_x) * 32 + threadIdx.x;
+        const int y = (local / it.sweep_tiles_x) * 8 + threadIdx.y;
+        if (x < it.s.nx && y < it.s.ny) {
+            const int lc = it.lcur ^ flip_l;
+            const S *l_in = reinterpret_cast<const S *>(it.s.pop[lc]) + (long long)NFHG * it.s.plane;
+            S *l_out = reinterpret_cast<S *>(it.s.pop[1 - lc]) + (long long)NFHG * it.s.plane;
+            sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(it.s.sigma), it.s.nx, it.s.ny,
+                                it.s.pitch, it.s.plane, consts[ii], it.sh, x, y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state (Sec. 2): equilibria of a resting droplet at T_init with all
+// latent heat held, linear potential between the electrodes.
+// ---------------------------------------------------------------------------
+template <typename S, typename T, typename A>
+__global__ void k_init(DevState s, const double *psi_dev, double R, double xc, double yc, double W,
+                       Consts<T> c, Shift sh) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= s.nx || y >= s.ny) return;
+    const long long P = s.plane, k = (long long)y * s.pitch + x;
+    double psd;
+    if (psi_dev) {
+        psd = psi_dev[(long long)y * s.nx + x];
+    } else {
+        const double dx = x - xc, dy = y - yc;
+        const double rr = sqrt(dx * dx + dy * dy);
+        psd = 0.5 + 0.5 * tanh(2.0 * (R - rr) / W);
+    }
+    const T ps = T(psd);
+    const T cpm = chi(T(0), ps, c.cp);
+    const T T0 = c.T_init;
+    const T H0 = cpm * T0 + ps * c.L;
+    const T phi0 = c.phi_bot + (c.phi_top - c.phi_bot) * (T(y) + T(0.5)) / T(s.ny);
+    const T rho0 = chi(T(0), ps, c.rho);
+    Refs<T> rf;
+    make_refs<S, T>(rf, sh, c, y, s.ny);
+    S *pop = reinterpret_cast<S *>(s.pop[0]);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const T feq = w9<T>(i) * ps * (T(1) + T(0) / cs2<T>());
+        const T pre = (i == 0) ? T(0) / cs2<T>() * (w9<T>(0) - T(1)) : T(0) / cs2<T>() * w9<T>(i);
+        const T heq = pre + rho0 * s_i<T>(i, T(0), T(0));
+        T geq;
+        if (i == 0)
+            geq = H0 - c.Cref * T0 + w9<T>(0) * cpm * T0 * (c.Cref / cpm - T(0) / (T(2) * cs2<T>()));
+        else
+            geq = w9<T>(i) * cpm * T0 * (c.Cref / cpm + T(0) / cs2<T>() + (T(0) - T(0)) / (T(2) * cs2<T>() * cs2<T>()));
+        Pol<S, T>::st(pop + i * P + k, feq, rf.f[i], sh.f_scale);
+        Pol<S, T>::st(pop + (9 + i) * P + k, heq, T(0), sh.h_scale);
+        Pol<S, T>::st(pop + (18 + i) * P + k, geq, rf.g[i], sh.g_scale);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const T leq = (i == 0) ? (w5<T>(0) - T(1)) * phi0 : w5<T>(i) * phi0;
+        Pol<S, T>::st(pop + (NFHG + i) * P + k, leq, rf.l[i], sh.l_scale);
+    }
+    A *aux = reinterpret_cast<A *>(s.aux[0]);
+#pragma unroll
+    for (int a = 0; a < NAUX; a++) aux[a * P + k] = A(0);
+    reinterpret_cast<A *>(s.sigma)[k] = A(chi(T(0), ps, c.sig));
+}
+
+// ---------------------------------------------------------------------------
+// Observables (row a10): FP64 reductions over the tile grid.  Each block
+// handles a 32 x 8 tile plus a one-cell halo (for q_v's stencils and the
+// interface crossings) and leaves block partial sums and order-independent
+// max/min candidates in the workspace; k_obs_final reduces them.
+// ---------------------------------------------------------------------------
+constexpr int OBS_BY = 8;
+
+static __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) {
+    atomicMax(a, (unsigned long long)__double_as_longlong(v));   // v >= 0: bits order like values
+}
+static __device__ __forceinline__ void atomic_min_pos(unsigned long long *a, double v) {
+    atomicMin(a, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void obs_macros(const S *fhg, const S *lb, const A *aux, long long P, long long k,
+                                           int y, int ny, const Consts<double> &c, const Shift &sh,
+                                           Macro<double> &m) {
+    Refs<T> rf;
+    Consts<T> ct;      // only phi_bot/phi_top/ny are used by make_refs
+    ct.phi_bot = T(c.phi_bot);
+    ct.phi_top = T(c.phi_top);
+    make_refs<S, T>(rf, sh, ct, y, ny);
+    double f[9], g[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        f[i] = double(Pol<S, T>::ld(fhg + i * P + k, rf.f[i], 1.0f / sh.f_scale));
+        g[i] = double(Pol<S, T>::ld(fhg + (18 + i) * P + k, rf.g[i], 1.0f / sh.g_scale));
+    }
+    double l1234 = 0.0;
+#pragma unroll
+    for (int i = 1; i < 5; i++) l1234 += double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
+    local_macros<double>(f, g, l1234, double(aux[AUX_FS * P + k]), double(aux[AUX_MDOT * P + k]),
+                         double(aux[AUX_Q * P + k]), c, m);
+}
+
+template <typename S, typename T, typename A>
+__global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<double> c, Shift sh,
+                                                    ObsScratch ws) {
+    __shared__ double s_psi[OBS_BY + 2][34], s_fs[OBS_BY + 2][34], s_eps[OBS_BY + 2][34], s_phi[OBS_BY + 2][34];
+    __shared__ double s_red[4][32 * OBS_BY / 32];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int nx = s.nx, ny = s.ny;
+    const long long P = s.plane;
+    const S *fhg = reinterpret_cast<const S *>(s.pop[cur]);
+    const S *lb = reinterpret_cast<const S *>(s.pop[lcur]) + (long long)NFHG * P;
+    const A *aux = reinterpret_cast<const A *>(s.aux[cur]);
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * OBS_BY;
+    // fill the extended tile (own + halo), ghost rows as in the step
+    for (int r = tid; r < 34 * (OBS_BY + 2); r += 32 * OBS_BY) {
+        const int ex = r % 34, ey = r / 34;
+        const int yy = y0 - 1 + ey;
+        if (yy < 0 || yy >= ny) continue;
+        int xx = (x0 - 1 + ex) % nx;
+        if (xx < 0) xx += nx;
+        Macro<double> m;
+        obs_macros<S, T, A>(fhg, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, m);
+        s_psi[ey][ex] = m.psi;
+        s_fs[ey][ex] = m.fs;
+        s_eps[ey][ex] = m.eps;
+        s_phi[ey][ex] = m.phi;
+    }
+    __syncthreads();
+    if (y0 == 0 && tid < 34) {
+        s_eps[0][tid] = s_eps[1][tid];
+        s_phi[0][tid] = 2.0 * c.phi_bot - s_phi[1][tid];
+    }
+    const int et = ny - y0 + 1;
+    if (et >= 1 && et <= OBS_BY + 1 && tid >= 64 && tid < 98) {
+        s_eps[et][tid - 64] = s_eps[et - 1][tid - 64];
+        s_phi[et][tid - 64] = 2.0 * c.phi_top - s_phi[et - 1][tid - 64];
+    }
+    __syncthreads();
+
+    const int x = x0 + tx, y = y0 + ty;
+    double v_psi = 0.0, v_H = 0.0, v_fs = 0.0, v_q = 0.0;
+    if (x < nx && y < ny) {
+        const int ex = tx + 1, ey = ty + 1;
+        Macro<double> m;
+        obs_macros<S, T, A>(fhg, lb, aux, P, (long long)y * s.pitch + x, y, ny, c, sh, m);
+        double gex, gey, gphx, gphy;
+        grad_s<double, 34>(s_eps, ex, ey, gex, gey);
+        grad_s<double, 34>(s_phi, ex, ey, gphx, gphy);
+        const double lphi = lap_s<double, 34>(s_phi, ex, ey);
+        v_q = -(gex * gphx + gey * gphy + m.eps * lphi);
+        v_psi = m.psi;
+        v_H = m.H;
+        v_fs = m.fs;
+        if (!isfinite(m.psi) || !isfinite(m.H)) atomicOr(ws.bad, 1u);
+        const double a = s_psi[ey][ex];
+        // column crossing (height): psi(y) >= 1/2 > psi(y+1)
+        if (a >= 0.5) {
+            atomicOr(&ws.rowany[y], 1u);
+            if (y == ny - 1) {
+                atomic_max_pos(&ws.maxv[0], (double)ny);
+            } else {
+                const double b = s_psi[ey + 1][ex];
+                if (b < 0.5) atomic_max_pos(&ws.maxv[0], y + (a - 0.5) / (a - b) + 0.5);
+            }
+            // row crossings (width): left edge needs x >= 1, right edge x <= nx - 2
+            if (x >= 1) {
+                const double bl = s_psi[ey][ex - 1];
+                if (bl < 0.5) {
+                    atomic_min_pos(&ws.minv[1 + y], (x - 1) + (0.5 - bl) / (a - bl));
+                    atomicOr(&ws.rowany[y], 2u);
+                }
+            }
+            if (x + 1 < nx) {
+                const double br = s_psi[ey][ex + 1];
+                if (br < 0.5) {
+                    atomic_max_pos(&ws.maxv[2 + y], x + (a - 0.5) / (a - br));
+                    atomicOr(&ws.rowany[y], 4u);
+                }
+            }
+        }
+        // freezing front on the centre column (lowest f_s = 1/2 crossing)
+        if (x == nx / 2) {
+            const double fa = s_fs[ey][ex];
+            if (y == 0 && fa >= 0.5) atomicOr(ws.bad + 1, 1u);
+            if (fa >= 0.5) {
+                if (y == ny - 1) {
+                    atomic_min_pos(&ws.minv[0], (double)ny);
+                } else {
+                    const double fb = s_fs[ey + 1][ex];
+                    if (fb < 0.5) atomic_min_pos(&ws.minv[0], y + (fa - 0.5) / (fa - fb) + 0.5);
+                }
+            }
+        }
+    }
+    // block sums (FP64, fixed shuffle order)
+    double v[4] = {v_psi, v_H, v_fs, v_q};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        double t = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (tx == 0) s_red[j][ty] = t;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double t = 0.0;
+        for (int w = 0; w < OBS_BY; w++) t += s_red[tid][w];
+        ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] = t;
+    }
+}
+
+// psi = 1/2 extent of row y: 0 without liquid, nx without a left or right
+// crossing (the row is liquid across the periodic seam), else right - left.
+static __device__ __forceinline__ double row_extent_of(const ObsScratch &ws, int y, int nx) {
+    const unsigned int bits = ws.rowany[y];
+    if (!(bits & 1u)) return 0.0;
+    if ((bits & 6u) != 6u) return (double)nx;
+    return __longlong_as_double((long long)ws.maxv[2 + y]) - __longlong_as_double((long long)ws.minv[1 + y]);
+}
+
+// Final reduction: one block of 256 threads.
+static __global__ void k_obs_final(int nx, int ny, ObsScratch ws, Scalars sc) {
+    __shared__ double s[4][256];
+    __shared__ double s_w[256];
+    const int t = threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = t; b < ws.nblocks; b += 256)
+        for (int j = 0; j < 4; j++) acc[j] += ws.partials[(long long)b * 4 + j];
+    for (int j = 0; j < 4; j++) s[j][t] = acc[j];
+    // widest row extent
+    double wmax = 0.0;
+    for (int y = t; y < ny; y += 256) {
+        const double w = row_extent_of(ws, y, nx);
+        wmax = fmax(wmax, w);
+    }
+    s_w[t] = wmax;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) {
+            for (int j = 0; j < 4; j++) s[j][t] += s[j][t + o];
+            s_w[t] = fmax(s_w[t], s_w[t + o]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        lbm_obs *o = ws.obs;
+        const double mass = s[0][0], enth = s[1][0], solid = s[2][0], charge = s[3][0];
+        o->step = sc.step;
+        o->Fo = sc.alpha_l * (double)sc.step / (sc.R0 * sc.R0);
+        o->mass = mass;
+        o->enthalpy = enth;
+        o->solid = solid;
+        o->charge = charge;
+        o->frozen_fraction = (mass != 0.0) ? solid / mass : 0.0;
+        o->height = __longlong_as_double((long long)ws.maxv[0]);
+        o->width = s_w[0];
+        o->aspect = (o->width > 0.0) ? o->height / o->width : 0.0;
+        o->R_tr = 0.5 * row_extent_of(ws, 0, nx);
+        if (ws.bad[1]) {
+            const unsigned long long fmin = ws.minv[0];
+            o->front = (fmin == ~0ull) ? (double)ny : __longlong_as_double((long long)fmin);
+        } else {
+            o->front = 0.0;
+        }
+        if (o->t_fre < 0 && o->frozen_fraction >= 0.99) o->t_fre = sc.step;
+        o->Fo_fre = (o->t_fre >= 0) ? sc.alpha_l * (double)o->t_fre / (sc.R0 * sc.R0) : -1.0;
+        o->status = ws.bad[0] ? LBM_ERR_DIVERGED : LBM_OK;
+        o->reserved = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Field access for tests and hand-over: stored planes <-> host doubles.
+// ---------------------------------------------------------------------------
+template <typename S, typename T, typename A>
+__global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c, Shift sh, double *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= s.nx || y >= s.ny) return;
+    const long long P = s.plane, k = (long long)y * s.pitch + x;
+    const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
+    const S *fhg = reinterpret_cast<const S *>(s.pop[cur]);
+    const S *lb = reinterpret_cast<const S *>(s.pop[lcur]) + (long long)NFHG * P;
+    const A *aux = reinterpret_cast<const A *>(s.aux[cur]);
+    Refs<T> rf;
+    Consts<T> ct;
+    ct.phi_bot = T(c.phi_bot);
+    ct.phi_top = T(c.phi_top);
+    make_refs<S, T>(rf, sh, ct, y, s.ny);
+    if (field == LBM_FIELD_F || field == LBM_FIELD_H || field == LBM_FIELD_G) {
+        const int base = field * 9;
+        for (int i = 0; i < 9; i++) {
+            const T ref = field == LBM_FIELD_F ? rf.f[i] : (field == LBM_FIELD_G ? rf.g[i] : T(0));
+            const float sc = field == LBM_FIELD_F ? sh.f_scale : (field == LBM_FIELD_G ? sh.g_scale : sh.h_scale);
+            out[i * N + o] = double(Pol<S, T>::ld(fhg + (base + i) * P + k, ref, 1.0f / sc));
+        }
+    } else if (field == LBM_FIELD_L) {
+        for (int i = 0; i < 5; i++) out[i * N + o] = double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
+    } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
+        out[o] = double(aux[(field - LBM_FIELD_FS_PREV) * P + k]);
+    } else if (field == LBM_FIELD_SIGMA) {
+        out[o] = double(reinterpret_cast<const A *>(s.sigma)[k]);
+    } else {
+        Macro<double> m;
+        obs_macros<S, T, A>(fhg, lb, aux, P, k, y, s.ny, c, sh, m);
+        out[o] = field == LBM_FIELD_PSI ? m.psi
+               : field == LBM_FIELD_FSOLID ? m.fs
+               : field == LBM_FIELD_T ? m.T_
+               : field == LBM_FIELD_PHI ? m.phi
+               : m.H;
+    }
+}
+
+template <typename S, typename T, typename A>
+__global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shift sh, const double *in) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= s.nx || y >= s.ny) return;
+    const long long P = s.plane, k = (long long)y * s.pitch + x;
+    const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
+    S *fhg = reinterpret_cast<S *>(s.pop[cur]);
+    S *lb = reinterpret_cast<S *>(s.pop[lcur]) + (long long)NFHG * P;
+    A *aux = reinterpret_cast<A *>(s.aux[cur]);
+    Refs<T> rf;
+    make_refs<S, T>(rf, sh, c, y, s.ny);
+    if (field == LBM_FIELD_F || field == LBM_FIELD_H || field == LBM_FIELD_G) {
+        const int base = field * 9;
+        for (int i = 0; i < 9; i++) {
+            const T ref = field == LBM_FIELD_F ? rf.f[i] : (field == LBM_FIELD_G ? rf.g[i] : T(0));
+            const float sc = field == LBM_FIELD_F ? sh.f_scale : (field == LBM_FIELD_G ? sh.g_scale : sh.h_scale);
+            Pol<S, T>::st(fhg + (base + i) * P + k, T(in[i * N + o]), ref, sc);
+        }
+    } else if (field == LBM_FIELD_L) {
+        for (int i = 0; i < 5; i++) Pol<S, T>::st(lb + i * P + k, T(in[i * N + o]), rf.l[i], sh.l_scale);
+    } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
+        aux[(field - LBM_FIELD_FS_PREV) * P + k] = A(in[o]);
+    } else if (field == LBM_FIELD_SIGMA) {
+        reinterpret_cast<A *>(s.sigma)[k] = A(in[o]);
+    }
+}
+
+}  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// Launchers for one (S, T, A) triple; SUFFIX names the precision.
+// ---------------------------------------------------------------------------
+#define LBM_DEFINE_LAUNCHERS(SUFFIX, S, T, A)                                                              \
+    namespace lbm {                                                                                         \
+    cudaError_t launch_step_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,                 \
+                                     const void *consts, const Shift &sh, int tile_rows, cudaStream_t st) { \
+        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
+        dim3 grid((s.nx + 31) / 32, (s.ny + tile_rows - 1) / tile_rows);                                   \
+        switch (tile_rows) {                                                                                \
+        case 4: k_step<S, T, A, 4><<<grid, dim3(32, 4), 0, st>>>(s, cur, lcur, write_sigma, c, sh); break; \
+        case 8: k_step<S, T, A, 8><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, write_sigma, c, sh); break; \
+        case 16: k_step<S, T, A, 16><<<grid, dim3(32, 16), 0, st>>>(s, cur, lcur, write_sigma, c, sh); break; \
+        default: return cudaErrorInvalidValue;                                                              \
+        }                                                                                                   \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, const void *consts, const Shift &sh,    \
+                                      cudaStream_t st) {                                                    \
+        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
+        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
+        k_sweep<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, lcur, c, sh);                                     \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    cudaError_t launch_init_##SUFFIX(const DevState &s, const double *psi_dev, double R, double xc,        \
+                                     double yc, const void *consts, const Shift &sh, cudaStream_t st) {    \
+        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
+        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
+        k_init<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, psi_dev, R, xc, yc, double(c.W), c, sh);           \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    cudaError_t launch_obs_##SUFFIX(const DevState &s, int cur, int lcur, const void *consts,              \
+                                    const Shift &sh, const ObsScratch &ws, const Scalars &sc,               \
+                                    cudaStream_t st) {                                                      \
+        const Consts<double> &c = *reinterpret_cast<const Consts<double> *>(consts);                      \
+        dim3 grid((s.nx + 31) / 32, (s.ny + OBS_BY - 1) / OBS_BY);                                          \
+        k_obs<S, T, A><<<grid, dim3(32, OBS_BY), 0, st>>>(s, cur, lcur, c, sh, ws);                         \
+        k_obs_final<<<1, 256, 0, st>>>(s.nx, s.ny, ws, sc);                                                 \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    cudaError_t launch_get_##SUFFIX(const DevState &s, int cur, int lcur, int field, const void *consts,   \
+                                    const Shift &sh, double *out, cudaStream_t st) {                        \
+        const Consts<double> &c = *reinterpret_cast<const Consts<double> *>(consts);                      \
+        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
+        k_get<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, field, c, sh, out);                      \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    cudaError_t launch_set_##SUFFIX(const DevState &s, int cur, int lcur, int field, const void *consts,   \
+                                    const Shift &sh, const double *in, cudaStream_t st) {                   \
+        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
+        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
+        k_set<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, field, c, sh, in);                       \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    }

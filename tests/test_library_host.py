@@ -1,0 +1,76 @@
+"""Host-side checks of the GPU library that need no GPU: it builds, loads,
+exports every entry point the header declares, rejects bad parameters
+before touching a device, and keeps the oracle out of the product path."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2410_06657_gb300 import lbm, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point():
+    L = lbm.load()
+    declared = header_functions()
+    assert declared, "no declarations found"
+    assert sorted(lbm.EXPORTS) == declared
+    out = subprocess.run(["nm", "-D", "--defined-only", lbm.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (lbm_\w+)", out))
+    for name in declared:
+        assert name in exported, name
+        assert hasattr(L, name)
+
+
+def test_struct_layouts_match_the_header():
+    # lbm_params: 4 int32 then 24 doubles; lbm_obs: 15 eight-byte slots
+    assert C.sizeof(lbm.Params) == 4 * 4 + 24 * 8
+    assert C.sizeof(lbm.Obs) == 15 * 8
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    body = src[src.index("typedef struct lbm_params"):src.index("} lbm_params;")]
+    names = re.findall(r"\b(?:int32_t|double)\s+([^;]+);", body)
+    fields = [n.strip() for group in names for n in group.split(",")]
+    assert fields == [f for f, _ in lbm.Params._fields_]
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(k_e=0), dict(precision=7),
+                                 dict(theta_deg=180.0), dict(theta_deg=0.0), dict(M=0.0),
+                                 dict(mu_l=-1.0), dict(Ste=0.0), dict(sigma_g=0.0),
+                                 dict(T_w=1.0), dict(W=float("nan"))])
+def test_create_rejects_bad_parameters_without_a_device(bad):
+    L = lbm.load()
+    p = lbm.make_params(W.params(**bad))
+    h = C.c_void_p()
+    rc = L.lbm_create(C.byref(p), None, C.byref(h))
+    assert rc == lbm.ERR_BADPARAM
+    assert not h.value
+    assert L.lbm_last_error()
+
+
+def test_calls_on_null_handles_fail_cleanly():
+    L = lbm.load()
+    assert L.lbm_step(None, 1) == lbm.ERR_BADPARAM
+    assert L.lbm_init_droplet(None, 5.0, 1.0, 1.0, 0) == lbm.ERR_BADPARAM
+    assert L.lbm_observables(None, None) == lbm.ERR_BADPARAM
+    assert L.lbm_batch_create(None, 0, None, 0, None) == lbm.ERR_BADPARAM
+    L.lbm_destroy(None)
+
+
+def test_product_path_never_uses_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2410_06657_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", text, re.M), f
+                assert "lbm_oracle" not in text, f
