@@ -16,8 +16,13 @@
  * (each one is cited again where it is used):
  *   R1  All four systems collide with time-n macroscopic fields (a Jacobi
  *       split of Algorithm 1's sequence); then all stream; then boundaries.
- *   R2  n = grad(psi)/|grad(psi)| and kappa*lap(psi) (Sec. 2 prints phi);
- *       n = 0 where |grad(psi)| < 1e-12.
+ *   R2  n = grad(psi)/|grad(psi)| and kappa*lap(psi) (Sec. 2 prints phi).
+ *       Sec. 2 leaves n undefined where grad(psi) vanishes; the normal is
+ *       regularised as grad(psi) / (|grad(psi)| + 1e-4).  Without it, cells
+ *       whose psi sits slightly off 0 or 1 (lambda = 4 psi (1 - psi)/W not
+ *       small) but whose gradient is at round-off level get a counter-flux
+ *       M lambda n of fixed size in a direction set by round-off, which
+ *       amplifies last-bit differences by ~1e8 within 200 steps.
  *   R5  H_s = C_p T_m, T_s = T_l = T_m (pure substance).
  *   R6  Latent heat is carried by the liquid only: L_eff = psi L,
  *       f_l = clamp((H - H_s)/L_eff, 0, 1) (f_l = 1 where L_eff < 1e-12),
@@ -582,8 +587,7 @@ static void one_step(orc_state *s)
             double pux = ps * ux, puy = ps * uy;
             double dtx = pux - s->psiux_prev[k], dty = puy - s->psiuy_prev[k];
             double gn = sqrt(gpsix * gpsix + gpsiy * gpsiy);
-            double nxv = 0.0, nyv = 0.0;
-            if (!(gn < 1e-12)) { nxv = gpsix / gn; nyv = gpsiy / gn; }      /* R2 */
+            double nxv = gpsix / (gn + 1e-4), nyv = gpsiy / (gn + 1e-4);    /* R2 */
             double lam = 4.0 * ps * (1.0 - ps) / s->P.W;
             for (int i = 0; i < 9; i++) {
                 double fi = s->f[i * N + k];

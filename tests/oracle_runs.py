@@ -114,7 +114,24 @@ def mass_conservation(steps=1000):
     return dict(m0=m0, m1=ob["mass"], solid=ob["solid"])
 
 
+def sensitivity(steps=500):
+    """Two 128 x 64 sessile runs whose initial f differ by 1e-15 relative."""
+    W = _W()
+    w = W.plain_fp64_small()
+    p = w["params"]
+    a, b = _oracle().Oracle(p), _oracle().Oracle(p)
+    xc, yc = W.sessile_center(128, 20.0, 90.0)
+    a.init_droplet(20.0, xc, yc, 0)
+    b.init_droplet(20.0, xc, yc, 0)
+    f = b.get("f")
+    b.set("f", f * (1 + 1e-15 * W.noise(f.shape, 3)))
+    a.step(steps)
+    b.step(steps)
+    return dict(steps=steps, dpsi=float(np.abs(a.get("psi") - b.get("psi")).max()))
+
+
 JOBS = {
+    "sensitivity": (sensitivity, ()),
     "laplace_10": (laplace, (10.0,)),
     "laplace_14": (laplace, (14.0,)),
     "laplace_18": (laplace, (18.0,)),
@@ -143,7 +160,7 @@ def run_all(processes=None):
     ctx = mp.get_context("spawn")
     procs = processes or min(len(JOBS), max(1, os.cpu_count() or 1))
     # longest jobs first so the pool drains evenly
-    order = ["deform_5_2", "deform_2_5", "laplace_10", "laplace_14", "laplace_18",
+    order = ["deform_5_2", "deform_2_5", "sensitivity", "laplace_10", "laplace_14", "laplace_18",
              "laplace_14_W5", "angle_60", "angle_90", "angle_120", "front_paper",
              "mass", "stefan", "volume_0.9", "volume_1.1"]
     with ctx.Pool(procs) as pool:
