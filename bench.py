@@ -1,0 +1,378 @@
+"""Benchmark of the fused electrofreezing LB step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                [--precision f32|f64|f16s] [--workload production|precision]
+
+A step is one pass of the whole hot path over the lattice: the fused
+collide-and-stream launch (local macros, stencils, forces, four collisions,
+streaming with walls) and, every `--obs-every` steps, the FP64 observables
+reduction.  The default workload is the production sessile droplet:
+512 x 256 lattice, R = 80, theta = 90, CaE = 0.2, S = 2, R_sigma = 5,
+Ste = 0.5, rho_s/rho_l = 0.9, FP32.  The lattice state (about 45 MB) fits in
+L2, so L2 is flushed (a 256 MB write) before every timed step, outside the
+timed events.  Under torchrun each rank advances its own instance (replicas,
+no collective on the data path) and the slowest rank's time counts.
+
+--impl reference times the FP64 CPU oracle on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_LU = {"f64": 2 * (32 + 7) * 8, "f32": 2 * (32 + 7) * 4, "f16s": 2 * 32 * 2 + 2 * 7 * 4}
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_MD = os.path.join(ROOT, "profiles", "k_step_f32_production_512x256.md")
+KERNEL_SOURCES = ["lbm_kernels.cuh", "step_f32.cu", "lbm_internal.h"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2410_06657_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(precision: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    if precision != "f32" or not os.path.exists(PROFILE_MD):
+        return None
+    text = open(PROFILE_MD).read()
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m_b or not m_h or m_h.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while a region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(name: str, precision: str):
+    from paper_2410_06657_gb300 import workloads as W
+    prec = W.PRECISIONS[precision]
+    if name == "production":
+        w = W.production(precision=prec)
+        label = "production sessile droplet 512x256, R=80, theta=90, CaE=0.2, S=2, R_sigma=5, Ste=0.5"
+    elif name == "precision":
+        w = W.precision_case(precision=prec)
+        label = "precision case 1024x512, R=160, theta=60, PR+ (R_sigma=2, S=0.5), CaE=0.2"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return w, label
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reported baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_mlups(params: dict, R: float, budget_s: float, max_steps=None):
+    """Time the FP64 oracle, as it stands, on this workload's lattice: steps
+    from the initial droplet until `budget_s` of CPU work (at least 2)."""
+    import oracle
+    from paper_2410_06657_gb300 import workloads as W
+    o = oracle.Oracle(params)
+    xc, yc = W.sessile_center(params["nx"], R, params["theta_deg"])
+    o.init_droplet(R, xc, yc, 0)
+    o.step(1)                      # warm the caches and pages
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if (n >= 2 and el >= budget_s) or (max_steps and n >= max_steps):
+            break
+    cells = params["nx"] * params["ny"]
+    return cells * n / el / 1e6, n, el
+
+
+def run_reference(args, world, rank):
+    from paper_2410_06657_gb300 import workloads as W
+    if rank != 0:
+        return
+    w, label = workload(args.workload, args.precision)
+    p = dict(w["params"])
+    cells = p["nx"] * p["ny"]
+    # one oracle step of the full lattice takes ~0.1-0.3 s; when K + W steps
+    # would not fit in about two minutes, each step runs on a 128 x 64 sample
+    # lattice with the same physics (the oracle's cost per cell is the same)
+    import oracle
+    probe = oracle.Oracle(p)
+    xc, yc = W.sessile_center(p["nx"], w["R"], p["theta_deg"])
+    probe.init_droplet(w["R"], xc, yc, 0)
+    t0 = time.perf_counter()
+    probe.step(1)
+    per_step = time.perf_counter() - t0
+    probe.close()
+    sample = f"full {p['nx']}x{p['ny']} lattice"
+    R = w["R"]
+    if per_step * (args.steps + args.warmup) > 120.0:
+        scale = p["ny"] / 64.0
+        R = w["R"] / scale
+        p.update(nx=128, ny=64, R0=R)
+        sample = f"128x64 sample lattice, same physics (R={R:g}); full lattice step {per_step:.3f} s"
+        cells = 128 * 64
+    o = oracle.Oracle(p)
+    xc, yc = W.sessile_center(p["nx"], R, p["theta_deg"])
+    o.init_droplet(R, xc, yc, 0)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    v = cells * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": label},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} FP64 oracle steps on the {sample}, 1 thread"},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2410_06657_gb300 import lbm, workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lbm.load()
+    w, label = workload(args.workload, args.precision)
+    p = dict(w["params"])
+    cells = p["nx"] * p["ny"]
+    stream = torch.cuda.current_stream()
+    sim = lbm.Simulation(p, stream)
+    xc, yc = W.sessile_center(p["nx"], w["R"], p["theta_deg"])
+    sim.init_droplet(w["R"], xc, yc, 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        flush.fill_(1.0)
+
+    obs_every = args.obs_every
+    for _ in range(args.warmup):
+        flush_l2()
+        sim.step(1)
+        sim.observables_async()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    n_obs = 0
+    for i in range(args.steps):
+        flush_l2()
+        a, b, c = ev[i]
+        a.record(stream)
+        sim.step(1)
+        b.record(stream)
+        if (i + 1) % obs_every == 0:
+            sim.observables_async()
+            n_obs += 1
+        c.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    step_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    tot_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    total_s = reduce_max(sum(tot_ms) / 1e3, world)
+    obs = sim.observables_fetch()
+    value = world * cells * args.steps / total_s / 1e6
+    launch_us = 1e3 * statistics.mean(step_ms)
+
+    # roofline of the dominant kernel (the fused step)
+    bpl = BYTES_PER_LU[args.precision]
+    alg_bytes = bpl * cells
+    achieved = alg_bytes / (launch_us * 1e-6) / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = profiled_traffic(args.precision)
+
+    # steady state (informational): a long graph-replayed run, L2 warm
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_ss = 2048
+    s0.record(stream)
+    sim.step(n_ss)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ss_mlups = cells * n_ss / (s0.elapsed_time(s1) / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # whole state from pinned host memory, steps, and reads the observables
+    nbytes = sim.state_bytes()
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    sim.export_state(host.numpy())
+    k_e2e = max(10, min(args.steps, 200))
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        sim.import_state(host.data_ptr())
+        sim.step(1)
+        sim.observables()
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e_value = world * cells * k_e2e / e2e_s / 1e6
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, n, el = oracle_mlups(p, w["R"], budget_s=args.cpu_budget)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{n} FP64 oracle steps of the same {p['nx']}x{p['ny']} lattice from the "
+                         f"initial droplet ({el:.1f} s, 1 thread)"}
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": label, "cells": cells, "precision": args.precision, "k_e": p["k_e"],
+                   "obs_every": obs_every, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": f"k_step<{args.precision}>", "launch_us": launch_us,
+                     "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_lu": bpl},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 120,
+                "steps": k_e2e},
+        "gpu_launches": args.steps + 2 * n_obs,
+        "clocks": clocks,
+        "steady_state": {"value": ss_mlups, "unit": "MLUPS",
+                         "note": f"lbm_step({n_ss}) graph replay, state resident in L2 (informational)"},
+        "observables": {k: obs[k] for k in ("step", "mass", "frozen_fraction", "height", "width", "status")},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16s"])
+    ap.add_argument("--workload", default="production", choices=["production", "precision"])
+    ap.add_argument("--obs-every", type=int, default=10)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -434,12 +434,9 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         const T dty = puy - T(io.aux_in[AUX_PUY * P + k]);
         pux_prev = pux;
         puy_prev = puy;
+        // interface normal, regularised where grad psi vanishes (Sec. 2)
         const T gn = sqrt(gpsix * gpsix + gpsiy * gpsiy);
-        T nxv = T(0), nyv = T(0);
-        if (!(gn < T(1e-12))) {
-            nxv = gpsix / gn;
-            nyv = gpsiy / gn;
-        }
+        const T nxv = gpsix / (gn + T(1e-4)), nyv = gpsiy / (gn + T(1e-4));
         const T lam = T(4) * ps * (T(1) - ps) / c.W;
         const T inv = T(1) / c.tau_f;
         const T pre = T(1) - T(1) / (T(2) * c.tau_f);

@@ -54,6 +54,16 @@ def sessile_center(nx: int, R: float, theta_deg: float):
     return nx / 2.0, -0.5 - R * math.cos(math.radians(theta_deg))
 
 
+def droplet_psi(nx: int, ny: int, R: float, xc: float, yc: float, W: float) -> np.ndarray:
+    """Initial order parameter of a circular droplet (Sec. 2): a tanh profile
+    of width W around the circle of radius R centred at (xc, yc), cell (x, y)
+    at (x, y).  Host copy for callers that want identical inputs on several
+    back ends (lbm_init_psi)."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    r = np.sqrt((x - xc) ** 2 + (y - yc) ** 2)
+    return 0.5 + 0.5 * np.tanh(2.0 * (R - r) / W)
+
+
 # ---------------------------------------------------------------------------
 # The five workloads.
 # ---------------------------------------------------------------------------
