@@ -2,7 +2,8 @@
 
 Each translation unit compiles in parallel; the FP64 unit is built without
 fused multiply-add contraction so its rounding follows the arithmetic as
-written (the CPU oracle is compiled the same way).
+written (the CPU oracle is compiled the same way).  The single-precision
+units use the hardware's fast division and square root and flush denormals.
 """
 from __future__ import annotations
 
@@ -19,11 +20,12 @@ LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I" + os.path.join(HERE, "..", "include")]
+FAST32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 UNITS = {
     "lbm_api.cu": [],
     "step_f64.cu": ["-fmad=false"],
-    "step_f32.cu": [],
-    "step_f16s.cu": [],
+    "step_f32.cu": FAST32,
+    "step_f16s.cu": FAST32,
 }
 
 

@@ -427,8 +427,8 @@ int lbm_observables_async(lbm_handle *h) {
     cudaError_t e;
     switch (h->P.precision) {
     case LBM_FP64: e = launch_obs_f64(h->s, h->cur, h->lcur, &h->cd, h->sh, h->ws, sc, h->st); break;
-    case LBM_FP32: e = launch_obs_f32(h->s, h->cur, h->lcur, &h->cd, h->sh, h->ws, sc, h->st); break;
-    default: e = launch_obs_f16s(h->s, h->cur, h->lcur, &h->cd, h->sh, h->ws, sc, h->st); break;
+    case LBM_FP32: e = launch_obs_f32(h->s, h->cur, h->lcur, &h->cf, h->sh, h->ws, sc, h->st); break;
+    default: e = launch_obs_f16s(h->s, h->cur, h->lcur, &h->cf, h->sh, h->ws, sc, h->st); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "observables kernels");
     return LBM_OK;

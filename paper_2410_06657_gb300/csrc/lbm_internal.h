@@ -75,7 +75,8 @@ struct Scalars {           // per-call scalars of the observables reduction
     cudaError_t launch_init_##SUFFIX(const DevState &s, const double *psi_dev, double R,       \
                                      double xc, double yc, const void *consts,                 \
                                      const Shift &sh, cudaStream_t st);                        \
-    cudaError_t launch_obs_##SUFFIX(const DevState &s, int cur, int lcur, const void *consts,  \
+    cudaError_t launch_obs_##SUFFIX(const DevState &s, int cur, int lcur,                      \
+                                    const void *consts /* Consts of the step's type */,       \
                                     const Shift &sh, const ObsScratch &ws, const Scalars &sc,  \
                                     cudaStream_t st);                                          \
     cudaError_t launch_get_##SUFFIX(const DevState &s, int cur, int lcur, int field,           \

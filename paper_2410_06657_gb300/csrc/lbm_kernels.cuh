@@ -152,22 +152,44 @@ __device__ __forceinline__ void local_macros(const T f[9], const T g[9], T l1234
     m.phi = l1234 / (T(1) - w5<T>(0));                    // Eq. (Computed_phi)
 }
 
-// Isotropic stencils (Eqs. eqtidi1-2) on a shared-memory tile.
+// c . (a, b) for a lattice vector with components in {-1, 0, 1}.  Terms
+// with a zero component are skipped and signs are applied exactly, so the
+// result has the bits of cx * a + cy * b evaluated in that order (adding a
+// signed zero or multiplying by +-1 is exact) without the zero products.
+template <typename T>
+__device__ __forceinline__ T cdot(int cx, int cy, T a, T b) {
+    T r = cx > 0 ? a : (cx < 0 ? -a : T(0));
+    if (cy > 0) r = cx != 0 ? r + b : b;
+    else if (cy < 0) r = cx != 0 ? r - b : -b;
+    return r;
+}
+
+// Isotropic stencils (Eqs. eqtidi1-2) on a shared-memory tile: the sums
+// over i = 1..8 of w_i c_i z(x + c_i) and 2 w_i (z(x + c_i) - z(x)), in
+// the order of i, with the zero terms of the gradient left out.
 template <typename T, int W>
 __device__ __forceinline__ void grad_s(const T (*z)[W], int ex, int ey, T &gx, T &gy) {
-    T sx = T(0), sy = T(0);
-#pragma unroll
-    for (int i = 1; i < 9; i++) {
-        T v = z[ey + CY[i]][ex + CX[i]];
-        sx += w9<T>(i) * T(CX[i]) * v;
-        sy += w9<T>(i) * T(CY[i]) * v;
-    }
+    const T wa = T(1.0 / 9.0), wd = T(1.0 / 36.0);
+    const T v1 = z[ey][ex + 1], v2 = z[ey + 1][ex], v3 = z[ey][ex - 1], v4 = z[ey - 1][ex];
+    const T v5 = z[ey + 1][ex + 1], v6 = z[ey + 1][ex - 1], v7 = z[ey - 1][ex - 1], v8 = z[ey - 1][ex + 1];
+    T sx = wa * v1;
+    sx = sx - wa * v3;
+    sx = sx + wd * v5;
+    sx = sx - wd * v6;
+    sx = sx - wd * v7;
+    sx = sx + wd * v8;
+    T sy = wa * v2;
+    sy = sy - wa * v4;
+    sy = sy + wd * v5;
+    sy = sy + wd * v6;
+    sy = sy - wd * v7;
+    sy = sy - wd * v8;
     gx = sx / cs2<T>();
     gy = sy / cs2<T>();
 }
 template <typename T, int W>
 __device__ __forceinline__ T lap_s(const T (*z)[W], int ex, int ey) {
-    T z0 = z[ey][ex];
+    const T z0 = z[ey][ex];
     T acc = T(0);
 #pragma unroll
     for (int i = 1; i < 9; i++) acc += T(2) * w9<T>(i) * (z[ey + CY[i]][ex + CX[i]] - z0);
@@ -177,7 +199,7 @@ __device__ __forceinline__ T lap_s(const T (*z)[W], int ex, int ey) {
 // s_i(u) of Sec. 3.2.
 template <typename T>
 __device__ __forceinline__ T s_i(int i, T ux, T uy) {
-    T cu = T(CX[i]) * ux + T(CY[i]) * uy;
+    T cu = cdot<T>(CX[i], CY[i], ux, uy);
     T uu = ux * ux + uy * uy;
     return w9<T>(i) * (cu / cs2<T>() + cu * cu / (T(2) * cs2<T>() * cs2<T>()) - uu / (T(2) * cs2<T>()));
 }
@@ -216,12 +238,14 @@ struct StepIO {
 template <typename S, typename T, typename A>
 __device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, int lcur, int write_sigma) {
     StepIO<S, T, A> io;
-    io.fhg_in = reinterpret_cast<const S *>(s.pop[cur]);
-    io.fhg_out = reinterpret_cast<S *>(s.pop[1 - cur]);
-    io.l_in = reinterpret_cast<const S *>(s.pop[lcur]) + (long long)NFHG * s.plane;
-    io.l_out = reinterpret_cast<S *>(s.pop[1 - lcur]) + (long long)NFHG * s.plane;
-    io.aux_in = reinterpret_cast<const A *>(s.aux[cur]);
-    io.aux_out = reinterpret_cast<A *>(s.aux[1 - cur]);
+    // select rather than index the parameter arrays (a dynamic index would
+    // copy them to local memory)
+    io.fhg_in = reinterpret_cast<const S *>(cur ? s.pop[1] : s.pop[0]);
+    io.fhg_out = reinterpret_cast<S *>(cur ? s.pop[0] : s.pop[1]);
+    io.l_in = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * s.plane;
+    io.l_out = reinterpret_cast<S *>(lcur ? s.pop[0] : s.pop[1]) + (long long)NFHG * s.plane;
+    io.aux_in = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
+    io.aux_out = reinterpret_cast<A *>(cur ? s.aux[0] : s.aux[1]);
     io.sigma = reinterpret_cast<A *>(s.sigma);
     io.nx = s.nx;
     io.ny = s.ny;
@@ -275,7 +299,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     const int x = xg < nx ? xg : xg % nx;       // wrapped slot of a ragged tile
     const long long k = (long long)y * io.pitch + x;
     Refs<T> rf;
-    T f[9], g[9], l[5];
+    T f[9], g[9], l[5], h[9];
     Macro<T> m;
     T fs_prev = T(0), mdot_prev = T(0), Q_prev = T(0), pux_prev = T(0), puy_prev = T(0);
     const float fsc = 1.0f / sh.f_scale, gsc = 1.0f / sh.g_scale, lsc = 1.0f / sh.l_scale;
@@ -289,6 +313,10 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         }
 #pragma unroll
         for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(io.l_in + i * P + k, rf.l[i], lsc);
+#pragma unroll
+        for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.fhg_in + (9 + i) * P + k, T(0), hsc);
+        pux_prev = T(io.aux_in[AUX_PUX * P + k]);
+        puy_prev = T(io.aux_in[AUX_PUY * P + k]);
         fs_prev = T(io.aux_in[AUX_FS * P + k]);
         mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
         Q_prev = T(io.aux_in[AUX_Q * P + k]);
@@ -372,15 +400,19 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     const T Fx = Fsx + Fex, Fy = Fsy + Fey;
 
     // ---- a4: flow macros (Sec. 3.2) ---------------------------------------
-    T h[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.fhg_in + (9 + i) * P + k, T(0), hsc);
-    T jx = T(0), jy = T(0);
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        jx += T(CX[i]) * h[i];
-        jy += T(CY[i]) * h[i];
-    }
+    // sum_i c_i h_i in the order of i (zero terms skipped)
+    T jx = h[1];
+    jx = jx - h[3];
+    jx = jx + h[5];
+    jx = jx - h[6];
+    jx = jx - h[7];
+    jx = jx + h[8];
+    T jy = h[2];
+    jy = jy - h[4];
+    jy = jy + h[5];
+    jy = jy + h[6];
+    jy = jy - h[7];
+    jy = jy - h[8];
     const T r = m.rho;
     const T mu = chi(m.fs, ps, c.mu), kth = chi(m.fs, ps, c.kth);
     const T sig = chi(m.fs, ps, c.sig), cp = chi(m.fs, ps, c.cp);
@@ -401,10 +433,13 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     const T p = cs2<T>() / (T(1) - w9<T>(0)) * (sh_ + T(0.5) * Sn + tau_h * R0 + r * s_i<T>(0, ux, uy));
 
     // ---- collisions + push streaming (a5-a9) -------------------------------
-    const int xl = x;                         // own column
-    const bool bot = (y == 0), top = (y == ny - 1);
+    // destinations of the push: wrapped columns and rows computed once
+    const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
+    const long long r0 = (long long)y * io.pitch;
     auto dest = [&](int i, int cxv, int cyv) -> long long {
-        return (long long)(y + cyv) * io.pitch + wrapx<T>(xl + cxv, nx);
+        (void)i;
+        const long long row = cyv < 0 ? r0 - io.pitch : (cyv > 0 ? r0 + io.pitch : r0);
+        return row + (cxv < 0 ? xm : (cxv > 0 ? xp : x));
     };
     Refs<T> ro;                               // destination references (half storage)
 
@@ -413,9 +448,9 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         const T pre = T(1) - T(1) / (T(2) * tau_h);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            const T cu = T(CX[i]) * ux + T(CY[i]) * uy;
-            const T cF = T(CX[i]) * Ftx + T(CY[i]) * Fty;
-            const T Ri = w9<T>(i) * (Sn + (T(CX[i]) * (Fx + rfx) + T(CY[i]) * (Fy + rfy)) / cs2<T>() +
+            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+            const T cF = cdot<T>(CX[i], CY[i], Ftx, Fty);
+            const T Ri = w9<T>(i) * (Sn + cdot<T>(CX[i], CY[i], Fx + rfx, Fy + rfy) / cs2<T>() +
                                      (cu * cF - cs2<T>() * uF) / (cs2<T>() * cs2<T>()));
             const T heq = ((i == 0) ? p / cs2<T>() * (w9<T>(0) - T(1)) : p / cs2<T>() * w9<T>(i)) +
                           r * s_i<T>(i, ux, uy);
@@ -430,24 +465,22 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     // a5: phase field
     {
         const T pux = ps * ux, puy = ps * uy;
-        const T dtx = pux - T(io.aux_in[AUX_PUX * P + k]);
-        const T dty = puy - T(io.aux_in[AUX_PUY * P + k]);
+        const T dtx = pux - pux_prev;         // Euler d_t(psi u) (Sec. 3.4)
+        const T dty = puy - puy_prev;
         pux_prev = pux;
         puy_prev = puy;
         // interface normal, regularised where grad psi vanishes (Sec. 2)
         const T gn = sqrt(gpsix * gpsix + gpsiy * gpsiy);
         const T nxv = gpsix / (gn + T(1e-4)), nyv = gpsiy / (gn + T(1e-4));
         const T lam = T(4) * ps * (T(1) - ps) / c.W;
-        const T inv = T(1) / c.tau_f;
         const T pre = T(1) - T(1) / (T(2) * c.tau_f);
-        (void)inv;
+        const T ax = dtx + cs2<T>() * lam * nxv;
+        const T ay = dty + cs2<T>() * lam * nyv;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            const T cu = T(CX[i]) * ux + T(CY[i]) * uy;
+            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
             const T feq = w9<T>(i) * ps * (T(1) + cu / cs2<T>());
-            const T ax = dtx + cs2<T>() * lam * nxv;
-            const T ay = dty + cs2<T>() * lam * nyv;
-            const T Fi = w9<T>(i) * (T(CX[i]) * ax + T(CY[i]) * ay) / cs2<T>() + w9<T>(i) * ps * mdot;
+            const T Fi = w9<T>(i) * cdot<T>(CX[i], CY[i], ax, ay) / cs2<T>() + w9<T>(i) * ps * mdot;
             const T post = f[i] - (f[i] - feq) / c.tau_f + pre * Fi;
             const int yt = y + CY[i];
             if (yt < 0 || yt >= ny) {
@@ -468,7 +501,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         const T pre = T(1) - T(1) / (T(2) * tau_g);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            const T cu = T(CX[i]) * ux + T(CY[i]) * uy;
+            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
             T geq;
             if (i == 0)
                 geq = m.H - c.Cref * m.T_ + w9<T>(0) * cp * m.T_ * (c.Cref / cp - uu / (T(2) * cs2<T>()));
@@ -505,13 +538,10 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
                               sh.l_scale);
             } else {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st(io.l_out + i * P + (long long)yt * io.pitch + wrapx<T>(xl + CX5[i], nx), post,
-                              ro.l[i], sh.l_scale);
+                Pol<S, T>::st(io.l_out + i * P + dest(i, CX5[i], CY5[i]), post, ro.l[i], sh.l_scale);
             }
         }
     }
-    (void)bot;
-    (void)top;
     // previous-step fields for the next step
     io.aux_out[AUX_FS * P + k] = A(m.fs);
     io.aux_out[AUX_MDOT * P + k] = A(mdot);
@@ -606,8 +636,8 @@ __global__ void k_sweep(DevState s, int lcur, Consts<T> c, Shift sh) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= s.nx || y >= s.ny) return;
-    const S *l_in = reinterpret_cast<const S *>(s.pop[lcur]) + (long long)NFHG * s.plane;
-    S *l_out = reinterpret_cast<S *>(s.pop[1 - lcur]) + (long long)NFHG * s.plane;
+    const S *l_in = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * s.plane;
+    S *l_out = reinterpret_cast<S *>(lcur ? s.pop[0] : s.pop[1]) + (long long)NFHG * s.plane;
     sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(s.sigma), s.nx, s.ny, s.pitch, s.plane, c,
                         sh, x, y);
 }
@@ -625,8 +655,8 @@ __global__ void __launch_bounds__(256) k_batch_sweep(const BatchItem *__restrict
         const int y = (local / it.sweep_tiles_x) * 8 + threadIdx.y;
         if (x < it.s.nx && y < it.s.ny) {
             const int lc = it.lcur ^ flip_l;
-            const S *l_in = reinterpret_cast<const S *>(it.s.pop[lc]) + (long long)NFHG * it.s.plane;
-            S *l_out = reinterpret_cast<S *>(it.s.pop[1 - lc]) + (long long)NFHG * it.s.plane;
+            const S *l_in = reinterpret_cast<const S *>(lc ? it.s.pop[1] : it.s.pop[0]) + (long long)NFHG * it.s.plane;
+            S *l_out = reinterpret_cast<S *>(lc ? it.s.pop[0] : it.s.pop[1]) + (long long)NFHG * it.s.plane;
             sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(it.s.sigma), it.s.nx, it.s.ny,
                                 it.s.pitch, it.s.plane, consts[ii], it.sh, x, y);
         }
@@ -723,17 +753,35 @@ __device__ __forceinline__ void obs_macros(const S *fhg, const S *lb, const A *a
                          double(aux[AUX_Q * P + k]), c, m);
 }
 
+// Local macros of one cell in the arithmetic type T (the step's own type).
 template <typename S, typename T, typename A>
-__global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<double> c, Shift sh,
+__device__ __forceinline__ void cell_macros_t(const S *fhg, const S *lb, const A *aux, long long P, long long k,
+                                              int y, int ny, const Consts<T> &c, const Shift &sh, Macro<T> &m) {
+    Refs<T> rf;
+    make_refs<S, T>(rf, sh, c, y, ny);
+    T f[9], g[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        f[i] = Pol<S, T>::ld(fhg + i * P + k, rf.f[i], 1.0f / sh.f_scale);
+        g[i] = Pol<S, T>::ld(fhg + (18 + i) * P + k, rf.g[i], 1.0f / sh.g_scale);
+    }
+    T l1234 = T(0);
+#pragma unroll
+    for (int i = 1; i < 5; i++) l1234 += Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale);
+    local_macros<T>(f, g, l1234, T(aux[AUX_FS * P + k]), T(aux[AUX_MDOT * P + k]), T(aux[AUX_Q * P + k]), c, m);
+}
+
+template <typename S, typename T, typename A>
+__global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<T> c, Shift sh,
                                                     ObsScratch ws) {
     __shared__ double s_psi[OBS_BY + 2][34], s_fs[OBS_BY + 2][34], s_eps[OBS_BY + 2][34], s_phi[OBS_BY + 2][34];
     __shared__ double s_red[4][32 * OBS_BY / 32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int nx = s.nx, ny = s.ny;
     const long long P = s.plane;
-    const S *fhg = reinterpret_cast<const S *>(s.pop[cur]);
-    const S *lb = reinterpret_cast<const S *>(s.pop[lcur]) + (long long)NFHG * P;
-    const A *aux = reinterpret_cast<const A *>(s.aux[cur]);
+    const S *fhg = reinterpret_cast<const S *>(cur ? s.pop[1] : s.pop[0]);
+    const S *lb = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * P;
+    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * OBS_BY;
     // fill the extended tile (own + halo), ghost rows as in the step
     for (int r = tid; r < 34 * (OBS_BY + 2); r += 32 * OBS_BY) {
@@ -742,22 +790,22 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         if (yy < 0 || yy >= ny) continue;
         int xx = (x0 - 1 + ex) % nx;
         if (xx < 0) xx += nx;
-        Macro<double> m;
-        obs_macros<S, T, A>(fhg, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, m);
-        s_psi[ey][ex] = m.psi;
-        s_fs[ey][ex] = m.fs;
-        s_eps[ey][ex] = m.eps;
-        s_phi[ey][ex] = m.phi;
+        Macro<T> m;
+        cell_macros_t<S, T, A>(fhg, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, m);
+        s_psi[ey][ex] = double(m.psi);
+        s_fs[ey][ex] = double(m.fs);
+        s_eps[ey][ex] = double(m.eps);
+        s_phi[ey][ex] = double(m.phi);
     }
     __syncthreads();
     if (y0 == 0 && tid < 34) {
         s_eps[0][tid] = s_eps[1][tid];
-        s_phi[0][tid] = 2.0 * c.phi_bot - s_phi[1][tid];
+        s_phi[0][tid] = 2.0 * double(c.phi_bot) - s_phi[1][tid];
     }
     const int et = ny - y0 + 1;
     if (et >= 1 && et <= OBS_BY + 1 && tid >= 64 && tid < 98) {
         s_eps[et][tid - 64] = s_eps[et - 1][tid - 64];
-        s_phi[et][tid - 64] = 2.0 * c.phi_top - s_phi[et - 1][tid - 64];
+        s_phi[et][tid - 64] = 2.0 * double(c.phi_top) - s_phi[et - 1][tid - 64];
     }
     __syncthreads();
 
@@ -765,17 +813,17 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
     double v_psi = 0.0, v_H = 0.0, v_fs = 0.0, v_q = 0.0;
     if (x < nx && y < ny) {
         const int ex = tx + 1, ey = ty + 1;
-        Macro<double> m;
-        obs_macros<S, T, A>(fhg, lb, aux, P, (long long)y * s.pitch + x, y, ny, c, sh, m);
+        Macro<T> m;
+        cell_macros_t<S, T, A>(fhg, lb, aux, P, (long long)y * s.pitch + x, y, ny, c, sh, m);
         double gex, gey, gphx, gphy;
         grad_s<double, 34>(s_eps, ex, ey, gex, gey);
         grad_s<double, 34>(s_phi, ex, ey, gphx, gphy);
         const double lphi = lap_s<double, 34>(s_phi, ex, ey);
-        v_q = -(gex * gphx + gey * gphy + m.eps * lphi);
-        v_psi = m.psi;
-        v_H = m.H;
-        v_fs = m.fs;
-        if (!isfinite(m.psi) || !isfinite(m.H)) atomicOr(ws.bad, 1u);
+        v_q = -(gex * gphx + gey * gphy + double(m.eps) * lphi);
+        v_psi = double(m.psi);
+        v_H = double(m.H);
+        v_fs = double(m.fs);
+        if (!isfinite(v_psi) || !isfinite(v_H)) atomicOr(ws.bad, 1u);
         const double a = s_psi[ey][ex];
         // column crossing (height): psi(y) >= 1/2 > psi(y+1)
         if (a >= 0.5) {
@@ -903,9 +951,9 @@ __global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c
     if (x >= s.nx || y >= s.ny) return;
     const long long P = s.plane, k = (long long)y * s.pitch + x;
     const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
-    const S *fhg = reinterpret_cast<const S *>(s.pop[cur]);
-    const S *lb = reinterpret_cast<const S *>(s.pop[lcur]) + (long long)NFHG * P;
-    const A *aux = reinterpret_cast<const A *>(s.aux[cur]);
+    const S *fhg = reinterpret_cast<const S *>(cur ? s.pop[1] : s.pop[0]);
+    const S *lb = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * P;
+    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     Refs<T> rf;
     Consts<T> ct;
     ct.phi_bot = T(c.phi_bot);
@@ -942,9 +990,9 @@ __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shi
     if (x >= s.nx || y >= s.ny) return;
     const long long P = s.plane, k = (long long)y * s.pitch + x;
     const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
-    S *fhg = reinterpret_cast<S *>(s.pop[cur]);
-    S *lb = reinterpret_cast<S *>(s.pop[lcur]) + (long long)NFHG * P;
-    A *aux = reinterpret_cast<A *>(s.aux[cur]);
+    S *fhg = reinterpret_cast<S *>(cur ? s.pop[1] : s.pop[0]);
+    S *lb = reinterpret_cast<S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * P;
+    A *aux = reinterpret_cast<A *>(cur ? s.aux[1] : s.aux[0]);
     Refs<T> rf;
     make_refs<S, T>(rf, sh, c, y, s.ny);
     if (field == LBM_FIELD_F || field == LBM_FIELD_H || field == LBM_FIELD_G) {
@@ -999,7 +1047,7 @@ __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shi
     cudaError_t launch_obs_##SUFFIX(const DevState &s, int cur, int lcur, const void *consts,              \
                                     const Shift &sh, const ObsScratch &ws, const Scalars &sc,               \
                                     cudaStream_t st) {                                                      \
-        const Consts<double> &c = *reinterpret_cast<const Consts<double> *>(consts);                      \
+        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
         dim3 grid((s.nx + 31) / 32, (s.ny + OBS_BY - 1) / OBS_BY);                                          \
         k_obs<S, T, A><<<grid, dim3(32, OBS_BY), 0, st>>>(s, cur, lcur, c, sh, ws);                         \
         k_obs_final<<<1, 256, 0, st>>>(s.nx, s.ny, ws, sc);                                                 \
