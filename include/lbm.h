@@ -239,6 +239,18 @@ size_t lbm_state_bytes(const struct lbm_handle *h);
 int lbm_export_state(struct lbm_handle *h, void *host, size_t bytes);
 int lbm_import_state(struct lbm_handle *h, const void *host, size_t bytes);
 
+/*
+ * Step kernel selection (tuning and testing; results do not depend on it in
+ * FP64, and differ only by rounding in FP32):
+ *   variant LBM_STEP_TMA (default): tensor-memory-accelerator loads bring
+ *     each tile with its halo into shared memory;
+ *   variant LBM_STEP_DIRECT: every thread loads its cell from global memory.
+ *   tile_rows: 4, 8 (default) or 16 lattice rows per 32-column tile.
+ * Errors: BADPARAM (unknown variant or height, NULL).
+ */
+enum { LBM_STEP_TMA = 0, LBM_STEP_DIRECT = 1 };
+int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
+
 /* Steps taken since the last init.  */
 int64_t lbm_step_count(const struct lbm_handle *h);
 

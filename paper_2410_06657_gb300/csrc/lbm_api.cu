@@ -1,6 +1,8 @@
 // Host side of the C ABI declared in include/lbm.h: parameter validation,
 // derived lattice constants, device memory, stepping (with CUDA-graph
 // replay of long runs), observables, field access, snapshots and batches.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -156,6 +158,9 @@ struct lbm_handle {
     int64_t step = 0;
     bool inited = false, diverged = false;
     int tile_rows = 8;
+    bool use_tma = true;       // TMA form of the step (tensor-map loads of the halo'd tile)
+    TmaMaps maps;              // tensor maps for tile_rows (encoded on first use)
+    unsigned int *err = nullptr;   // device status word of bounded waits (sticky)
     // graph cache: one per starting parity (cur, lcur)
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int gsteps = 0;
@@ -178,6 +183,63 @@ struct lbm_batch {
 
 namespace {
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// One 3-D map (x, y, plane) over `planes` planes starting at `base`, with a
+// box of (32 + 2 * 16/elem) x (by + 2) x planes elements.
+int encode_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, size_t elem, int nx, int ny, int pitch,
+               long long plane, int planes, int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * elem, (cuuint64_t)plane * elem};
+    const cuuint32_t box[3] = {(cuuint32_t)(32 + 2 * (16 / elem)), (cuuint32_t)(by + 2), (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return LBM_OK;
+}
+
+const void *consts_for(const lbm_handle *h);
+
+int ensure_maps(lbm_handle *h) {
+    if (h->maps.by == h->tile_rows) return LBM_OK;
+    const int prec = h->P.precision;
+    const size_t sb = storage_bytes(prec), ab = aux_bytes(prec);
+    const CUtensorMapDataType dp = prec == LBM_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : prec == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const CUtensorMapDataType da = prec == LBM_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const DevState &s = h->s;
+    for (int b = 0; b < 2; b++) {
+        int rc = encode_map(&h->maps.fhg[b], s.pop[b], dp, sb, s.nx, s.ny, s.pitch, s.plane, NFHG, h->tile_rows);
+        if (!rc)
+            rc = encode_map(&h->maps.l[b], static_cast<char *>(s.pop[b]) + (size_t)NFHG * s.plane * sb, dp, sb, s.nx,
+                            s.ny, s.pitch, s.plane, NPOP - NFHG, h->tile_rows);
+        if (!rc) rc = encode_map(&h->maps.aux[b], s.aux[b], da, ab, s.nx, s.ny, s.pitch, s.plane, NAUX, h->tile_rows);
+        if (rc) return rc;
+    }
+    h->maps.by = h->tile_rows;
+    return LBM_OK;
+}
+
 const void *consts_for(const lbm_handle *h) {
     return h->P.precision == LBM_FP64 ? static_cast<const void *>(&h->cd) : static_cast<const void *>(&h->cf);
 }
@@ -186,10 +248,18 @@ cudaError_t do_step(lbm_handle *h, cudaStream_t st) {
     const int ws = h->P.k_e > 1 ? 1 : 0;
     const void *c = consts_for(h);
     cudaError_t e;
-    switch (h->P.precision) {
-    case LBM_FP64: e = launch_step_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
-    case LBM_FP32: e = launch_step_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
-    default: e = launch_step_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
+    if (h->use_tma) {
+        switch (h->P.precision) {
+        case LBM_FP64: e = launch_step_tma_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->maps, st); break;
+        case LBM_FP32: e = launch_step_tma_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->maps, st); break;
+        default: e = launch_step_tma_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->maps, st); break;
+        }
+    } else {
+        switch (h->P.precision) {
+        case LBM_FP64: e = launch_step_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
+        case LBM_FP32: e = launch_step_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
+        default: e = launch_step_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
+        }
     }
     if (e != cudaSuccess) return e;
     h->cur ^= 1;
@@ -317,7 +387,8 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->ws_min_bytes = round_up((size_t)(1 + ny) * 8, 256);
     h->ws_u32_bytes = round_up((size_t)(ny + 2) * 4, 256);
     const size_t obs_b = round_up(sizeof(lbm_obs), 256);
-    if (cudaMalloc(&h->ws_mem, part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b) !=
+    const size_t err_b = 256;
+    if (cudaMalloc(&h->ws_mem, part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b + err_b) !=
         cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->mem);
@@ -334,7 +405,16 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->ws.rowany = h->ws_u32_base;
     h->ws.bad = h->ws_u32_base + ny;
     h->ws.obs = reinterpret_cast<lbm_obs *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes);
+    h->err = reinterpret_cast<unsigned int *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b);
+    h->s.err = h->err;
     h->ws.nblocks = nb;
+    if (cudaMemset(h->err, 0, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->ws_mem);
+        cudaFree(h->mem);
+        delete h;
+        return fail(LBM_ERR_CUDA, "workspace initialisation failed");
+    }
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->ws_mem);
@@ -378,6 +458,10 @@ int lbm_step(lbm_handle *h, int64_t n) {
     if (n < 0) return fail(LBM_ERR_BADPARAM, "n must be >= 0");
     if (!h->inited) return fail(LBM_ERR_STATE, "step before init");
     if (h->diverged) return fail(LBM_ERR_DIVERGED, "instance diverged earlier");
+    if (h->use_tma) {
+        int rc = ensure_maps(h);
+        if (rc) return rc;
+    }
     // Long runs replay a captured graph of G steps (G even, so both parities
     // return to their starting values and the graph can be reused).
     const int G = 32;
@@ -437,8 +521,11 @@ int lbm_observables_async(lbm_handle *h) {
 int lbm_observables_fetch(lbm_handle *h, lbm_obs *out) {
     if (!h || !out) return fail(LBM_ERR_BADPARAM, "NULL argument");
     if (!h->inited) return fail(LBM_ERR_STATE, "observables before init");
+    unsigned int err = 0;
     CK(cudaMemcpyAsync(out, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&err, h->err, sizeof err, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    if (err) return fail(LBM_ERR_CUDA, "a bounded wait in the step kernel timed out (tensor loads did not complete)");
     if (out->status == LBM_ERR_DIVERGED) {
         h->diverged = true;
         return fail(LBM_ERR_DIVERGED, "non-finite psi or H");
@@ -580,6 +667,20 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
 }
 
 int64_t lbm_step_count(const lbm_handle *h) { return h ? h->step : -1; }
+
+int lbm_configure(lbm_handle *h, int32_t variant, int32_t tile_rows) {
+    if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    if (variant != LBM_STEP_TMA && variant != LBM_STEP_DIRECT) return fail(LBM_ERR_BADPARAM, "unknown variant");
+    if (tile_rows != 4 && tile_rows != 8 && tile_rows != 16) return fail(LBM_ERR_BADPARAM, "tile_rows must be 4, 8 or 16");
+    CK(cudaStreamSynchronize(h->st));
+    h->use_tma = (variant == LBM_STEP_TMA);
+    if (h->tile_rows != tile_rows) {
+        h->tile_rows = tile_rows;
+        h->maps.by = 0;
+    }
+    drop_graphs(h);
+    return LBM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Batches

@@ -2,6 +2,7 @@
 // library (host API, and one kernel unit per storage precision).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -44,8 +45,16 @@ struct DevState {
     void *pop[2];          // two copies of NPOP planes
     void *aux[2];          // two copies of NAUX planes
     void *sigma;           // one plane
+    unsigned int *err;     // device status word: bit 0 = a bounded wait timed out
     int nx, ny, pitch;     // pitch: elements per row (multiple of 32)
     long long plane;       // elements per plane (pitch * ny)
+};
+
+// Tensor maps of one buffer copy for the TMA step (tile height BY):
+// f, h, g planes, l planes, auxiliary planes.
+struct TmaMaps {
+    CUtensorMap fhg[2], l[2], aux[2];
+    int by;                // tile height the boxes were encoded for (0: none)
 };
 
 // Workspace of the observables reduction.
@@ -70,6 +79,10 @@ struct Scalars {           // per-call scalars of the observables reduction
     cudaError_t launch_step_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,    \
                                      const void *consts, const Shift &sh, int tile_rows,       \
                                      cudaStream_t st);                                         \
+    cudaError_t launch_step_tma_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,\
+                                         const void *consts, const Shift &sh, const TmaMaps &m,\
+                                         cudaStream_t st);                                     \
+    size_t tma_smem_##SUFFIX(int tile_rows);                                                   \
     cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, const void *consts,         \
                                       const Shift &sh, cudaStream_t st);                       \
     cudaError_t launch_init_##SUFFIX(const DevState &s, const double *psi_dev, double R,       \

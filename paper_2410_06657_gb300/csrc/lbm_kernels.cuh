@@ -23,6 +23,7 @@
 // destinations in the other copy, applying the wall rules (a9).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -285,6 +286,233 @@ __device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Co
     sm.S[ey][ex] = T(io.aux_in[AUX_S * P + k]);
 }
 
+// Population sources for step_cell.
+template <typename T>
+struct RegPops {
+    const T (&f_)[9];
+    const T (&g_)[9];
+    const T (&l_)[5];
+    const T (&h_)[9];
+    __device__ __forceinline__ T f(int i) const { return f_[i]; }
+    __device__ __forceinline__ T g(int i) const { return g_[i]; }
+    __device__ __forceinline__ T l(int i) const { return l_[i]; }
+    __device__ __forceinline__ T h(int i) const { return h_[i]; }
+};
+
+// Wall ghost rows of the stencil tile (readings R17, R19): wetting ghost of
+// psi at the bottom wall, neutral at the top, copies of rho, eps, p, S, and
+// phi mirrored about the electrode potential.
+template <typename T, int BY>
+__device__ __forceinline__ void fill_ghosts(TileSmem<T, BY> &sm, const Consts<T> &c, int y0, int ny, int tid) {
+    if (y0 == 0 && tid < 34) {              // bottom wall: wetting, copy, mirror
+        const T z = sm.psi[1][tid];
+        sm.psi[0][tid] = z + c.wet * z * (T(1) - z);
+        sm.rho[0][tid] = sm.rho[1][tid];
+        sm.eps[0][tid] = sm.eps[1][tid];
+        sm.phi[0][tid] = T(2) * c.phi_bot - sm.phi[1][tid];
+        sm.p[0][tid] = sm.p[1][tid];
+        sm.S[0][tid] = sm.S[1][tid];
+    }
+    const int et = ny - y0 + 1;              // ext row of y = ny, if inside the tile
+    if (et >= 1 && et <= BY + 1 && tid >= 64 && tid < 98) {
+        const int e = tid - 64;              // top wall: neutral wetting, copy, mirror
+        sm.psi[et][e] = sm.psi[et - 1][e];
+        sm.rho[et][e] = sm.rho[et - 1][e];
+        sm.eps[et][e] = sm.eps[et - 1][e];
+        sm.phi[et][e] = T(2) * c.phi_top - sm.phi[et - 1][e];
+        sm.p[et][e] = sm.p[et - 1][e];
+        sm.S[et][e] = sm.S[et - 1][e];
+    }
+}
+
+// Row a2-a9 for one own cell: stencils from the shared-memory tile, forces,
+// flow macros, the four collisions and the push into the other copy.  PS
+// supplies the cell's time-n populations (registers or shared memory).
+template <typename S, typename T, typename A, int BY, typename PopSrc>
+__device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
+                                          const TileSmem<T, BY> &sm, const PopSrc &PS, int tx, int ty, int x,
+                                          int y, const Macro<T> &m, T fs_prev, T pux_prev, T puy_prev) {
+    const int nx = io.nx, ny = io.ny;
+    const long long P = io.plane;
+    const long long k = (long long)y * io.pitch + x;
+    Refs<T> ro;                               // destination references (half storage)
+    const int ex = tx + 1, ey = ty + 1;
+    // ---- a2: stencils ----------------------------------------------------
+    T gpsix, gpsiy, grhox, grhoy, gepsx, gepsy, gphix, gphiy, gpx, gpy, gSx, gSy;
+    grad_s<T, 34>(sm.psi, ex, ey, gpsix, gpsiy);
+    const T lpsi = lap_s<T, 34>(sm.psi, ex, ey);
+    grad_s<T, 34>(sm.rho, ex, ey, grhox, grhoy);
+    grad_s<T, 34>(sm.eps, ex, ey, gepsx, gepsy);
+    grad_s<T, 34>(sm.phi, ex, ey, gphix, gphiy);
+    const T lphi = lap_s<T, 34>(sm.phi, ex, ey);
+    grad_s<T, 34>(sm.p, ex, ey, gpx, gpy);
+    grad_s<T, 34>(sm.S, ex, ey, gSx, gSy);
+
+    // ---- a3: forces (Eq. Fs with the chemical potential of Sec. 2; Eq. Fe)
+    const T ps = m.psi;
+    const T muc = T(4) * c.beta * (ps - T(1)) * (ps - T(0)) * (ps - T(0.5)) - c.kappa * lpsi;
+    const T Fsx = muc * gpsix, Fsy = muc * gpsiy;
+    const T Ex = -gphix, Ey = -gphiy;
+    const T qv = -(gepsx * gphix + gepsy * gphiy + m.eps * lphi);
+    const T E2 = Ex * Ex + Ey * Ey;
+    const T Fex = qv * Ex - T(0.5) * E2 * gepsx;
+    const T Fey = qv * Ey - T(0.5) * E2 * gepsy;
+    const T Fx = Fsx + Fex, Fy = Fsy + Fey;
+
+    // ---- a4: flow macros (Sec. 3.2) ---------------------------------------
+    // sum_i c_i h_i in the order of i (zero terms skipped)
+    T jx = PS.h(1);
+    jx = jx - PS.h(3);
+    jx = jx + PS.h(5);
+    jx = jx - PS.h(6);
+    jx = jx - PS.h(7);
+    jx = jx + PS.h(8);
+    T jy = PS.h(2);
+    jy = jy - PS.h(4);
+    jy = jy + PS.h(5);
+    jy = jy + PS.h(6);
+    jy = jy - PS.h(7);
+    jy = jy - PS.h(8);
+    const T r = m.rho;
+    const T mu = chi(m.fs, ps, c.mu), kth = chi(m.fs, ps, c.kth);
+    const T sig = chi(m.fs, ps, c.sig), cp = chi(m.fs, ps, c.cp);
+    const T mdot = c.one_m_rsl * (m.fs - fs_prev);                 // Eq. (ns1)
+    const T usx = (jx + T(0.5) * Fx) / r, usy = (jy + T(0.5) * Fy) / r;
+    const T fx = m.fs * (T(0) - usx), fy = m.fs * (T(0) - usy);    // u_s = 0
+    const T ux = usx + T(0.5) * fx, uy = usy + T(0.5) * fy;        // Eq. (Computed_u)
+    const T rfx = r * fx, rfy = r * fy;
+    const T Sn = r * mdot + (ux * grhox + uy * grhoy);
+    const T Ftx = Fx - gpx + cs2<T>() * grhox + cs2<T>() * gSx;
+    const T Fty = Fy - gpy + cs2<T>() * grhoy + cs2<T>() * gSy;
+    const T uF = ux * Ftx + uy * Fty;
+    const T R0 = w9<T>(0) * (Sn - uF / cs2<T>());
+    const T tau_h = mu / r / cs2<T>() + T(0.5);
+    T sh_ = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; i++) sh_ += PS.h(i);
+    const T p = cs2<T>() / (T(1) - w9<T>(0)) * (sh_ + T(0.5) * Sn + tau_h * R0 + r * s_i<T>(0, ux, uy));
+
+    // ---- collisions + push streaming (a5-a9) -------------------------------
+    // destinations of the push: wrapped columns and rows computed once
+    const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
+    const long long r0 = (long long)y * io.pitch;
+    auto dest = [&](int i, int cxv, int cyv) -> long long {
+        (void)i;
+        const long long row = cyv < 0 ? r0 - io.pitch : (cyv > 0 ? r0 + io.pitch : r0);
+        return row + (cxv < 0 ? xm : (cxv > 0 ? xp : x));
+    };
+
+    // a7: flow
+    {
+        const T pre = T(1) - T(1) / (T(2) * tau_h);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+            const T cF = cdot<T>(CX[i], CY[i], Ftx, Fty);
+            const T Ri = w9<T>(i) * (Sn + cdot<T>(CX[i], CY[i], Fx + rfx, Fy + rfy) / cs2<T>() +
+                                     (cu * cF - cs2<T>() * uF) / (cs2<T>() * cs2<T>()));
+            const T heq = ((i == 0) ? p / cs2<T>() * (w9<T>(0) - T(1)) : p / cs2<T>() * w9<T>(i)) +
+                          r * s_i<T>(i, ux, uy);
+            const T post = PS.h(i) - (PS.h(i) - heq) / tau_h + pre * Ri;
+            const int yt = y + CY[i];
+            if (yt < 0 || yt >= ny)
+                Pol<S, T>::st(io.fhg_out + (9 + OPP9[i]) * P + k, post, T(0), sh.h_scale);
+            else
+                Pol<S, T>::st(io.fhg_out + (9 + i) * P + dest(i, CX[i], CY[i]), post, T(0), sh.h_scale);
+        }
+    }
+    // a5: phase field
+    {
+        const T pux = ps * ux, puy = ps * uy;
+        const T dtx = pux - pux_prev;         // Euler d_t(psi u) (Sec. 3.4)
+        const T dty = puy - puy_prev;
+        pux_prev = pux;
+        puy_prev = puy;
+        // interface normal, regularised where grad psi vanishes (Sec. 2)
+        const T gn = sqrt(gpsix * gpsix + gpsiy * gpsiy);
+        const T nxv = gpsix / (gn + T(1e-4)), nyv = gpsiy / (gn + T(1e-4));
+        const T lam = T(4) * ps * (T(1) - ps) / c.W;
+        const T pre = T(1) - T(1) / (T(2) * c.tau_f);
+        const T ax = dtx + cs2<T>() * lam * nxv;
+        const T ay = dty + cs2<T>() * lam * nyv;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+            const T feq = w9<T>(i) * ps * (T(1) + cu / cs2<T>());
+            const T Fi = w9<T>(i) * cdot<T>(CX[i], CY[i], ax, ay) / cs2<T>() + w9<T>(i) * ps * mdot;
+            const T post = PS.f(i) - (PS.f(i) - feq) / c.tau_f + pre * Fi;
+            const int yt = y + CY[i];
+            if (yt < 0 || yt >= ny) {
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+                Pol<S, T>::st(io.fhg_out + OPP9[i] * P + k, post, ro.f[OPP9[i]], sh.f_scale);
+            } else {
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
+                Pol<S, T>::st(io.fhg_out + i * P + dest(i, CX[i], CY[i]), post, ro.f[i], sh.f_scale);
+            }
+        }
+    }
+    // a8: enthalpy (Sec. 3.3)
+    T Qn;
+    {
+        const T tau_g = kth / (r * c.Cref * cs2<T>()) + T(0.5);
+        Qn = r * cp * m.T_ * mdot;
+        const T uu = ux * ux + uy * uy;
+        const T pre = T(1) - T(1) / (T(2) * tau_g);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+            T geq;
+            if (i == 0)
+                geq = m.H - c.Cref * m.T_ + w9<T>(0) * cp * m.T_ * (c.Cref / cp - uu / (T(2) * cs2<T>()));
+            else
+                geq = w9<T>(i) * cp * m.T_ *
+                      (c.Cref / cp + cu / cs2<T>() + (cu * cu - cs2<T>() * uu) / (T(2) * cs2<T>() * cs2<T>()));
+            const T post = PS.g(i) - (PS.g(i) - geq) / tau_g + pre * (w9<T>(i) * Qn);
+            const int yt = y + CY[i];
+            if (yt < 0) {            // cold wall: anti-bounce-back to C_p,ref T_w
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+                Pol<S, T>::st(io.fhg_out + (18 + OPP9[i]) * P + k,
+                              -post + T(2) * w9<T>(i) * c.Cref_Tw, ro.g[OPP9[i]], sh.g_scale);
+            } else if (yt >= ny) {   // top wall: adiabatic bounce-back
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+                Pol<S, T>::st(io.fhg_out + (18 + OPP9[i]) * P + k, post, ro.g[OPP9[i]], sh.g_scale);
+            } else {
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
+                Pol<S, T>::st(io.fhg_out + (18 + i) * P + dest(i, CX[i], CY[i]), post, ro.g[i], sh.g_scale);
+            }
+        }
+    }
+    // a6: potential (Sec. 3.4), one sweep inside the fused step
+    {
+        const T tau_l = sig / cs2<T>() + T(0.5);
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            const T leq = (i == 0) ? (w5<T>(0) - T(1)) * m.phi : w5<T>(i) * m.phi;
+            const T post = PS.l(i) - (PS.l(i) - leq) / tau_l;
+            const int yt = y + CY5[i];
+            if (yt < 0 || yt >= ny) {   // electrodes: anti-bounce-back
+                const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+                Pol<S, T>::st(io.l_out + OPP5[i] * P + k, -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]],
+                              sh.l_scale);
+            } else {
+                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
+                Pol<S, T>::st(io.l_out + i * P + dest(i, CX5[i], CY5[i]), post, ro.l[i], sh.l_scale);
+            }
+        }
+    }
+    // previous-step fields for the next step
+    io.aux_out[AUX_FS * P + k] = A(m.fs);
+    io.aux_out[AUX_MDOT * P + k] = A(mdot);
+    io.aux_out[AUX_Q * P + k] = A(Qn);
+    io.aux_out[AUX_PUX * P + k] = A(pux_prev);
+    io.aux_out[AUX_PUY * P + k] = A(puy_prev);
+    io.aux_out[AUX_P * P + k] = A(p);
+    io.aux_out[AUX_S * P + k] = A(Sn);
+    if (io.write_sigma) io.sigma[k] = A(sig);
+}
+
+
 template <typename S, typename T, typename A, int BY>
 __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Consts<T> &c,
                                           const Shift &sh, TileSmem<T, BY> &sm, int x0, int y0) {
@@ -353,204 +581,11 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     }
     __syncthreads();
 
-    // ---- wall ghost rows for the stencils (readings R17, R19) ----------
-    if (y0 == 0 && tid < 34) {              // bottom wall: wetting, copy, mirror
-        const T z = sm.psi[1][tid];
-        sm.psi[0][tid] = z + c.wet * z * (T(1) - z);
-        sm.rho[0][tid] = sm.rho[1][tid];
-        sm.eps[0][tid] = sm.eps[1][tid];
-        sm.phi[0][tid] = T(2) * c.phi_bot - sm.phi[1][tid];
-        sm.p[0][tid] = sm.p[1][tid];
-        sm.S[0][tid] = sm.S[1][tid];
-    }
-    const int et = ny - y0 + 1;              // ext row of y = ny, if inside the tile
-    if (et >= 1 && et <= BY + 1 && tid >= 64 && tid < 98) {
-        const int e = tid - 64;              // top wall: neutral wetting, copy, mirror
-        sm.psi[et][e] = sm.psi[et - 1][e];
-        sm.rho[et][e] = sm.rho[et - 1][e];
-        sm.eps[et][e] = sm.eps[et - 1][e];
-        sm.phi[et][e] = T(2) * c.phi_top - sm.phi[et - 1][e];
-        sm.p[et][e] = sm.p[et - 1][e];
-        sm.S[et][e] = sm.S[et - 1][e];
-    }
+    fill_ghosts<T, BY>(sm, c, y0, ny, tid);
     __syncthreads();
     if (!own) return;
-
-    const int ex = tx + 1, ey = ty + 1;
-    // ---- a2: stencils ----------------------------------------------------
-    T gpsix, gpsiy, grhox, grhoy, gepsx, gepsy, gphix, gphiy, gpx, gpy, gSx, gSy;
-    grad_s<T, 34>(sm.psi, ex, ey, gpsix, gpsiy);
-    const T lpsi = lap_s<T, 34>(sm.psi, ex, ey);
-    grad_s<T, 34>(sm.rho, ex, ey, grhox, grhoy);
-    grad_s<T, 34>(sm.eps, ex, ey, gepsx, gepsy);
-    grad_s<T, 34>(sm.phi, ex, ey, gphix, gphiy);
-    const T lphi = lap_s<T, 34>(sm.phi, ex, ey);
-    grad_s<T, 34>(sm.p, ex, ey, gpx, gpy);
-    grad_s<T, 34>(sm.S, ex, ey, gSx, gSy);
-
-    // ---- a3: forces (Eq. Fs with the chemical potential of Sec. 2; Eq. Fe)
-    const T ps = m.psi;
-    const T muc = T(4) * c.beta * (ps - T(1)) * (ps - T(0)) * (ps - T(0.5)) - c.kappa * lpsi;
-    const T Fsx = muc * gpsix, Fsy = muc * gpsiy;
-    const T Ex = -gphix, Ey = -gphiy;
-    const T qv = -(gepsx * gphix + gepsy * gphiy + m.eps * lphi);
-    const T E2 = Ex * Ex + Ey * Ey;
-    const T Fex = qv * Ex - T(0.5) * E2 * gepsx;
-    const T Fey = qv * Ey - T(0.5) * E2 * gepsy;
-    const T Fx = Fsx + Fex, Fy = Fsy + Fey;
-
-    // ---- a4: flow macros (Sec. 3.2) ---------------------------------------
-    // sum_i c_i h_i in the order of i (zero terms skipped)
-    T jx = h[1];
-    jx = jx - h[3];
-    jx = jx + h[5];
-    jx = jx - h[6];
-    jx = jx - h[7];
-    jx = jx + h[8];
-    T jy = h[2];
-    jy = jy - h[4];
-    jy = jy + h[5];
-    jy = jy + h[6];
-    jy = jy - h[7];
-    jy = jy - h[8];
-    const T r = m.rho;
-    const T mu = chi(m.fs, ps, c.mu), kth = chi(m.fs, ps, c.kth);
-    const T sig = chi(m.fs, ps, c.sig), cp = chi(m.fs, ps, c.cp);
-    const T mdot = c.one_m_rsl * (m.fs - fs_prev);                 // Eq. (ns1)
-    const T usx = (jx + T(0.5) * Fx) / r, usy = (jy + T(0.5) * Fy) / r;
-    const T fx = m.fs * (T(0) - usx), fy = m.fs * (T(0) - usy);    // u_s = 0
-    const T ux = usx + T(0.5) * fx, uy = usy + T(0.5) * fy;        // Eq. (Computed_u)
-    const T rfx = r * fx, rfy = r * fy;
-    const T Sn = r * mdot + (ux * grhox + uy * grhoy);
-    const T Ftx = Fx - gpx + cs2<T>() * grhox + cs2<T>() * gSx;
-    const T Fty = Fy - gpy + cs2<T>() * grhoy + cs2<T>() * gSy;
-    const T uF = ux * Ftx + uy * Fty;
-    const T R0 = w9<T>(0) * (Sn - uF / cs2<T>());
-    const T tau_h = mu / r / cs2<T>() + T(0.5);
-    T sh_ = T(0);
-#pragma unroll
-    for (int i = 1; i < 9; i++) sh_ += h[i];
-    const T p = cs2<T>() / (T(1) - w9<T>(0)) * (sh_ + T(0.5) * Sn + tau_h * R0 + r * s_i<T>(0, ux, uy));
-
-    // ---- collisions + push streaming (a5-a9) -------------------------------
-    // destinations of the push: wrapped columns and rows computed once
-    const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
-    const long long r0 = (long long)y * io.pitch;
-    auto dest = [&](int i, int cxv, int cyv) -> long long {
-        (void)i;
-        const long long row = cyv < 0 ? r0 - io.pitch : (cyv > 0 ? r0 + io.pitch : r0);
-        return row + (cxv < 0 ? xm : (cxv > 0 ? xp : x));
-    };
-    Refs<T> ro;                               // destination references (half storage)
-
-    // a7: flow
-    {
-        const T pre = T(1) - T(1) / (T(2) * tau_h);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-            const T cF = cdot<T>(CX[i], CY[i], Ftx, Fty);
-            const T Ri = w9<T>(i) * (Sn + cdot<T>(CX[i], CY[i], Fx + rfx, Fy + rfy) / cs2<T>() +
-                                     (cu * cF - cs2<T>() * uF) / (cs2<T>() * cs2<T>()));
-            const T heq = ((i == 0) ? p / cs2<T>() * (w9<T>(0) - T(1)) : p / cs2<T>() * w9<T>(i)) +
-                          r * s_i<T>(i, ux, uy);
-            const T post = h[i] - (h[i] - heq) / tau_h + pre * Ri;
-            const int yt = y + CY[i];
-            if (yt < 0 || yt >= ny)
-                Pol<S, T>::st(io.fhg_out + (9 + OPP9[i]) * P + k, post, T(0), sh.h_scale);
-            else
-                Pol<S, T>::st(io.fhg_out + (9 + i) * P + dest(i, CX[i], CY[i]), post, T(0), sh.h_scale);
-        }
-    }
-    // a5: phase field
-    {
-        const T pux = ps * ux, puy = ps * uy;
-        const T dtx = pux - pux_prev;         // Euler d_t(psi u) (Sec. 3.4)
-        const T dty = puy - puy_prev;
-        pux_prev = pux;
-        puy_prev = puy;
-        // interface normal, regularised where grad psi vanishes (Sec. 2)
-        const T gn = sqrt(gpsix * gpsix + gpsiy * gpsiy);
-        const T nxv = gpsix / (gn + T(1e-4)), nyv = gpsiy / (gn + T(1e-4));
-        const T lam = T(4) * ps * (T(1) - ps) / c.W;
-        const T pre = T(1) - T(1) / (T(2) * c.tau_f);
-        const T ax = dtx + cs2<T>() * lam * nxv;
-        const T ay = dty + cs2<T>() * lam * nyv;
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-            const T feq = w9<T>(i) * ps * (T(1) + cu / cs2<T>());
-            const T Fi = w9<T>(i) * cdot<T>(CX[i], CY[i], ax, ay) / cs2<T>() + w9<T>(i) * ps * mdot;
-            const T post = f[i] - (f[i] - feq) / c.tau_f + pre * Fi;
-            const int yt = y + CY[i];
-            if (yt < 0 || yt >= ny) {
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st(io.fhg_out + OPP9[i] * P + k, post, ro.f[OPP9[i]], sh.f_scale);
-            } else {
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st(io.fhg_out + i * P + dest(i, CX[i], CY[i]), post, ro.f[i], sh.f_scale);
-            }
-        }
-    }
-    // a8: enthalpy (Sec. 3.3)
-    T Qn;
-    {
-        const T tau_g = kth / (r * c.Cref * cs2<T>()) + T(0.5);
-        Qn = r * cp * m.T_ * mdot;
-        const T uu = ux * ux + uy * uy;
-        const T pre = T(1) - T(1) / (T(2) * tau_g);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-            T geq;
-            if (i == 0)
-                geq = m.H - c.Cref * m.T_ + w9<T>(0) * cp * m.T_ * (c.Cref / cp - uu / (T(2) * cs2<T>()));
-            else
-                geq = w9<T>(i) * cp * m.T_ *
-                      (c.Cref / cp + cu / cs2<T>() + (cu * cu - cs2<T>() * uu) / (T(2) * cs2<T>() * cs2<T>()));
-            const T post = g[i] - (g[i] - geq) / tau_g + pre * (w9<T>(i) * Qn);
-            const int yt = y + CY[i];
-            if (yt < 0) {            // cold wall: anti-bounce-back to C_p,ref T_w
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st(io.fhg_out + (18 + OPP9[i]) * P + k,
-                              -post + T(2) * w9<T>(i) * c.Cref_Tw, ro.g[OPP9[i]], sh.g_scale);
-            } else if (yt >= ny) {   // top wall: adiabatic bounce-back
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st(io.fhg_out + (18 + OPP9[i]) * P + k, post, ro.g[OPP9[i]], sh.g_scale);
-            } else {
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st(io.fhg_out + (18 + i) * P + dest(i, CX[i], CY[i]), post, ro.g[i], sh.g_scale);
-            }
-        }
-    }
-    // a6: potential (Sec. 3.4), one sweep inside the fused step
-    {
-        const T tau_l = sig / cs2<T>() + T(0.5);
-#pragma unroll
-        for (int i = 0; i < 5; i++) {
-            const T leq = (i == 0) ? (w5<T>(0) - T(1)) * m.phi : w5<T>(i) * m.phi;
-            const T post = l[i] - (l[i] - leq) / tau_l;
-            const int yt = y + CY5[i];
-            if (yt < 0 || yt >= ny) {   // electrodes: anti-bounce-back
-                const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st(io.l_out + OPP5[i] * P + k, -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]],
-                              sh.l_scale);
-            } else {
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st(io.l_out + i * P + dest(i, CX5[i], CY5[i]), post, ro.l[i], sh.l_scale);
-            }
-        }
-    }
-    // previous-step fields for the next step
-    io.aux_out[AUX_FS * P + k] = A(m.fs);
-    io.aux_out[AUX_MDOT * P + k] = A(mdot);
-    io.aux_out[AUX_Q * P + k] = A(Qn);
-    io.aux_out[AUX_PUX * P + k] = A(pux_prev);
-    io.aux_out[AUX_PUY * P + k] = A(puy_prev);
-    io.aux_out[AUX_P * P + k] = A(p);
-    io.aux_out[AUX_S * P + k] = A(Sn);
-    if (io.write_sigma) io.sigma[k] = A(sig);
+    const RegPops<T> PS{f, g, l, h};
+    step_cell<S, T, A, BY>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev);
 }
 
 template <typename S, typename T, typename A, int BY>
@@ -559,6 +594,222 @@ __global__ void __launch_bounds__(32 * BY) k_step(DevState s, int cur, int lcur,
     __shared__ TileSmem<T, BY> sm;
     const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
     step_tile<S, T, A, BY>(io, c, sh, sm, blockIdx.x * 32, blockIdx.y * BY);
+}
+
+// ---------------------------------------------------------------------------
+// TMA form of the step.  One thread issues three 3-D tensor loads that bring
+// the tile and its one-cell halo, for all 32 population planes and the 7
+// auxiliary planes, into shared memory (completion tracked by an mbarrier);
+// the cells then read their populations from shared memory, so no global
+// load sits in a thread's register file and the halo needs no second pass.
+// The box starts 16 bytes left of the tile so its x origin is aligned; the
+// out-of-range columns that the periodic wrap needs (x = -1 and x = nx) are
+// filled from the opposite edge with plain loads.
+// ---------------------------------------------------------------------------
+template <typename S, typename A, int BY>
+struct TmaGeom {
+    static constexpr int PADX = 16 / int(sizeof(S));   // box x origin = x0 - PADX (16-byte aligned)
+    static constexpr int BW = 32 + 2 * PADX;             // box width (population planes)
+    static constexpr int PADA = 16 / int(sizeof(A));
+    static constexpr int BWA = 32 + 2 * PADA;            // box width (auxiliary planes)
+    static constexpr int BH = BY + 2;                    // box height
+    static constexpr int PL = BW * BH;                   // elements per population plane
+    static constexpr int PLA = BWA * BH;                 // elements per auxiliary plane
+    static constexpr size_t fhg_bytes = size_t(PL) * NFHG * sizeof(S);
+    static constexpr size_t l_bytes = size_t(PL) * (NPOP - NFHG) * sizeof(S);
+    static constexpr size_t aux_bytes = size_t(PLA) * NAUX * sizeof(A);
+    static constexpr size_t l_off = (fhg_bytes + 127) / 128 * 128;
+    static constexpr size_t aux_off = (l_off + l_bytes + 127) / 128 * 128;
+    static constexpr size_t total = aux_off + aux_bytes;
+    static constexpr uint32_t tx_bytes = uint32_t(fhg_bytes + l_bytes + aux_bytes);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+}
+// Bounded wait on phase `parity`: true once complete, false after the limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *map, int c0, int c1, int c2, uint32_t mb) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mb)
+        : "memory");
+}
+
+// Populations of one cell read from the shared-memory box.
+template <typename S, typename T>
+struct BoxPops {
+    const S *f_;   // plane 0 of f at the cell
+    const S *l_;   // plane 0 of l at the cell
+    int pl;        // elements per plane
+    Refs<T> rf;
+    float fsc, gsc, hsc, lsc;
+    __device__ __forceinline__ T f(int i) const { return Pol<S, T>::ld(f_ + i * pl, rf.f[i], fsc); }
+    __device__ __forceinline__ T h(int i) const { return Pol<S, T>::ld(f_ + (9 + i) * pl, T(0), hsc); }
+    __device__ __forceinline__ T g(int i) const { return Pol<S, T>::ld(f_ + (18 + i) * pl, rf.g[i], gsc); }
+    __device__ __forceinline__ T l(int i) const { return Pol<S, T>::ld(l_ + i * pl, rf.l[i], lsc); }
+};
+
+constexpr int TMA_WAIT_LIMIT = 1 << 22;   // try_wait rounds before the step gives up
+
+template <typename S, typename T, typename A, int BY>
+__device__ __forceinline__ void step_tile_tma(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
+                                              TileSmem<T, BY> &sm, unsigned char *dsm, unsigned long long *mbar,
+                                              const void *mF, const void *mL, const void *mA, int x0, int y0,
+                                              unsigned int *err) {
+    using G = TmaGeom<S, A, BY>;
+    __shared__ int s_ok;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    const int nx = io.nx, ny = io.ny;
+    const long long P = io.plane;
+    // tensor-copy destinations must be 128-byte aligned; the launch
+    // requests 128 bytes of slack for this
+    unsigned char *base = dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u);
+    S *bF = reinterpret_cast<S *>(base);
+    S *bL = reinterpret_cast<S *>(base + G::l_off);
+    A *bA = reinterpret_cast<A *>(base + G::aux_off);
+    const uint32_t mb = smem_u32(mbar);
+    if (tid == 0) mbar_init(mb, 1);
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(mb, G::tx_bytes);
+        tma_load_3d(smem_u32(bF), mF, x0 - G::PADX, y0 - 1, 0, mb);
+        tma_load_3d(smem_u32(bL), mL, x0 - G::PADX, y0 - 1, 0, mb);
+        tma_load_3d(smem_u32(bA), mA, x0 - G::PADA, y0 - 1, 0, mb);
+        s_ok = mbar_wait(mb, 0, TMA_WAIT_LIMIT) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) {
+        // report, then let the copies in flight land (bounded) before the
+        // block's shared memory is released
+        if (tid == 0) {
+            atomicOr(err, 1u);
+            mbar_wait(mb, 0, TMA_WAIT_LIMIT);
+        }
+        return;
+    }
+    mbar_wait(mb, 0, TMA_WAIT_LIMIT);      // complete: acquire the bytes for this thread
+
+    // periodic wrap: box columns of x = -1 and x = nx come from the far edge
+    {
+        // only the first tile holds x = -1 and only the last one x = nx; the
+        // latter sits at box column nx - x0 + pad <= 32 + pad < box width
+        const bool first = (x0 == 0), last = (nx - x0) <= 32;
+        const int nfix = (NPOP + NAUX) * G::BH;
+        for (int side = 0; side < 2; side++) {
+            if (side == 0 ? !first : !last) continue;
+            const int col = side == 0 ? G::PADX - 1 : nx - x0 + G::PADX;
+            const int cola = side == 0 ? G::PADA - 1 : nx - x0 + G::PADA;
+            const int srcx = side == 0 ? nx - 1 : 0;
+            for (int t = tid; t < nfix; t += 32 * BY) {
+                const int q = t / G::BH, r = t % G::BH;
+                const int yy = y0 - 1 + r;
+                if (yy < 0 || yy >= ny) continue;
+                const long long kk = (long long)yy * io.pitch + srcx;
+                if (q < NFHG)
+                    bF[q * G::PL + r * G::BW + col] = io.fhg_in[q * P + kk];
+                else if (q < NPOP)
+                    bL[(q - NFHG) * G::PL + r * G::BW + col] = io.l_in[(q - NFHG) * P + kk];
+                else
+                    bA[(q - NPOP) * G::PLA + r * G::BWA + cola] = io.aux_in[(q - NPOP) * P + kk];
+            }
+        }
+    }
+    __syncthreads();
+
+    const float fsc = 1.0f / sh.f_scale, gsc = 1.0f / sh.g_scale, lsc = 1.0f / sh.l_scale;
+    const float hsc = 1.0f / sh.h_scale;
+    // macros of one extended-tile cell (ex, ey) from the box
+    auto ext_macros = [&](int ex, int ey, int yy, Macro<T> &mm, T &fs_p) {
+        const int o = ey * G::BW + ex - 1 + G::PADX;
+        const int oa = ey * G::BWA + ex - 1 + G::PADA;
+        BoxPops<S, T> bp{bF + o, bL + o, G::PL, {}, fsc, gsc, hsc, lsc};
+        make_refs<S, T>(bp.rf, sh, c, yy, ny);
+        T f[9], g[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            f[i] = bp.f(i);
+            g[i] = bp.g(i);
+        }
+        T l1234 = T(0);
+#pragma unroll
+        for (int i = 1; i < 5; i++) l1234 += bp.l(i);
+        fs_p = T(bA[AUX_FS * G::PLA + oa]);
+        local_macros(f, g, l1234, fs_p, T(bA[AUX_MDOT * G::PLA + oa]), T(bA[AUX_Q * G::PLA + oa]), c, mm);
+        sm.psi[ey][ex] = mm.psi;
+        sm.rho[ey][ex] = mm.rho;
+        sm.eps[ey][ex] = mm.eps;
+        sm.phi[ey][ex] = mm.phi;
+        sm.p[ey][ex] = T(bA[AUX_P * G::PLA + oa]);
+        sm.S[ey][ex] = T(bA[AUX_S * G::PLA + oa]);
+    };
+
+    // ---- phase 1: own cell, then the halo ring --------------------------
+    const int xg = x0 + tx, y = y0 + ty;
+    const bool own = (xg < nx) && (y < ny);
+    Macro<T> m;
+    T fs_prev = T(0);
+    if (y < ny) ext_macros(tx + 1, ty + 1, y, m, fs_prev);
+    constexpr int NRING = 2 * 34 + 2 * BY;
+    for (int r = tid; r < NRING; r += 32 * BY) {
+        int ex, ey;
+        if (r < 34) {
+            ex = r; ey = 0;
+        } else if (r < 68) {
+            ex = r - 34; ey = BY + 1;
+        } else if (r < 68 + BY) {
+            ex = 0; ey = r - 68 + 1;
+        } else {
+            ex = 33; ey = r - 68 - BY + 1;
+        }
+        const int hy = y0 - 1 + ey;
+        if (hy < 0 || hy >= ny) continue;
+        Macro<T> mr;
+        T fsr;
+        ext_macros(ex, ey, hy, mr, fsr);
+    }
+    __syncthreads();
+    fill_ghosts<T, BY>(sm, c, y0, ny, tid);
+    __syncthreads();
+    if (!own) return;
+    const int o = (ty + 1) * G::BW + tx + G::PADX;
+    const int oa = (ty + 1) * G::BWA + tx + G::PADA;
+    BoxPops<S, T> PS{bF + o, bL + o, G::PL, {}, fsc, gsc, hsc, lsc};
+    make_refs<S, T>(PS.rf, sh, c, y, ny);
+    step_cell<S, T, A, BY>(io, c, sh, sm, PS, tx, ty, xg, y, m, fs_prev, T(bA[AUX_PUX * G::PLA + oa]),
+                           T(bA[AUX_PUY * G::PLA + oa]));
+}
+
+template <typename S, typename T, typename A, int BY>
+__global__ void __launch_bounds__(32 * BY) k_step_tma(DevState s, int cur, int lcur, int write_sigma, Consts<T> c,
+                                                      Shift sh, const __grid_constant__ CUtensorMap mF,
+                                                      const __grid_constant__ CUtensorMap mL,
+                                                      const __grid_constant__ CUtensorMap mA) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ TileSmem<T, BY> sm;
+    __shared__ __align__(8) unsigned long long mbar;
+    const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
+    step_tile_tma<S, T, A, BY>(io, c, sh, sm, dsm, &mbar, &mF, &mL, &mA, blockIdx.x * 32, blockIdx.y * BY, s.err);
 }
 
 // Batched form: blocks walk a flat list of tiles of many instances.  The
@@ -1029,6 +1280,42 @@ __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shi
         default: return cudaErrorInvalidValue;                                                              \
         }                                                                                                   \
         return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    size_t tma_smem_##SUFFIX(int tile_rows) {                                                              \
+        switch (tile_rows) {                                                                                \
+        case 4: return TmaGeom<S, A, 4>::total + 128;                                                       \
+        case 8: return TmaGeom<S, A, 8>::total + 128;                                                       \
+        case 16: return TmaGeom<S, A, 16>::total + 128;                                                     \
+        default: return 0;                                                                                  \
+        }                                                                                                   \
+    }                                                                                                       \
+    template <int BY>                                                                                       \
+    static cudaError_t launch_tma_by_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,        \
+                                              const Consts<T> &c, const Shift &sh, const TmaMaps &m,        \
+                                              cudaStream_t st) {                                            \
+        static bool ready = false;                                                                          \
+        if (!ready) {                                                                                       \
+            cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, T, A, BY>,                                   \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,               \
+                                                 (int)TmaGeom<S, A, BY>::total + 128);                      \
+            if (e != cudaSuccess) return e;                                                                 \
+            ready = true;                                                                                   \
+        }                                                                                                   \
+        dim3 grid((s.nx + 31) / 32, (s.ny + BY - 1) / BY);                                                  \
+        k_step_tma<S, T, A, BY><<<grid, dim3(32, BY), TmaGeom<S, A, BY>::total + 128, st>>>(                \
+            s, cur, lcur, write_sigma, c, sh, m.fhg[cur], m.l[lcur], m.aux[cur]);                           \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    cudaError_t launch_step_tma_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,             \
+                                         const void *consts, const Shift &sh, const TmaMaps &m,             \
+                                         cudaStream_t st) {                                                 \
+        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
+        switch (m.by) {                                                                                     \
+        case 4: return launch_tma_by_##SUFFIX<4>(s, cur, lcur, write_sigma, c, sh, m, st);                  \
+        case 8: return launch_tma_by_##SUFFIX<8>(s, cur, lcur, write_sigma, c, sh, m, st);                  \
+        case 16: return launch_tma_by_##SUFFIX<16>(s, cur, lcur, write_sigma, c, sh, m, st);                \
+        default: return cudaErrorInvalidValue;                                                              \
+        }                                                                                                   \
     }                                                                                                       \
     cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, const void *consts, const Shift &sh,    \
                                       cudaStream_t st) {                                                    \

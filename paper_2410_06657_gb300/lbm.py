@@ -14,6 +14,7 @@ import numpy as np
 from . import build as _build
 
 FP64, FP32, FP16S = 0, 1, 2
+STEP_TMA, STEP_DIRECT = 0, 1
 OK, ERR_BADPARAM, ERR_OOM, ERR_DIVERGED, ERR_CUDA, ERR_STATE = 0, -1, -2, -3, -4, -5
 
 FIELD_IDS = {
@@ -28,7 +29,7 @@ EXPORTS = [
     "lbm_last_error", "lbm_create", "lbm_init_droplet", "lbm_init_psi", "lbm_step",
     "lbm_observables", "lbm_observables_async", "lbm_observables_fetch", "lbm_get_field",
     "lbm_set_field", "lbm_state_bytes", "lbm_export_state", "lbm_import_state",
-    "lbm_step_count", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
+    "lbm_step_count", "lbm_configure", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tile_rows", "lbm_batch_destroy",
 ]
 
@@ -102,6 +103,7 @@ def load(build_if_missing: bool = True):
     L.lbm_state_bytes.argtypes = [vp]
     L.lbm_export_state.argtypes = [vp, vp, C.c_size_t]
     L.lbm_import_state.argtypes = [vp, vp, C.c_size_t]
+    L.lbm_configure.argtypes = [vp, C.c_int32, C.c_int32]
     L.lbm_step_count.restype = C.c_int64
     L.lbm_step_count.argtypes = [vp]
     L.lbm_destroy.argtypes = [vp]
@@ -176,6 +178,9 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+    def configure(self, variant=STEP_TMA, tile_rows=8):
+        _check(load().lbm_configure(self._h, int(variant), int(tile_rows)))
 
     def init_droplet(self, R, xc, yc, presolve=0):
         _check(load().lbm_init_droplet(self._h, float(R), float(xc), float(yc), int(presolve)))

@@ -183,6 +183,29 @@ def test_fp64_full_size_production_lattice(lbm):
     assert_fp64(worst(g, o))
 
 
+@pytest.mark.parametrize("nx,ny", [(4, 3), (37, 19), (64, 32), (100, 45)])
+def test_tma_and_direct_step_kernels_agree_bitwise(lbm, nx, ny):
+    """The tensor-load step (halo'd tile brought into shared memory, wrap
+    columns patched from the far edge) and the direct-load step compute the
+    same FP64 bits for every tile height, on ragged and tiny lattices."""
+    R = 0.3 * min(nx, 2 * ny)
+    p = W.params(nx=nx, ny=ny, R0=R, theta_deg=105.0, precision=W.FP64, k_e=2)
+    xc, yc = W.sessile_center(nx, R, 105.0)
+    psi = W.droplet_psi(nx, ny, R, xc, yc, p["W"])
+    ref = lbm.Simulation(p)
+    ref.configure(lbm.STEP_DIRECT, 8)
+    ref.init_psi(psi, 4)
+    ref.step(40)
+    want = {n: ref.get(n) for n in STORED}
+    for rows in (4, 8, 16):
+        s = lbm.Simulation(p)
+        s.configure(lbm.STEP_TMA, rows)
+        s.init_psi(psi, 4)
+        s.step(40)
+        for n in STORED:
+            assert np.array_equal(s.get(n), want[n]), (rows, n)
+
+
 def test_graph_replay_and_single_launches_agree_bitwise(lbm):
     """lbm_step(64) replays a captured graph; 64 single steps must give the
     same bits."""
@@ -203,10 +226,14 @@ def test_graph_replay_and_single_launches_agree_bitwise(lbm):
 # Batched form: same bits as stepping alone
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", [W.FP64, W.FP32])
-def test_batch_equals_members_stepped_alone(lbm, prec):
-    """Uneven members, autotuned tile height, a member that starts at the
-    other parity; FP64 results are bitwise those of stepping alone."""
+@pytest.mark.parametrize("prec,tile", [(W.FP64, 0), (W.FP32, 8), (W.FP32, 0)])
+def test_batch_equals_members_stepped_alone(lbm, prec, tile):
+    """Uneven members, a member that starts at the other parity.  FP64
+    results are bitwise those of stepping alone whatever the tile shape (no
+    FMA contraction, same operation order).  FP32 with the single-instance
+    tile height must agree to FP32 rounding; with an autotuned height the
+    compiler may contract differently, and the gap after 45 steps is held to
+    the FP32 field bar (1e-4 with natural-scale floors)."""
     cases = [(96, 48, 15.0, 80.0, 0.1, 2.0, 5.0), (64, 32, 10.0, 110.0, 0.4, 0.5, 2.0),
              (37, 21, 6.0, 95.0, 0.0, 5.0, 9.5)]
     sims, alone = [], []
@@ -219,19 +246,20 @@ def test_batch_equals_members_stepped_alone(lbm, prec):
             lst.append(s)
     alone[1].step(1)          # members may start at different parities
     sims[1].step(1)
-    b = lbm.Batch(sims, tile_rows=0)
+    b = lbm.Batch(sims, tile_rows=tile)
     assert b.tile_rows in (4, 8, 16)
     b.step(45)               # one graph of 32 steps + 13 single launches
     for s in alone:
         s.step(45)
+    tol = 1e-5 if tile else 1e-4
     for s, a in zip(sims, alone):
         assert s.t == a.t
         fl = floors(s.params)
         for n in STORED:
-            if prec == W.FP64:      # no FMA contraction: identical bits
+            if prec == W.FP64:
                 assert np.array_equal(s.get(n), a.get(n)), n
-            else:                   # tile shapes may contract differently
-                assert normwise(s.get(n), a.get(n), fl.get(n, 0.0)) <= 1e-5, n
+            else:
+                assert normwise(s.get(n), a.get(n), fl.get(n, 0.0)) <= tol, n
 
 
 # --------------------------------------------------------------------------
