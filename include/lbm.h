@@ -242,10 +242,12 @@ int lbm_import_state(struct lbm_handle *h, const void *host, size_t bytes);
 /*
  * Step kernel selection (tuning and testing; results do not depend on it in
  * FP64, and differ only by rounding in FP32):
- *   variant LBM_STEP_TMA (default): tensor-memory-accelerator loads bring
- *     each tile with its halo into shared memory;
- *   variant LBM_STEP_DIRECT: every thread loads its cell from global memory.
- *   tile_rows: 4, 8 (default) or 16 lattice rows per 32-column tile.
+ *   variant LBM_STEP_DIRECT (default): every thread loads its cell from
+ *     global memory and stashes it in shared memory for the collisions;
+ *   variant LBM_STEP_TMA: tensor-memory-accelerator loads bring each tile
+ *     with its halo into shared memory (faster on large lattices).
+ *   tile_rows: 4, 8 or 16 lattice rows per 32-column tile (default 4 in
+ *     single precision, 8 in FP64).
  * Errors: BADPARAM (unknown variant or height, NULL).
  */
 enum { LBM_STEP_TMA = 0, LBM_STEP_DIRECT = 1 };

@@ -287,6 +287,16 @@ __device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Co
 }
 
 // Population sources for step_cell.
+template <typename T, int BY>
+struct StashPops {            // own cell's populations stashed in shared memory
+    const T (*q)[BY][32];
+    int ty, tx;
+    __device__ __forceinline__ T f(int i) const { return q[i][ty][tx]; }
+    __device__ __forceinline__ T h(int i) const { return q[9 + i][ty][tx]; }
+    __device__ __forceinline__ T g(int i) const { return q[18 + i][ty][tx]; }
+    __device__ __forceinline__ T l(int i) const { return q[27 + i][ty][tx]; }
+};
+
 template <typename T>
 struct RegPops {
     const T (&f_)[9];
@@ -515,7 +525,8 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
 
 template <typename S, typename T, typename A, int BY>
 __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Consts<T> &c,
-                                          const Shift &sh, TileSmem<T, BY> &sm, int x0, int y0) {
+                                          const Shift &sh, TileSmem<T, BY> &sm, T (*stash)[BY][32], int x0,
+                                          int y0) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
     const int nx = io.nx, ny = io.ny;
@@ -552,6 +563,15 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
 #pragma unroll
         for (int i = 1; i < 5; i++) l1234 += l[i];
         local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
+        // keep the populations for phase 2 in shared memory, not registers
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            stash[i][ty][tx] = f[i];
+            stash[9 + i][ty][tx] = h[i];
+            stash[18 + i][ty][tx] = g[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 5; i++) stash[27 + i][ty][tx] = l[i];
         sm.psi[ty + 1][tx + 1] = m.psi;
         sm.rho[ty + 1][tx + 1] = m.rho;
         sm.eps[ty + 1][tx + 1] = m.eps;
@@ -584,16 +604,37 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     fill_ghosts<T, BY>(sm, c, y0, ny, tid);
     __syncthreads();
     if (!own) return;
-    const RegPops<T> PS{f, g, l, h};
+    const StashPops<T, BY> PS{stash, ty, tx};
     step_cell<S, T, A, BY>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev);
 }
 
+// Blocks per SM the single-precision step asks the register allocator for:
+// with 4-row tiles, 7 blocks (28 warps) hold a 512 x 256 lattice in one wave.
+template <typename T, int BY>
+constexpr int step_min_blocks() {
+    return sizeof(T) == 8 ? 1 : (BY == 4 ? 7 : (BY == 8 ? 3 : 1));
+}
+
+template <typename T, int BY>
+constexpr size_t stash_bytes() { return size_t(NPOP) * BY * 32 * sizeof(T); }
+
+// Opt a step kernel into its dynamic shared memory once per process.
+template <typename K>
+inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes, bool &done) {
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 template <typename S, typename T, typename A, int BY>
-__global__ void __launch_bounds__(32 * BY) k_step(DevState s, int cur, int lcur, int write_sigma,
-                                                  Consts<T> c, Shift sh) {
+__global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_step(DevState s, int cur, int lcur,
+                                                                             int write_sigma, Consts<T> c, Shift sh) {
     __shared__ TileSmem<T, BY> sm;
+    extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
+    T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
     const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
-    step_tile<S, T, A, BY>(io, c, sh, sm, blockIdx.x * 32, blockIdx.y * BY);
+    step_tile<S, T, A, BY>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
 }
 
 // ---------------------------------------------------------------------------
@@ -827,11 +868,13 @@ __device__ __forceinline__ int find_item(const BatchItem *__restrict__ items, in
 }
 
 template <typename S, typename T, typename A, int BY>
-__global__ void __launch_bounds__(32 * BY) k_batch_step(const BatchItem *__restrict__ items,
+__global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_batch_step(const BatchItem *__restrict__ items,
                                                         const Consts<T> *__restrict__ consts,
                                                         int n_items, int total_tiles, int flip_cur,
                                                         int flip_l) {
     __shared__ TileSmem<T, BY> sm;
+    extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
+    T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
     __shared__ int s_item;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
         if (threadIdx.x == 0 && threadIdx.y == 0) s_item = find_item<false>(items, n_items, t);
@@ -840,7 +883,7 @@ __global__ void __launch_bounds__(32 * BY) k_batch_step(const BatchItem *__restr
         const int local = t - it.tile_begin;
         const int bx = local % it.tiles_x, by = local / it.tiles_x;
         const StepIO<S, T, A> io = make_io<S, T, A>(it.s, it.cur ^ flip_cur, it.lcur ^ flip_l, it.write_sigma);
-        step_tile<S, T, A, BY>(io, consts[s_item], it.sh, sm, bx * 32, by * BY);
+        step_tile<S, T, A, BY>(io, consts[s_item], it.sh, sm, stash, bx * 32, by * BY);
         __syncthreads();
     }
 }
@@ -1273,12 +1316,27 @@ __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shi
                                      const void *consts, const Shift &sh, int tile_rows, cudaStream_t st) { \
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
         dim3 grid((s.nx + 31) / 32, (s.ny + tile_rows - 1) / tile_rows);                                   \
+        static bool r4 = false, r8 = false, r16 = false;                                                    \
+        cudaError_t e = cudaSuccess;                                                                        \
         switch (tile_rows) {                                                                                \
-        case 4: k_step<S, T, A, 4><<<grid, dim3(32, 4), 0, st>>>(s, cur, lcur, write_sigma, c, sh); break; \
-        case 8: k_step<S, T, A, 8><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, write_sigma, c, sh); break; \
-        case 16: k_step<S, T, A, 16><<<grid, dim3(32, 16), 0, st>>>(s, cur, lcur, write_sigma, c, sh); break; \
+        case 4:                                                                                             \
+            e = allow_dynamic_smem(k_step<S, T, A, 4>, stash_bytes<T, 4>(), r4);                            \
+            if (e == cudaSuccess)                                                                           \
+                k_step<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
+            break;                                                                                          \
+        case 8:                                                                                             \
+            e = allow_dynamic_smem(k_step<S, T, A, 8>, stash_bytes<T, 8>(), r8);                            \
+            if (e == cudaSuccess)                                                                           \
+                k_step<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
+            break;                                                                                          \
+        case 16:                                                                                            \
+            e = allow_dynamic_smem(k_step<S, T, A, 16>, stash_bytes<T, 16>(), r16);                         \
+            if (e == cudaSuccess)                                                                           \
+                k_step<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
+            break;                                                                                          \
         default: return cudaErrorInvalidValue;                                                              \
         }                                                                                                   \
+        if (e != cudaSuccess) return e;                                                                     \
         return cudaGetLastError();                                                                          \
     }                                                                                                       \
     size_t tma_smem_##SUFFIX(int tile_rows) {                                                              \

@@ -10,13 +10,28 @@ cudaError_t launch_batch_step_f32(const BatchItem *items_dev, const void *consts
     const Consts<float> *c = reinterpret_cast<const Consts<float> *>(consts_dev);
     switch (tile_rows) {
     case 4:
-        k_batch_step<float, float, float, 4><<<grid, dim3(32, 4), 0, st>>>(items_dev, c, n_items, total_tiles, flip_cur, flip_l);
+        {
+            static bool ready = false;
+            cudaError_t e = allow_dynamic_smem(k_batch_step<float, float, float, 4>, stash_bytes<float, 4>(), ready);
+            if (e != cudaSuccess) return e;
+        }
+        k_batch_step<float, float, float, 4><<<grid, dim3(32, 4), stash_bytes<float, 4>(), st>>>(items_dev, c, n_items, total_tiles, flip_cur, flip_l);
         break;
     case 8:
-        k_batch_step<float, float, float, 8><<<grid, dim3(32, 8), 0, st>>>(items_dev, c, n_items, total_tiles, flip_cur, flip_l);
+        {
+            static bool ready = false;
+            cudaError_t e = allow_dynamic_smem(k_batch_step<float, float, float, 8>, stash_bytes<float, 8>(), ready);
+            if (e != cudaSuccess) return e;
+        }
+        k_batch_step<float, float, float, 8><<<grid, dim3(32, 8), stash_bytes<float, 8>(), st>>>(items_dev, c, n_items, total_tiles, flip_cur, flip_l);
         break;
     case 16:
-        k_batch_step<float, float, float, 16><<<grid, dim3(32, 16), 0, st>>>(items_dev, c, n_items, total_tiles, flip_cur, flip_l);
+        {
+            static bool ready = false;
+            cudaError_t e = allow_dynamic_smem(k_batch_step<float, float, float, 16>, stash_bytes<float, 16>(), ready);
+            if (e != cudaSuccess) return e;
+        }
+        k_batch_step<float, float, float, 16><<<grid, dim3(32, 16), stash_bytes<float, 16>(), st>>>(items_dev, c, n_items, total_tiles, flip_cur, flip_l);
         break;
     default:
         return cudaErrorInvalidValue;

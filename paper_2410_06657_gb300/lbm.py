@@ -179,7 +179,7 @@ class Simulation:
         except Exception:
             pass
 
-    def configure(self, variant=STEP_TMA, tile_rows=8):
+    def configure(self, variant=STEP_DIRECT, tile_rows=4):
         _check(load().lbm_configure(self._h, int(variant), int(tile_rows)))
 
     def init_droplet(self, R, xc, yc, presolve=0):
