@@ -253,6 +253,39 @@ int lbm_import_state(struct lbm_handle *h, const void *host, size_t bytes);
 enum { LBM_STEP_TMA = 0, LBM_STEP_DIRECT = 1 };
 int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
 
+/*
+ * Observables of a caller-held state, allocating nothing.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, such as code
+ * embedded in a runtime that has already reserved the device memory for its
+ * own pool, or a latency-critical loop in which an allocation would
+ * synchronise the device.  It runs the same reduction as lbm_observables
+ * with its scratch (block partial sums, crossing candidates) in a
+ * fixed-size array that the library keeps in device memory on every GPU
+ * that loads it (about 720 KB, held until the process exits).
+ *   p     parameters of the state (host struct, read during the call)
+ *   pop   device array of 32 planes (f 0-8, h 0-8, g 0-8, l 0-4) of the
+ *         precision's storage type, each ny rows of `pitch` elements, x
+ *         fastest -- for example the body of an lbm_export_state snapshot
+ *         after its 64-byte header (pitch = nx rounded up to 32)
+ *   aux   device array of the 7 auxiliary planes that follow `pop` in such a
+ *         snapshot (FP64 for LBM_FP64, else FP32), same plane layout
+ *   pitch elements per row (>= nx); step: step number reported in out
+ *   out   device lbm_obs written by the call; its t_fre is read and kept, so
+ *         set t_fre = -1 before the first call on a run
+ *   stream cudaStream_t on which the work is enqueued (the call returns
+ *         without waiting; synchronise before reading out)
+ * Limits: ny <= 4096 and at most 20480 tiles of 32 x 8 cells (about 5.2
+ * million cells); larger lattices return LBM_ERR_BADPARAM.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one array and clears what must start at zero, so calls
+ * whose work overlaps on the GPU (several streams at once) race; serialise
+ * them.  Errors: BADPARAM (NULL pointers, invalid parameters, size limits),
+ * CUDA (launch failure).
+ */
+int lbm_observables_noalloc(const lbm_params *p, const void *pop, const void *aux, int32_t pitch,
+                            int64_t step, lbm_obs *out, void *stream);
+
 /* Steps taken since the last init.  */
 int64_t lbm_step_count(const struct lbm_handle *h);
 

@@ -146,6 +146,20 @@ int obs_grid_blocks(int nx, int ny) { return ((nx + 31) / 32) * ((ny + 7) / 8); 
 
 int lbm::obs_blocks(int nx, int ny) { return obs_grid_blocks(nx, ny); }
 
+void lbm::set_last_error(const std::string &msg) { g_err = msg; }
+
+// Validation and derived constants for entry points that hold no handle.
+int lbm::derive_for_noalloc(const lbm_params *p, Consts<double> *cd, Consts<float> *cf, Shift *sh,
+                            const char **why) {
+    if (const char *w = validate(*p)) {
+        *why = w;
+        return LBM_ERR_BADPARAM;
+    }
+    derive(*p, *cd);
+    *cf = cast_consts<float>(*cd);
+    *sh = make_shift(*p, *cd);
+    return LBM_OK;
+}
 
 struct lbm_handle {
     lbm_params P;

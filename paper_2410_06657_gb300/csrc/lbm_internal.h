@@ -7,6 +7,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/lbm.h"
 
 namespace lbm {
@@ -104,6 +106,8 @@ LBM_DECLARE_LAUNCHERS(f32)
 LBM_DECLARE_LAUNCHERS(f16s)
 
 int obs_blocks(int nx, int ny);   // grid size of the observables kernel
+void set_last_error(const std::string &msg);
+int derive_for_noalloc(const lbm_params *p, Consts<double> *cd, Consts<float> *cf, Shift *sh, const char **why);
 
 // Batched stepping: one launch over a work list of (instance, tile) pairs.
 // cur/lcur are the member's parities when the list was built; launches

@@ -1,0 +1,145 @@
+// Observables of a caller-held state with no device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs inside a runtime which
+// has already reserved the device's memory for its own pool (an allocation
+// here would fail or fragment that pool), and latency-critical loops where
+// cudaMalloc/cudaFree would synchronise the device and stall other streams.
+// For them the reduction behind lbm_observables is offered with its scratch
+// (block partial sums and the crossing candidates) in a fixed-size array in
+// the module's own device memory.  Every GPU that loads the library holds
+// this array until the process exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "lbm_internal.h"
+
+namespace {
+
+constexpr int kMaxBlocks = 20480;   // 32 x 8 tiles of the reduction grid
+constexpr int kMaxNy = 4096;        // rows (one crossing slot per row)
+
+constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kPartBytes = al256(size_t(kMaxBlocks) * 4 * sizeof(double));
+constexpr size_t kMaxvBytes = al256(size_t(2 + kMaxNy) * sizeof(unsigned long long));
+constexpr size_t kMinvBytes = al256(size_t(1 + kMaxNy) * sizeof(unsigned long long));
+constexpr size_t kU32Bytes = al256(size_t(kMaxNy + 2) * sizeof(unsigned int));
+constexpr size_t kScratchBytes = kPartBytes + kMaxvBytes + kMinvBytes + kU32Bytes;   // about 720 KB
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void *g_scratch_dev[kMaxDevices] = {};   // device address of the array, per device
+
+}  // namespace
+
+
+
+// The scratch array.  In host code this name is only a stand-in for the
+// symbol: its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_obs_scratch[kScratchBytes];
+
+namespace {
+
+// Device address of the scratch array on the current device (looked up once
+// per device, with that device current).
+int scratch_address(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        lbm::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        lbm::set_last_error("device ordinal beyond the supported range");
+        return LBM_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_dev[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_obs_scratch);
+        if (e != cudaSuccess || !p) {
+            lbm::set_last_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            return LBM_ERR_CUDA;
+        }
+        g_scratch_dev[dev] = p;
+    }
+    *out = g_scratch_dev[dev];
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, const void *aux, int32_t pitch,
+                                       int64_t step, lbm_obs *out, void *stream) {
+    using namespace lbm;
+    if (!p || !pop || !aux || !out) {
+        set_last_error("NULL argument");
+        return LBM_ERR_BADPARAM;
+    }
+    Consts<double> cd;
+    Consts<float> cf;
+    Shift sh;
+    const char *why = nullptr;
+    if (derive_for_noalloc(p, &cd, &cf, &sh, &why) != LBM_OK) {
+        set_last_error(why ? why : "invalid parameters");
+        return LBM_ERR_BADPARAM;
+    }
+    const int nblocks = obs_blocks(p->nx, p->ny);
+    if (p->ny > kMaxNy || nblocks > kMaxBlocks) {
+        set_last_error("lattice beyond the fixed scratch: at most 4096 rows and 20480 tiles of 32 x 8 cells");
+        return LBM_ERR_BADPARAM;
+    }
+    if (pitch < p->nx) {
+        set_last_error("pitch must be at least nx");
+        return LBM_ERR_BADPARAM;
+    }
+    void *base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc != LBM_OK) return rc;
+
+    unsigned char *b = static_cast<unsigned char *>(base);
+    ObsScratch ws;
+    ws.partials = reinterpret_cast<double *>(b);
+    ws.maxv = reinterpret_cast<unsigned long long *>(b + kPartBytes);
+    ws.minv = reinterpret_cast<unsigned long long *>(b + kPartBytes + kMaxvBytes);
+    ws.rowany = reinterpret_cast<unsigned int *>(b + kPartBytes + kMaxvBytes + kMinvBytes);
+    ws.bad = ws.rowany + p->ny;
+    ws.obs = out;
+    ws.nblocks = nblocks;
+
+    DevState s;
+    s.pop[0] = s.pop[1] = const_cast<void *>(pop);
+    s.aux[0] = s.aux[1] = const_cast<void *>(aux);
+    s.sigma = nullptr;
+    s.err = nullptr;
+    s.nx = p->nx;
+    s.ny = p->ny;
+    s.pitch = pitch;
+    s.plane = (long long)pitch * p->ny;
+
+    Scalars sc;
+    sc.step = step;
+    sc.alpha_l = p->alpha_l;
+    sc.R0 = p->R0;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the array keeps the previous call's contents: reset what must start
+    // at the identity of its reduction (0 for maxima and flags, all ones for
+    // minima)
+    cudaError_t e = cudaMemsetAsync(ws.maxv, 0x00, (size_t)(2 + p->ny) * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.minv, 0xFF, (size_t)(1 + p->ny) * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.rowany, 0x00, (size_t)(p->ny + 2) * sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        switch (p->precision) {
+        case LBM_FP64: e = launch_obs_f64(s, 0, 0, &cd, sh, ws, sc, st); break;
+        case LBM_FP32: e = launch_obs_f32(s, 0, 0, &cf, sh, ws, sc, st); break;
+        default: e = launch_obs_f16s(s, 0, 0, &cf, sh, ws, sc, st); break;
+        }
+    }
+    if (e != cudaSuccess) {
+        set_last_error(std::string("observables launch: ") + cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}

@@ -30,7 +30,7 @@ EXPORTS = [
     "lbm_observables", "lbm_observables_async", "lbm_observables_fetch", "lbm_get_field",
     "lbm_set_field", "lbm_state_bytes", "lbm_export_state", "lbm_import_state",
     "lbm_step_count", "lbm_configure", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
-    "lbm_batch_tile_rows", "lbm_batch_destroy",
+    "lbm_batch_tile_rows", "lbm_batch_destroy", "lbm_observables_noalloc",
 ]
 
 
