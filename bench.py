@@ -1,7 +1,8 @@
 """Benchmark of the fused electrofreezing LB step on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                [--precision f32|f64|f16s] [--workload production|precision]
+                [--precision f32|f64|f16s]
+                [--workload production|precision|batched|serving]
 
 A step is one pass of the whole hot path over the lattice: the fused
 collide-and-stream launch (local macros, stencils, forces, four collisions,
@@ -353,6 +354,109 @@ def run_gpu(args, world, rank, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Batched workload: 64 uneven instances, one launch per step, against the same
+# instances advanced one after another
+# ---------------------------------------------------------------------------
+
+def run_batched(args, world, rank, local):
+    import torch
+    from paper_2410_06657_gb300 import lbm, workloads as W
+
+    torch.cuda.set_device(local)
+    lbm.load()
+    stream = torch.cuda.current_stream()
+    prec = W.PRECISIONS[args.precision]
+    items = W.batched(n=64, seed=2410066570 + rank, precision=prec)
+    sims = []
+    for it in items:
+        p = it["params"]
+        s = lbm.Simulation(p, stream)
+        xc, yc = W.sessile_center(p["nx"], it["R"], p["theta_deg"])
+        s.init_droplet(it["R"], xc, yc, 0)
+        sims.append(s)
+    cells = sum(it["params"]["nx"] * it["params"]["ny"] for it in items)
+    K = args.steps
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    # plain: each instance's K steps (graph-replayed) one after another
+    for s in sims:
+        s.step(args.warmup)
+    t_plain = timed(lambda: [s.step(K) for s in sims])
+    batch = lbm.Batch(sims, stream, tile_rows=0)
+    batch.step(args.warmup)
+    barrier(world)
+    t_batch = timed(lambda: batch.step(K))
+    t_batch = reduce_max(t_batch, world)
+    v_batch = world * cells * K / t_batch / 1e6
+    v_plain = cells * K / t_plain / 1e6
+    if rank == 0:
+        print(json.dumps({
+            "metric": "MLUPS", "value": v_batch, "unit": "MLUPS", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "batched: 64 instances, sizes uniform in {128x64 .. 512x256}, seeded "
+                                   "CaE/R/S/theta/Ste draws", "cells": cells,
+                       "tile_rows": batch.tile_rows, "l2": "state (1.2 GB in FP32) larger than L2"},
+            "plain_one_after_another": {"value": v_plain, "unit": "MLUPS"},
+            "batched_over_plain": v_batch / v_plain,
+            "gpu_launches": K * (1 if items[0]["params"]["k_e"] == 1 else items[0]["params"]["k_e"]),
+        }))
+
+
+# ---------------------------------------------------------------------------
+# Serving: Poisson arrivals, continuous batching, p50/p99 time to result
+# ---------------------------------------------------------------------------
+
+def run_serving(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2410_06657_gb300 import lbm, workloads as W
+    from paper_2410_06657_gb300.serving import Request, Server
+
+    torch.cuda.set_device(local)
+    lbm.load()
+    stream = torch.cuda.current_stream()
+    prec = W.PRECISIONS[args.precision]
+    stream_items = W.serving_stream(n=args.requests, rate=20.0, seed=2410066571 + rank,
+                                    max_ny=args.max_ny, precision=prec)
+    reqs = []
+    for it in stream_items:
+        p = it["params"]
+        xc, yc = W.sessile_center(p["nx"], it["R"], p["theta_deg"])
+        reqs.append(Request(id=it["id"], arrival=it["arrival"], params=p, R=it["R"], xc=xc, yc=yc))
+    srv = Server(int(args.budget_gb * 1e9), stream, chunk=200)
+    barrier(world)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    wall = reduce_max(time.perf_counter() - t0, world)
+    lat = np.array([r.latency for r in res])
+    lu = srv.lattice_updates
+    bpl = BYTES_PER_LU[args.precision]
+    if rank == 0:
+        print(json.dumps({
+            "metric": "MLUPS", "value": world * lu / wall / 1e6, "unit": "MLUPS", "n_gpus": world,
+            "steps": int(lu), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"serving: {args.requests} Poisson arrivals at 20/s, sizes up to "
+                                   f"{2 * args.max_ny}x{args.max_ny}, run to frozen fraction 0.99",
+                       "budget_gb": args.budget_gb, "chunk": 200},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "hbm_gbs_algorithmic": lu * bpl / wall / 1e9,
+            "all_frozen": bool(all(r.frozen for r in res)), "wall_s": wall,
+        }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,7 +464,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16s"])
-    ap.add_argument("--workload", default="production", choices=["production", "precision"])
+    ap.add_argument("--workload", default="production",
+                    choices=["production", "precision", "batched", "serving"])
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--max-ny", type=int, default=128)
+    ap.add_argument("--budget-gb", type=float, default=80.0)
     ap.add_argument("--obs-every", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -370,6 +478,12 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batched":
+        run_batched(args, world, rank, local)
+        return
+    if args.workload == "serving":
+        run_serving(args, world, rank, local)
         return
     run_gpu(args, world, rank, local)
 

@@ -412,18 +412,40 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         return row + (cxv < 0 ? xm : (cxv > 0 ? xp : x));
     };
 
+    // Single precision evaluates the collisions in an algebraically equal
+    // form with the 1/c_s^2 factors folded (c_s^2 = 1/3) and the shared
+    // terms hoisted; double precision keeps the printed operation order.
+    constexpr bool FAST = sizeof(T) == 4;
+    const T uu_ = ux * ux + uy * uy;
+    const T B15 = T(1.5) * uu_;                    // u.u / (2 c_s^2)
+
     // a7: flow
     {
         const T pre = T(1) - T(1) / (T(2) * tau_h);
+        const T om = T(1) / tau_h;
+        const T A3 = T(3) * p;                      // p / c_s^2
+        const T S3 = Sn - T(3) * uF;                // S - u.F~ / c_s^2
+        const T Gx = Fx + rfx, Gy = Fy + rfy;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-            const T cF = cdot<T>(CX[i], CY[i], Ftx, Fty);
-            const T Ri = w9<T>(i) * (Sn + cdot<T>(CX[i], CY[i], Fx + rfx, Fy + rfy) / cs2<T>() +
-                                     (cu * cF - cs2<T>() * uF) / (cs2<T>() * cs2<T>()));
-            const T heq = ((i == 0) ? p / cs2<T>() * (w9<T>(0) - T(1)) : p / cs2<T>() * w9<T>(i)) +
-                          r * s_i<T>(i, ux, uy);
-            const T post = PS.h(i) - (PS.h(i) - heq) / tau_h + pre * Ri;
+            T post;
+            if constexpr (FAST) {
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                const T cF = cdot<T>(CX[i], CY[i], Ftx, Fty);
+                const T cG = cdot<T>(CX[i], CY[i], Gx, Gy);
+                const T t = cu * (T(3) + T(4.5) * cu);   // c.u/c_s^2 + (c.u)^2/(2 c_s^4)
+                const T heq = (i == 0) ? w9<T>(0) * (A3 - r * B15) - A3 : w9<T>(i) * (A3 + r * (t - B15));
+                const T Ri = w9<T>(i) * (S3 + T(3) * cG + T(9) * cu * cF);
+                post = PS.h(i) + om * (heq - PS.h(i)) + pre * Ri;
+            } else {
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                const T cF = cdot<T>(CX[i], CY[i], Ftx, Fty);
+                const T Ri = w9<T>(i) * (Sn + cdot<T>(CX[i], CY[i], Fx + rfx, Fy + rfy) / cs2<T>() +
+                                         (cu * cF - cs2<T>() * uF) / (cs2<T>() * cs2<T>()));
+                const T heq = ((i == 0) ? p / cs2<T>() * (w9<T>(0) - T(1)) : p / cs2<T>() * w9<T>(i)) +
+                              r * s_i<T>(i, ux, uy);
+                post = PS.h(i) - (PS.h(i) - heq) / tau_h + pre * Ri;
+            }
             const int yt = y + CY[i];
             if (yt < 0 || yt >= ny)
                 Pol<S, T>::st(io.fhg_out + (9 + OPP9[i]) * P + k, post, T(0), sh.h_scale);
@@ -445,12 +467,22 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         const T pre = T(1) - T(1) / (T(2) * c.tau_f);
         const T ax = dtx + cs2<T>() * lam * nxv;
         const T ay = dty + cs2<T>() * lam * nyv;
+        const T om = T(1) / c.tau_f;
+        const T pmd = ps * mdot;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-            const T feq = w9<T>(i) * ps * (T(1) + cu / cs2<T>());
-            const T Fi = w9<T>(i) * cdot<T>(CX[i], CY[i], ax, ay) / cs2<T>() + w9<T>(i) * ps * mdot;
-            const T post = PS.f(i) - (PS.f(i) - feq) / c.tau_f + pre * Fi;
+            T post;
+            if constexpr (FAST) {
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                const T feq = w9<T>(i) * ps * (T(1) + T(3) * cu);
+                const T Fi = w9<T>(i) * (T(3) * cdot<T>(CX[i], CY[i], ax, ay) + pmd);
+                post = PS.f(i) + om * (feq - PS.f(i)) + pre * Fi;
+            } else {
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                const T feq = w9<T>(i) * ps * (T(1) + cu / cs2<T>());
+                const T Fi = w9<T>(i) * cdot<T>(CX[i], CY[i], ax, ay) / cs2<T>() + w9<T>(i) * ps * mdot;
+                post = PS.f(i) - (PS.f(i) - feq) / c.tau_f + pre * Fi;
+            }
             const int yt = y + CY[i];
             if (yt < 0 || yt >= ny) {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
@@ -466,18 +498,28 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     {
         const T tau_g = kth / (r * c.Cref * cs2<T>()) + T(0.5);
         Qn = r * cp * m.T_ * mdot;
-        const T uu = ux * ux + uy * uy;
+        const T uu = uu_;
         const T pre = T(1) - T(1) / (T(2) * tau_g);
+        const T om = T(1) / tau_g;
+        const T CT = c.Cref * m.T_, cpT = cp * m.T_;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-            T geq;
-            if (i == 0)
-                geq = m.H - c.Cref * m.T_ + w9<T>(0) * cp * m.T_ * (c.Cref / cp - uu / (T(2) * cs2<T>()));
-            else
-                geq = w9<T>(i) * cp * m.T_ *
-                      (c.Cref / cp + cu / cs2<T>() + (cu * cu - cs2<T>() * uu) / (T(2) * cs2<T>() * cs2<T>()));
-            const T post = PS.g(i) - (PS.g(i) - geq) / tau_g + pre * (w9<T>(i) * Qn);
+            T post;
+            if constexpr (FAST) {
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                const T t = cu * (T(3) + T(4.5) * cu);
+                const T geq = (i == 0) ? m.H - CT + w9<T>(0) * (CT - cpT * B15) : w9<T>(i) * (CT + cpT * (t - B15));
+                post = PS.g(i) + om * (geq - PS.g(i)) + pre * (w9<T>(i) * Qn);
+            } else {
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                T geq;
+                if (i == 0)
+                    geq = m.H - c.Cref * m.T_ + w9<T>(0) * cp * m.T_ * (c.Cref / cp - uu / (T(2) * cs2<T>()));
+                else
+                    geq = w9<T>(i) * cp * m.T_ *
+                          (c.Cref / cp + cu / cs2<T>() + (cu * cu - cs2<T>() * uu) / (T(2) * cs2<T>() * cs2<T>()));
+                post = PS.g(i) - (PS.g(i) - geq) / tau_g + pre * (w9<T>(i) * Qn);
+            }
             const int yt = y + CY[i];
             if (yt < 0) {            // cold wall: anti-bounce-back to C_p,ref T_w
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
@@ -495,10 +537,15 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     // a6: potential (Sec. 3.4), one sweep inside the fused step
     {
         const T tau_l = sig / cs2<T>() + T(0.5);
+        const T om = T(1) / tau_l;
 #pragma unroll
         for (int i = 0; i < 5; i++) {
             const T leq = (i == 0) ? (w5<T>(0) - T(1)) * m.phi : w5<T>(i) * m.phi;
-            const T post = PS.l(i) - (PS.l(i) - leq) / tau_l;
+            T post;
+            if constexpr (FAST)
+                post = PS.l(i) + om * (leq - PS.l(i));
+            else
+                post = PS.l(i) - (PS.l(i) - leq) / tau_l;
             const int yt = y + CY5[i];
             if (yt < 0 || yt >= ny) {   // electrodes: anti-bounce-back
                 const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
@@ -1105,6 +1152,7 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
 
     const int x = x0 + tx, y = y0 + ty;
     double v_psi = 0.0, v_H = 0.0, v_fs = 0.0, v_q = 0.0;
+    unsigned int rowbits = 0u;                // this lane's row flags (one warp = one row)
     if (x < nx && y < ny) {
         const int ex = tx + 1, ey = ty + 1;
         Macro<T> m;
@@ -1121,7 +1169,7 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         const double a = s_psi[ey][ex];
         // column crossing (height): psi(y) >= 1/2 > psi(y+1)
         if (a >= 0.5) {
-            atomicOr(&ws.rowany[y], 1u);
+            rowbits |= 1u;
             if (y == ny - 1) {
                 atomic_max_pos(&ws.maxv[0], (double)ny);
             } else {
@@ -1133,14 +1181,14 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
                 const double bl = s_psi[ey][ex - 1];
                 if (bl < 0.5) {
                     atomic_min_pos(&ws.minv[1 + y], (x - 1) + (0.5 - bl) / (a - bl));
-                    atomicOr(&ws.rowany[y], 2u);
+                    rowbits |= 2u;
                 }
             }
             if (x + 1 < nx) {
                 const double br = s_psi[ey][ex + 1];
                 if (br < 0.5) {
                     atomic_max_pos(&ws.maxv[2 + y], x + (a - 0.5) / (a - br));
-                    atomicOr(&ws.rowany[y], 4u);
+                    rowbits |= 4u;
                 }
             }
         }
@@ -1157,6 +1205,13 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
                 }
             }
         }
+    }
+    // row flags: OR across the warp (all lanes share the row), one atomic
+    {
+        unsigned int b = rowbits;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
+        if (tx == 0 && b && y < ny) atomicOr(&ws.rowany[y], b);
     }
     // block sums (FP64, fixed shuffle order)
     double v[4] = {v_psi, v_H, v_fs, v_q};

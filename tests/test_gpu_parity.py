@@ -44,15 +44,15 @@ def normwise(a, b, floor=0.0):
 def floors(p):
     """Natural scales: a fraction is O(1); T is measured against the imposed
     temperature difference; H against the latent heat; p and h against the
-    drop's Laplace pressure; S and psi u against the size they reach once
-    freezing drives a flow (1e-5).  At t = 0, T = T_m and f_s = 0
+    drop's Laplace pressure; S against rho (1 - rho_s/rho_l) df_s/dt at a
+    moving front (1e-3) and psi u against the flow freezing drives (1e-5).  At t = 0, T = T_m and f_s = 0
     everywhere, so max|field| alone would divide last-bit differences of the
     initial tanh profile by ~1e-17."""
     dT = max(p["T_m"] - p["T_w"], 1e-3)
     L = p["cp_l"] * dT / p["Ste"]
     lap = p["gamma"] / p["R0"]          # Laplace pressure of the drop
     return {"psi": 1.0, "fsolid": 1.0, "fs_prev": 1.0, "T": dT, "H": L, "g": L,
-            "mdot_prev": 1e-2, "Q_prev": 1e-2, "p": lap, "h": lap, "S": 1e-5,
+            "mdot_prev": 1e-2, "Q_prev": 1e-2, "p": lap, "h": lap, "S": 1e-3,
             "psiux": 1e-5, "psiuy": 1e-5}
 
 
