@@ -189,19 +189,28 @@ struct lbm_handle {
     int gsteps = 0;
 };
 
+// A device work list of (member, tile) pairs with its launch shape and a
+// graph cache per starting parity.
+struct WorkList {
+    BatchItem *items_dev = nullptr;
+    void *consts_dev = nullptr;
+    int n = 0;
+    int total_tiles = 0, total_sweep_tiles = 0, grid = 0, sweep_grid = 0;
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+};
+
 struct lbm_batch {
     std::vector<lbm_handle *> m;
     int precision = LBM_FP32;
     int k_e = 1;
+    int tile_rows = 8;
     cudaStream_t st = nullptr;
-    BatchItem *items_dev = nullptr;
-    void *consts_dev = nullptr;
-    int total_tiles = 0, total_sweep_tiles = 0, tile_rows = 8, grid = 0, sweep_grid = 0;
-    int flips = 0;                 // steps since the list was built (mod 2 matters)
+    WorkList all;                  // every member: one launch per step
+    std::vector<WorkList> groups;  // members grouped so each group's state fits in L2
+    int flips = 0;                 // steps since the lists were built (mod 2 matters)
     int lflips = 0;                // potential sweeps since then
-    std::vector<int> cur0, lcur0;  // member parities when the list was built
+    std::vector<int> cur0, lcur0;  // member parities when the lists were built
     cudaStream_t cap = nullptr;    // private capture stream
-    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 };
 
 namespace {
@@ -712,56 +721,73 @@ int lbm_configure(lbm_handle *h, int32_t variant, int32_t tile_rows) {
 // Batches
 // ---------------------------------------------------------------------------
 
-static cudaError_t batch_launch_steps(lbm_batch *b, int64_t n, cudaStream_t st) {
+static cudaError_t list_steps(const lbm_batch *b, const WorkList &L, int64_t n, int &flips, int &lflips,
+                              cudaStream_t st) {
     for (int64_t j = 0; j < n; j++) {
-        const int fc = b->flips & 1, fl = b->lflips & 1;
+        const int fc = flips & 1, fl = lflips & 1;
         cudaError_t e;
         switch (b->precision) {
         case LBM_FP64:
-            e = launch_batch_step_f64(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_tiles, b->tile_rows,
-                                      b->grid, fc, fl, st);
+            e = launch_batch_step_f64(L.items_dev, L.consts_dev, L.n, L.total_tiles, b->tile_rows, L.grid, fc, fl, st);
             break;
         case LBM_FP32:
-            e = launch_batch_step_f32(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_tiles, b->tile_rows,
-                                      b->grid, fc, fl, st);
+            e = launch_batch_step_f32(L.items_dev, L.consts_dev, L.n, L.total_tiles, b->tile_rows, L.grid, fc, fl, st);
             break;
         default:
-            e = launch_batch_step_f16s(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_tiles,
-                                       b->tile_rows, b->grid, fc, fl, st);
+            e = launch_batch_step_f16s(L.items_dev, L.consts_dev, L.n, L.total_tiles, b->tile_rows, L.grid, fc, fl, st);
             break;
         }
         if (e != cudaSuccess) return e;
-        b->flips++;
-        b->lflips++;
-        for (int s = 1; s < b->k_e; s++) {
-            const int fl2 = b->lflips & 1;
+        flips++;
+        lflips++;
+        for (int sw = 1; sw < b->k_e; sw++) {
+            const int fl2 = lflips & 1;
             switch (b->precision) {
             case LBM_FP64:
-                e = launch_batch_sweep_f64(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_sweep_tiles,
-                                           b->sweep_grid, fl2, st);
+                e = launch_batch_sweep_f64(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2, st);
                 break;
             case LBM_FP32:
-                e = launch_batch_sweep_f32(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_sweep_tiles,
-                                           b->sweep_grid, fl2, st);
+                e = launch_batch_sweep_f32(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2, st);
                 break;
             default:
-                e = launch_batch_sweep_f16s(b->items_dev, b->consts_dev, (int)b->m.size(), b->total_sweep_tiles,
-                                            b->sweep_grid, fl2, st);
+                e = launch_batch_sweep_f16s(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2, st);
                 break;
             }
             if (e != cudaSuccess) return e;
-            b->lflips++;
+            lflips++;
         }
     }
     return cudaSuccess;
 }
 
-static int batch_build(lbm_batch *b, int tile_rows) {
-    std::vector<BatchItem> items(b->m.size());
+static void free_list(WorkList &L) {
+    for (int a = 0; a < 2; a++)
+        for (int c = 0; c < 2; c++)
+            if (L.gexec[a][c]) {
+                cudaGraphExecDestroy(L.gexec[a][c]);
+                L.gexec[a][c] = nullptr;
+            }
+    cudaFree(L.items_dev);
+    cudaFree(L.consts_dev);
+    L.items_dev = nullptr;
+    L.consts_dev = nullptr;
+}
+
+// Device bytes a member's step touches (both copies of every plane).
+static size_t member_state_bytes(const lbm_handle *h) {
+    const size_t sb = storage_bytes(h->P.precision), ab = aux_bytes(h->P.precision);
+    return (size_t)h->s.plane * (2 * NPOP * sb + 2 * NAUX * ab + ab);
+}
+
+static int build_list(lbm_batch *b, const std::vector<int> &idx, int tile_rows, int sms, WorkList &L) {
+    free_list(L);
+    std::vector<BatchItem> items(idx.size());
+    const size_t csz = b->precision == LBM_FP64 ? sizeof(Consts<double>) : sizeof(Consts<float>);
+    std::vector<char> cs(csz * idx.size());
     int tiles = 0, sweeps = 0;
-    for (size_t i = 0; i < b->m.size(); i++) {
-        lbm_handle *h = b->m[i];
-        BatchItem &it = items[i];
+    for (size_t j = 0; j < idx.size(); j++) {
+        lbm_handle *h = b->m[idx[j]];
+        BatchItem &it = items[j];
         it.s = h->s;
         it.cur = h->cur;
         it.lcur = h->lcur;
@@ -774,35 +800,92 @@ static int batch_build(lbm_batch *b, int tile_rows) {
         it.sweep_begin = sweeps;
         sweeps += it.tiles_x * ((h->P.ny + 7) / 8);
         it.sh = h->sh;
+        std::memcpy(cs.data() + csz * j, consts_for(h), csz);
     }
+    L.n = (int)idx.size();
+    L.total_tiles = tiles;
+    L.total_sweep_tiles = sweeps;
+    const int per_sm = tile_rows == 16 ? 2 : (tile_rows == 8 ? 4 : 8);
+    L.grid = std::min(tiles, sms * per_sm);
+    L.sweep_grid = std::min(sweeps, sms * 8);
+    CK(cudaMalloc(&L.items_dev, items.size() * sizeof(BatchItem)));
+    CK(cudaMalloc(&L.consts_dev, cs.size()));
+    CK(cudaMemcpyAsync(L.items_dev, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, b->st));
+    CK(cudaMemcpyAsync(L.consts_dev, cs.data(), cs.size(), cudaMemcpyHostToDevice, b->st));
+    return LBM_OK;
+}
+
+// Build the all-member list and the L2-sized groups (consecutive members
+// whose combined state stays within half of the L2 cache).
+static int batch_build(lbm_batch *b, int tile_rows) {
+    int dev = 0, sms = 0, l2 = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    b->tile_rows = tile_rows;
+    std::vector<int> all(b->m.size());
+    for (size_t i = 0; i < all.size(); i++) all[i] = (int)i;
+    int rc = build_list(b, all, tile_rows, sms, b->all);
+    if (rc) return rc;
+    for (WorkList &g : b->groups) free_list(g);
+    b->groups.clear();
+    const size_t budget = (size_t)l2 / 2;
+    std::vector<int> cur;
+    size_t used = 0;
+    for (size_t i = 0; i <= b->m.size(); i++) {
+        const bool end = (i == b->m.size());
+        const size_t need = end ? 0 : member_state_bytes(b->m[i]);
+        if (!cur.empty() && (end || used + need > budget)) {
+            b->groups.emplace_back();
+            if ((rc = build_list(b, cur, tile_rows, sms, b->groups.back()))) return rc;
+            cur.clear();
+            used = 0;
+        }
+        if (!end) {
+            cur.push_back((int)i);
+            used += need;
+        }
+    }
+    CK(cudaStreamSynchronize(b->st));
     b->cur0.resize(b->m.size());
     b->lcur0.resize(b->m.size());
     for (size_t i = 0; i < b->m.size(); i++) {
         b->cur0[i] = b->m[i]->cur;
         b->lcur0[i] = b->m[i]->lcur;
     }
-    for (int a = 0; a < 2; a++)
-        for (int c = 0; c < 2; c++)
-            if (b->gexec[a][c]) {
-                cudaGraphExecDestroy(b->gexec[a][c]);
-                b->gexec[a][c] = nullptr;
-            }
-    b->total_tiles = tiles;
-    b->total_sweep_tiles = sweeps;
-    b->tile_rows = tile_rows;
-    cudaFree(b->items_dev);
-    b->items_dev = nullptr;
-    CK(cudaMalloc(&b->items_dev, items.size() * sizeof(BatchItem)));
-    CK(cudaMemcpyAsync(b->items_dev, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, b->st));
-    CK(cudaStreamSynchronize(b->st));
     b->flips = 0;
     b->lflips = 0;
-    int dev = 0, sms = 0, per_sm = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    per_sm = tile_rows == 16 ? 2 : (tile_rows == 8 ? 4 : 8);
-    b->grid = std::min(tiles, sms * per_sm);
-    b->sweep_grid = std::min(sweeps, sms * 8);
+    return LBM_OK;
+}
+
+// n steps of one list starting at parities (flips, lflips); long runs replay
+// a captured graph of G steps (G even: both parities return to the start).
+static int run_list(lbm_batch *b, WorkList &L, int64_t n, int flips, int lflips) {
+    const int G = 32;
+    while (n >= G) {
+        cudaGraphExec_t &ex = L.gexec[flips & 1][lflips & 1];
+        if (!ex) {
+            int f = flips, lf = lflips;
+            CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = list_steps(b, L, G, f, lf, b->cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+            if (e != cudaSuccess) return cuda_fail(e, "graph capture of the batch step");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ex = nullptr;
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+        }
+        CK(cudaGraphLaunch(ex, b->st));
+        flips += G;
+        lflips += G * b->k_e;
+        n -= G;
+    }
+    cudaError_t e = list_steps(b, L, n, flips, lflips, b->st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch step");
     return LBM_OK;
 }
 
@@ -830,19 +913,8 @@ int lbm_batch_create(lbm_handle *const *members, int32_t n, void *stream, int32_
         delete b;
         return fail(LBM_ERR_CUDA, "stream creation failed");
     }
-    // per-member constants in the arithmetic type
-    const size_t csz = b->precision == LBM_FP64 ? sizeof(Consts<double>) : sizeof(Consts<float>);
-    std::vector<char> cs(csz * n);
-    for (int i = 0; i < n; i++) std::memcpy(cs.data() + csz * i, consts_for(members[i]), csz);
-    if (cudaMalloc(&b->consts_dev, cs.size()) != cudaSuccess) {
-        cudaGetLastError();
-        delete b;
-        return fail(LBM_ERR_OOM, "batch constants allocation failed");
-    }
     int rc = LBM_OK;
-    if (cudaMemcpy(b->consts_dev, cs.data(), cs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-        rc = fail(LBM_ERR_CUDA, "batch constants copy failed");
-    if (!rc && tile_rows == 0) {
+    if (tile_rows == 0) {
         // Autotune: time each tile height on the members' own data.  The step
         // reads one copy and writes the other, so re-running it without
         // flipping parities leaves every member's state unchanged.
@@ -855,12 +927,13 @@ int lbm_batch_create(lbm_handle *const *members, int32_t n, void *stream, int32_
             if ((rc = batch_build(b, rows))) break;
             const int k_e = b->k_e;
             b->k_e = 1;
-            cudaError_t e = batch_launch_steps(b, 1, b->st);          // warm-up
-            b->flips = 0; b->lflips = 0;
+            int f = 0, lf = 0;
+            cudaError_t e = list_steps(b, b->all, 1, f, lf, b->st);       // warm-up
             cudaEventRecord(e0, b->st);
             for (int r = 0; r < 5 && e == cudaSuccess; r++) {
-                e = batch_launch_steps(b, 1, b->st);
-                b->flips = 0; b->lflips = 0;
+                f = 0;
+                lf = 0;
+                e = list_steps(b, b->all, 1, f, lf, b->st);
             }
             cudaEventRecord(e1, b->st);
             b->k_e = k_e;
@@ -898,33 +971,20 @@ int lbm_batch_step(lbm_batch *b, int64_t n) {
         }
     }
     const int64_t total = n;
-    const int G = 32;   // graph length: even, so every parity returns to its start
-    while (n >= G) {
-        cudaGraphExec_t &ex = b->gexec[b->flips & 1][b->lflips & 1];
-        if (!ex) {
-            const int f0 = b->flips, l0 = b->lflips;
-            CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = batch_launch_steps(b, G, b->cap);
-            cudaGraph_t g = nullptr;
-            cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
-            b->flips = f0;
-            b->lflips = l0;
-            if (e != cudaSuccess) return cuda_fail(e, "graph capture of the batch step");
-            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(&ex, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) {
-                ex = nullptr;
-                return cuda_fail(e, "cudaGraphInstantiate");
-            }
+    // Members are independent: for longer runs each L2-sized group advances
+    // all n steps while its state is resident, instead of streaming every
+    // member's state through HBM on every step.
+    if (n >= 8 && b->groups.size() > 1) {
+        for (WorkList &g : b->groups) {
+            int rc = run_list(b, g, n, b->flips, b->lflips);
+            if (rc) return rc;
         }
-        CK(cudaGraphLaunch(ex, b->st));
-        b->flips += G;
-        b->lflips += G * b->k_e;
-        n -= G;
+    } else {
+        int rc = run_list(b, b->all, n, b->flips, b->lflips);
+        if (rc) return rc;
     }
-    cudaError_t e = batch_launch_steps(b, n, b->st);
-    if (e != cudaSuccess) return cuda_fail(e, "batch step");
+    b->flips += (int)(n & 1);
+    b->lflips += (int)((n * b->k_e) & 1);
     for (lbm_handle *h : b->m) {
         h->cur ^= (int)(total & 1);
         h->lcur ^= (int)((total * h->P.k_e) & 1);
@@ -938,12 +998,9 @@ int32_t lbm_batch_tile_rows(const lbm_batch *b) { return b ? b->tile_rows : 0; }
 void lbm_batch_destroy(lbm_batch *b) {
     if (!b) return;
     cudaStreamSynchronize(b->st);
-    for (int a = 0; a < 2; a++)
-        for (int c = 0; c < 2; c++)
-            if (b->gexec[a][c]) cudaGraphExecDestroy(b->gexec[a][c]);
+    free_list(b->all);
+    for (WorkList &g : b->groups) free_list(g);
     if (b->cap) cudaStreamDestroy(b->cap);
-    cudaFree(b->items_dev);
-    cudaFree(b->consts_dev);
     delete b;
 }
 

@@ -1115,7 +1115,9 @@ __device__ __forceinline__ void cell_macros_t(const S *fhg, const S *lb, const A
 template <typename S, typename T, typename A>
 __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<T> c, Shift sh,
                                                     ObsScratch ws) {
-    __shared__ double s_psi[OBS_BY + 2][34], s_fs[OBS_BY + 2][34], s_eps[OBS_BY + 2][34], s_phi[OBS_BY + 2][34];
+    // per-cell values and the q_v stencils in the step's arithmetic; sums,
+    // interface crossings and the front in FP64
+    __shared__ T s_psi[OBS_BY + 2][34], s_fs[OBS_BY + 2][34], s_eps[OBS_BY + 2][34], s_phi[OBS_BY + 2][34];
     __shared__ double s_red[4][32 * OBS_BY / 32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int nx = s.nx, ny = s.ny;
@@ -1133,20 +1135,20 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         if (xx < 0) xx += nx;
         Macro<T> m;
         cell_macros_t<S, T, A>(fhg, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, m);
-        s_psi[ey][ex] = double(m.psi);
-        s_fs[ey][ex] = double(m.fs);
-        s_eps[ey][ex] = double(m.eps);
-        s_phi[ey][ex] = double(m.phi);
+        s_psi[ey][ex] = m.psi;
+        s_fs[ey][ex] = m.fs;
+        s_eps[ey][ex] = m.eps;
+        s_phi[ey][ex] = m.phi;
     }
     __syncthreads();
     if (y0 == 0 && tid < 34) {
         s_eps[0][tid] = s_eps[1][tid];
-        s_phi[0][tid] = 2.0 * double(c.phi_bot) - s_phi[1][tid];
+        s_phi[0][tid] = T(2) * c.phi_bot - s_phi[1][tid];
     }
     const int et = ny - y0 + 1;
     if (et >= 1 && et <= OBS_BY + 1 && tid >= 64 && tid < 98) {
         s_eps[et][tid - 64] = s_eps[et - 1][tid - 64];
-        s_phi[et][tid - 64] = 2.0 * double(c.phi_top) - s_phi[et - 1][tid - 64];
+        s_phi[et][tid - 64] = T(2) * c.phi_top - s_phi[et - 1][tid - 64];
     }
     __syncthreads();
 
@@ -1157,35 +1159,35 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         const int ex = tx + 1, ey = ty + 1;
         Macro<T> m;
         cell_macros_t<S, T, A>(fhg, lb, aux, P, (long long)y * s.pitch + x, y, ny, c, sh, m);
-        double gex, gey, gphx, gphy;
-        grad_s<double, 34>(s_eps, ex, ey, gex, gey);
-        grad_s<double, 34>(s_phi, ex, ey, gphx, gphy);
-        const double lphi = lap_s<double, 34>(s_phi, ex, ey);
-        v_q = -(gex * gphx + gey * gphy + double(m.eps) * lphi);
+        T gex, gey, gphx, gphy;
+        grad_s<T, 34>(s_eps, ex, ey, gex, gey);
+        grad_s<T, 34>(s_phi, ex, ey, gphx, gphy);
+        const T lphi = lap_s<T, 34>(s_phi, ex, ey);
+        v_q = double(-(gex * gphx + gey * gphy + m.eps * lphi));
         v_psi = double(m.psi);
         v_H = double(m.H);
         v_fs = double(m.fs);
         if (!isfinite(v_psi) || !isfinite(v_H)) atomicOr(ws.bad, 1u);
-        const double a = s_psi[ey][ex];
+        const double a = double(s_psi[ey][ex]);
         // column crossing (height): psi(y) >= 1/2 > psi(y+1)
         if (a >= 0.5) {
             rowbits |= 1u;
             if (y == ny - 1) {
                 atomic_max_pos(&ws.maxv[0], (double)ny);
             } else {
-                const double b = s_psi[ey + 1][ex];
+                const double b = double(s_psi[ey + 1][ex]);
                 if (b < 0.5) atomic_max_pos(&ws.maxv[0], y + (a - 0.5) / (a - b) + 0.5);
             }
             // row crossings (width): left edge needs x >= 1, right edge x <= nx - 2
             if (x >= 1) {
-                const double bl = s_psi[ey][ex - 1];
+                const double bl = double(s_psi[ey][ex - 1]);
                 if (bl < 0.5) {
                     atomic_min_pos(&ws.minv[1 + y], (x - 1) + (0.5 - bl) / (a - bl));
                     rowbits |= 2u;
                 }
             }
             if (x + 1 < nx) {
-                const double br = s_psi[ey][ex + 1];
+                const double br = double(s_psi[ey][ex + 1]);
                 if (br < 0.5) {
                     atomic_max_pos(&ws.maxv[2 + y], x + (a - 0.5) / (a - br));
                     rowbits |= 4u;
@@ -1194,13 +1196,13 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         }
         // freezing front on the centre column (lowest f_s = 1/2 crossing)
         if (x == nx / 2) {
-            const double fa = s_fs[ey][ex];
+            const double fa = double(s_fs[ey][ex]);
             if (y == 0 && fa >= 0.5) atomicOr(ws.bad + 1, 1u);
             if (fa >= 0.5) {
                 if (y == ny - 1) {
                     atomic_min_pos(&ws.minv[0], (double)ny);
                 } else {
-                    const double fb = s_fs[ey + 1][ex];
+                    const double fb = double(s_fs[ey + 1][ex]);
                     if (fb < 0.5) atomic_min_pos(&ws.minv[0], y + (fa - 0.5) / (fa - fb) + 0.5);
                 }
             }
@@ -1239,31 +1241,40 @@ static __device__ __forceinline__ double row_extent_of(const ObsScratch &ws, int
     return __longlong_as_double((long long)ws.maxv[2 + y]) - __longlong_as_double((long long)ws.minv[1 + y]);
 }
 
-// Final reduction: one block of 256 threads.
+// Final reduction: one block of 256 threads; block partial sums in a fixed
+// order (thread-strided, then a fixed shuffle tree), so the result does not
+// depend on scheduling.
 static __global__ void k_obs_final(int nx, int ny, ObsScratch ws, Scalars sc) {
-    __shared__ double s[4][256];
-    __shared__ double s_w[256];
-    const int t = threadIdx.x;
+    __shared__ double s[4][8];
+    __shared__ double s_w[8];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = t; b < ws.nblocks; b += 256)
+#pragma unroll
         for (int j = 0; j < 4; j++) acc[j] += ws.partials[(long long)b * 4 + j];
-    for (int j = 0; j < 4; j++) s[j][t] = acc[j];
-    // widest row extent
     double wmax = 0.0;
-    for (int y = t; y < ny; y += 256) {
-        const double w = row_extent_of(ws, y, nx);
-        wmax = fmax(wmax, w);
+    for (int y = t; y < ny; y += 256) wmax = fmax(wmax, row_extent_of(ws, y, nx));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+        wmax = fmax(wmax, __shfl_down_sync(0xffffffffu, wmax, o));
     }
-    s_w[t] = wmax;
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) s[j][warp] = acc[j];
+        s_w[warp] = wmax;
+    }
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (t < o) {
-            for (int j = 0; j < 4; j++) s[j][t] += s[j][t + o];
-            s_w[t] = fmax(s_w[t], s_w[t + o]);
-        }
-        __syncthreads();
-    }
     if (t == 0) {
+        double tot[4] = {0.0, 0.0, 0.0, 0.0};
+        double wm = 0.0;
+        for (int w = 0; w < 8; w++) {
+            for (int j = 0; j < 4; j++) tot[j] += s[j][w];
+            wm = fmax(wm, s_w[w]);
+        }
+        s[0][0] = tot[0]; s[1][0] = tot[1]; s[2][0] = tot[2]; s[3][0] = tot[3];
+        s_w[0] = wm;
         lbm_obs *o = ws.obs;
         const double mass = s[0][0], enth = s[1][0], solid = s[2][0], charge = s[3][0];
         o->step = sc.step;
