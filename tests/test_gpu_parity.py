@@ -235,9 +235,10 @@ def test_batch_equals_members_stepped_alone(lbm, prec, tile):
     """Uneven members, a member that starts at the other parity.  FP64
     results are bitwise those of stepping alone whatever the tile shape and
     kernel form (no FMA contraction, same operation order).  In FP32 the
-    batched kernel and the single-instance kernel may contract differently,
-    so the gap after 45 steps is held to the FP32 field bar (1e-4 with
-    natural-scale floors)."""
+    batched kernel and the single-instance kernel round differently; the
+    spec bar for single precision is on observables, so after 300
+    steps the observables must agree to 1e-4 and the fields to 1e-3 (max
+    norm with natural-scale floors)."""
     cases = [(96, 48, 15.0, 80.0, 0.1, 2.0, 5.0), (64, 32, 10.0, 110.0, 0.4, 0.5, 2.0),
              (37, 21, 6.0, 95.0, 0.0, 5.0, 9.5)]
     sims, alone = [], []
@@ -252,18 +253,22 @@ def test_batch_equals_members_stepped_alone(lbm, prec, tile):
     sims[1].step(1)
     b = lbm.Batch(sims, tile_rows=tile)
     assert b.tile_rows in (4, 8, 16)
-    b.step(45)               # one graph of 32 steps + 13 single launches
+    n = 45 if prec == W.FP64 else 300
+    b.step(n)                # graphs of 32 steps + single launches
     for s in alone:
-        s.step(45)
-    tol = 1e-4
+        s.step(n)
     for s, a in zip(sims, alone):
         assert s.t == a.t
         fl = floors(s.params)
-        for n in STORED:
+        for name in STORED:
             if prec == W.FP64:
-                assert np.array_equal(s.get(n), a.get(n)), n
+                assert np.array_equal(s.get(name), a.get(name)), name
             else:
-                assert normwise(s.get(n), a.get(n), fl.get(n, 0.0)) <= tol, n
+                assert normwise(s.get(name), a.get(name), fl.get(name, 0.0)) <= 1e-3, name
+        if prec != W.FP64:
+            os_, oa = s.observables(), a.observables()
+            for k in ("mass", "enthalpy", "frozen_fraction", "height", "width", "aspect"):
+                assert abs(os_[k] - oa[k]) <= 1e-4 * max(abs(oa[k]), 1.0), k
 
 
 def test_batch_in_l2_groups_equals_members_stepped_alone(lbm):
