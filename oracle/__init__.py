@@ -41,7 +41,7 @@ class OrcParams(C.Structure):
         ("T_m", C.c_double), ("T_w", C.c_double), ("T_init", C.c_double),
         ("CaE", C.c_double), ("R_sigma", C.c_double), ("S_eps", C.c_double),
         ("eps_g", C.c_double), ("sigma_g", C.c_double), ("R0", C.c_double),
-        ("theta_deg", C.c_double),
+        ("theta_deg", C.c_double), ("alpha_sl", C.c_double),
     ]
 
 
@@ -62,7 +62,7 @@ class OrcObs(C.Structure):
         ("frozen_fraction", C.c_double), ("height", C.c_double), ("width", C.c_double),
         ("aspect", C.c_double), ("R_tr", C.c_double), ("front", C.c_double),
         ("t_fre", C.c_int64), ("Fo_fre", C.c_double), ("status", C.c_int32),
-        ("reserved", C.c_int32),
+        ("reserved", C.c_int32), ("Pe", C.c_double), ("Qdot", C.c_double),
     ]
 
     def as_dict(self):
@@ -105,6 +105,7 @@ def lib():
         L.orc_get_field.argtypes = [C.c_void_p, C.c_int32, P(C.c_double)]
         L.orc_set_field.argtypes = [C.c_void_p, C.c_int32, P(C.c_double)]
         L.orc_observables.argtypes = [C.c_void_p, P(OrcObs)]
+        L.orc_heat_flux.argtypes = [C.c_void_p, P(C.c_double)]
         L.orc_lattice.argtypes = [P(C.c_int32), P(C.c_int32), P(C.c_double)]
         L.orc_enthalpy_inversion.argtypes = [C.c_double] * 5 + [P(C.c_double), P(C.c_double)]
         L.orc_stencils.argtypes = [C.c_int32, C.c_int32, P(C.c_double), C.c_int32, C.c_double,
@@ -202,6 +203,13 @@ class Oracle:
         o = OrcObs()
         lib().orc_observables(self._h, C.byref(o))
         return o.as_dict()
+
+    def heat_flux(self) -> np.ndarray:
+        """Local substrate heat flux per column (Sec. 4.3, reading R24)."""
+        out = np.zeros(self.nx)
+        if lib().orc_heat_flux(self._h, _dp(out)) != 0:
+            raise ValueError("oracle: heat flux needs ny >= 3")
+        return out
 
 
 def lattice():

@@ -45,8 +45,18 @@
  *   R19 Stencil ghosts: rho, eps, p, S copied; phi mirrored about phi_wall.
  *   R20 phi = 0 at the bottom electrode, E0 * ny at the top one,
  *       E0 = sqrt(CaE gamma / (eps_g R0)).
- *   R21 Solid mu, eps, sigma equal the liquid's; solid alpha equals the
- *       liquid's; F_b = 0.
+ *   R21 Solid mu, eps, sigma equal the liquid's; F_b = 0.  The solid's
+ *       thermal diffusivity is alpha_l * alpha_sl (alpha_sl = 1 unless a
+ *       property set such as Table 1 gives the solid its own).
+ *   R24 Substrate heat flux (Sec. 4.3): Fourier's law with the one-sided
+ *       second-order difference applied to the first three cell rows,
+ *       Qdot(x) = -k(x,0) (4 T(x,1) - T(x,2) - 3 T(x,0)) / 2, k the local
+ *       conductivity of row 0; the sign is the paper's (negative when heat
+ *       flows into the cold wall).  Qdot in the observables is its sum over x.
+ *   R25 Peclet number (Sec. 4.3): Pe = D_d u_d / alpha_l with D_d = 2 R0 and
+ *       u_d the liquid-weighted mean speed, sum w |psi u| / psi over sum w,
+ *       w = psi - f_s (the liquid content of a cell), using the psi u that
+ *       the last step stored (the velocity at that step's start).
  */
 #include <math.h>
 #include <stdint.h>
@@ -80,6 +90,7 @@ typedef struct {
     double sigma_g;     /* gas conductivity                                  */
     double R0;          /* reference radius (CaE, Fo)                        */
     double theta_deg;   /* static contact angle on the bottom wall           */
+    double alpha_sl;    /* alpha_s / alpha_l (R21)                           */
 } orc_params;
 
 /* Phase-resolved properties in lattice units: index 0 solid, 1 liquid, 2 gas */
@@ -96,6 +107,8 @@ typedef struct {
     double Fo_fre;
     int32_t status;
     int32_t reserved;
+    double Pe;          /* R25 */
+    double Qdot;        /* R24: sum over the substrate */
 } orc_obs;
 
 typedef struct {
@@ -163,7 +176,7 @@ int orc_derive(const orc_params *P, orc_derived *D)
         !(P->Ste > 0) || !(P->alpha_l > 0) || !(P->alpha_lg > 0) || !(P->cp_l > 0) ||
         !(P->cp_s > 0) || !(P->cp_g > 0) || !(P->CaE >= 0) || !(P->R_sigma > 0) ||
         !(P->S_eps > 0) || !(P->eps_g > 0) || !(P->sigma_g > 0) || !(P->R0 > 0) ||
-        !(P->theta_deg > 0 && P->theta_deg < 180))
+        !(P->theta_deg > 0 && P->theta_deg < 180) || !(P->alpha_sl > 0))
         return -1;
     D->rho[1] = P->rho_l;
     D->rho[2] = P->rho_l / P->rho_lg;
@@ -172,7 +185,7 @@ int orc_derive(const orc_params *P, orc_derived *D)
     D->mu[2] = P->mu_l / P->mu_lg;
     D->mu[0] = P->mu_l;                                   /* R21 */
     D->cp[0] = P->cp_s; D->cp[1] = P->cp_l; D->cp[2] = P->cp_g;
-    D->alpha_s = P->alpha_l;                              /* R21 */
+    D->alpha_s = P->alpha_l * P->alpha_sl;                /* R21 */
     D->kth[1] = D->rho[1] * D->cp[1] * P->alpha_l;        /* k = rho C_p alpha */
     D->kth[2] = D->rho[2] * D->cp[2] * (P->alpha_l / P->alpha_lg);
     D->kth[0] = D->rho[0] * D->cp[0] * D->alpha_s;
@@ -810,6 +823,21 @@ static double row_extent(const double *psi, int nx, int y)
     return right - left;
 }
 
+/* R24: local substrate heat flux Qdot(x) = -k dT/dy at the substrate
+ * (Sec. 4.3), one value per column.  Needs ny >= 3. */
+int orc_heat_flux(const orc_state *s, double *out)
+{
+    if (s->ny < 3) return -1;
+    for (int x = 0; x < s->nx; x++) {
+        macro m0, m1, m2;
+        cell_macros(s, x, &m0);
+        cell_macros(s, (long)s->nx + x, &m1);
+        cell_macros(s, 2L * s->nx + x, &m2);
+        out[x] = -m0.kth * (4.0 * m1.T - m2.T - 3.0 * m0.T) / 2.0;
+    }
+    return 0;
+}
+
 int orc_observables(orc_state *s, orc_obs *o)
 {
     const int nx = s->nx, ny = s->ny;
@@ -821,6 +849,24 @@ int orc_observables(orc_state *s, orc_obs *o)
         cell_macros(s, k, &m);
         psi[k] = m.psi; fsv[k] = m.fs; eps[k] = m.eps; phi[k] = m.phi; Hv[k] = m.H;
         if (!isfinite(m.psi) || !isfinite(m.H)) bad = 1;
+    }
+    /* R25: liquid-weighted mean speed from the stored psi u */
+    double liq = 0.0, liq_u = 0.0;
+    for (long k = 0; k < N; k++) {
+        double w = psi[k] - fsv[k];
+        if (w > 0.0) {
+            double sp = sqrt(s->psiux_prev[k] * s->psiux_prev[k] + s->psiuy_prev[k] * s->psiuy_prev[k]);
+            liq += w;
+            liq_u += w * sp / psi[k];
+        }
+    }
+    /* R24: substrate heat flux summed over x */
+    double qsum = 0.0;
+    if (ny >= 3) {
+        double *q = zeros(nx);
+        orc_heat_flux(s, q);
+        for (int x = 0; x < nx; x++) qsum += q[x];
+        free(q);
     }
     double mass = 0.0, enth = 0.0, solid = 0.0, charge = 0.0;
     for (int y = 0; y < ny; y++)
@@ -856,6 +902,8 @@ int orc_observables(orc_state *s, orc_obs *o)
     o->Fo_fre = (s->t_fre >= 0) ? s->P.alpha_l * (double)s->t_fre / (s->P.R0 * s->P.R0) : -1.0;
     o->status = bad ? -3 : 0;
     o->reserved = 0;
+    o->Pe = (liq > 0.0) ? 2.0 * s->P.R0 * (liq_u / liq) / s->P.alpha_l : 0.0;
+    o->Qdot = qsum;
     free(psi); free(fsv); free(eps); free(phi); free(Hv);
     return o->status;
 }

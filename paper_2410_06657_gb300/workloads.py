@@ -31,7 +31,7 @@ BASE = dict(
     cp_l=1.0, cp_s=1.0, cp_g=1.0,
     T_m=0.0, T_w=-1.0, T_init=0.0,
     CaE=0.2, R_sigma=5.0, S_eps=2.0, eps_g=1.0, sigma_g=1.0 / 6.0,
-    R0=20.0, theta_deg=90.0,
+    R0=20.0, theta_deg=90.0, alpha_sl=1.0,
 )
 
 # The three electric regimes of Sec. 5 (Fig. 6): (R, S) = (sigma ratio, eps ratio)
@@ -90,6 +90,36 @@ def precision_case(precision=FP32) -> dict:
     p = params(nx=1024, ny=512, R0=160.0, theta_deg=60.0, precision=precision,
                R_sigma=Rs, S_eps=Se)
     return dict(params=p, R=160.0, steps=0, presolve=0)
+
+
+# Physical properties of Table 1 (liquid / solid), wall temperatures of Sec. 4.1.
+TABLE1 = {
+    "water": dict(rho=(999.0, 917.0), k=(0.581, 2.16), cp=(4220.0, 2100.0), mu=0.003,
+                  sigma=0.076, L=333.4e3, T_m=0.0, T_wall=-10.0),
+    "hexadecane": dict(rho=(774.0, 833.0), k=(0.15, 0.15), cp=(2310.0, 1800.0), mu=0.003,
+                       sigma=0.028, L=230.0e3, T_m=18.0, T_wall=15.0),
+}
+
+
+def table1_dimensionless(substance: str) -> dict:
+    """Dimensionless groups of a Table 1 substance: Ste = C_p,l (T_m - T_w)/L,
+    rho_s/rho_l, C_p,s/C_p,l and alpha_s/alpha_l (alpha = k / (rho C_p))."""
+    t = TABLE1[substance]
+    (rl, rs), (kl, ks), (cl, cs) = t["rho"], t["k"], t["cp"]
+    return dict(Ste=cl * (t["T_m"] - t["T_wall"]) / t["L"], rho_sl=rs / rl, cp_sl=cs / cl,
+                alpha_sl=(ks / (rs * cs)) / (kl / (rl * cl)))
+
+
+def table1_case(substance: str, precision=FP32, nx=512, ny=256) -> dict:
+    """Sessile freezing of a Table 1 droplet without a field (Sec. 4.1): the
+    liquid/solid ratios of Table 1 in lattice units (C_p,l = 1), theta = 87
+    degrees, R = 0.3125 ny; gas properties and the lattice choices as in the
+    base set."""
+    d = table1_dimensionless(substance)
+    R = 0.3125 * ny
+    p = params(nx=nx, ny=ny, R0=R, theta_deg=87.0, precision=precision, CaE=0.0,
+               Ste=d["Ste"], rho_sl=d["rho_sl"], cp_l=1.0, cp_s=d["cp_sl"], alpha_sl=d["alpha_sl"])
+    return dict(params=p, R=R, presolve=0)
 
 
 BATCH_SIZES = [(128, 64), (256, 128), (384, 192), (512, 256)]

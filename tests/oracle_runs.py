@@ -47,17 +47,18 @@ def contact_angle(theta, R=16.0, nx=96, ny=48, steps=5000):
     return dict(theta=theta, height=ob["height"], base_half=ob["R_tr"])
 
 
-def stefan(Ste=0.1, alpha=0.1, h0=56.0, ny=64, steps=20000, samples=8):
-    """One-phase Stefan problem: liquid layer at T_m, cold wall below."""
+def stefan(Ste=0.1, alpha=0.1, h0=56.0, ny=64, steps=20000, samples=8, alpha_sl=1.0):
+    """One-phase Stefan problem: liquid layer at T_m, cold wall below; the
+    heat crosses the growing solid layer (diffusivity alpha * alpha_sl)."""
     o = _oracle().Oracle(_W().params(nx=4, ny=ny, rho_sl=1.0, Ste=Ste, alpha_l=alpha,
-                                     CaE=0.0, R0=h0, theta_deg=90.0))
+                                     CaE=0.0, R0=h0, theta_deg=90.0, alpha_sl=alpha_sl))
     o.init_psi(layer_psi(4, ny, h0, 4.0))
     ts, fronts = [], []
     for _ in range(samples):
         o.step(steps // samples)
         ts.append(o.t)
         fronts.append(o.observables()["front"])
-    return dict(Ste=Ste, alpha=alpha, t=ts, front=fronts)
+    return dict(Ste=Ste, alpha=alpha * alpha_sl, t=ts, front=fronts)
 
 
 def volume_change(rho_sl, h0=20.0, ny=48, steps=8000):
@@ -140,6 +141,7 @@ JOBS = {
     "angle_90": (contact_angle, (90.0,)),
     "angle_120": (contact_angle, (120.0,)),
     "stefan": (stefan, ()),
+    "stefan_solid_diffusivity": (stefan, (0.1, 0.05, 56.0, 64, 20000, 8, 2.0)),
     "volume_0.9": (volume_change, (0.9,)),
     "volume_1.1": (volume_change, (1.1,)),
     "deform_5_2": (deformation, (5.0, 2.0)),
@@ -162,6 +164,6 @@ def run_all(processes=None):
     # longest jobs first so the pool drains evenly
     order = ["deform_5_2", "deform_2_5", "sensitivity", "laplace_10", "laplace_14", "laplace_18",
              "laplace_14_W5", "angle_60", "angle_90", "angle_120", "front_paper",
-             "mass", "stefan", "volume_0.9", "volume_1.1"]
+             "mass", "stefan", "stefan_solid_diffusivity", "volume_0.9", "volume_1.1"]
     with ctx.Pool(procs) as pool:
         return dict(pool.map(_run, order, chunksize=1))

@@ -173,7 +173,8 @@ def test_derived_constants_invert_the_dimensionless_numbers():
 
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(theta_deg=0.0), dict(theta_deg=180.0),
-                                 dict(M=0.0), dict(mu_l=0.0), dict(k_e=0), dict(Ste=0.0)])
+                                 dict(M=0.0), dict(mu_l=0.0), dict(k_e=0), dict(Ste=0.0),
+                                 dict(alpha_sl=0.0)])
 def test_invalid_parameters_rejected(bad):
     with pytest.raises(ValueError):
         oracle.Oracle(W.params(**bad))
@@ -238,13 +239,16 @@ def test_static_contact_angle(runs, theta):
     assert abs(meas - theta) < 3.0
 
 
-def test_stefan_front_follows_neumann_solution(runs):
+@pytest.mark.parametrize("job", ["stefan", "stefan_solid_diffusivity"])
+def test_stefan_front_follows_neumann_solution(runs, job):
     """One-phase Stefan problem (Sec. 4, Sec. 5.3): the front advances as
-    h = 2 lam sqrt(alpha t) with lam exp(lam^2) erf(lam) = Ste / sqrt(pi)
-    (the textbook Neumann root); fitted slope within 3 %."""
+    h = 2 lam sqrt(alpha_s t) with lam exp(lam^2) erf(lam) = Ste / sqrt(pi)
+    (the textbook Neumann root; the heat crosses the solid layer, so alpha is
+    the solid's); fitted slope within 3 %.  The second case halves alpha_l
+    and doubles alpha_s / alpha_l, so only the solid's diffusivity is right."""
     from scipy.optimize import brentq
     from scipy.special import erf
-    r = runs["stefan"]
+    r = runs[job]
     lam = brentq(lambda l: l * math.exp(l * l) * erf(l) - r["Ste"] / math.sqrt(math.pi), 1e-9, 5)
     t = np.array(r["t"], float)
     h = np.array(r["front"])
@@ -328,3 +332,106 @@ def test_regularised_normal_keeps_round_off_from_growing(runs):
     normal it reaches 1e-3 within 200 steps)."""
     r = runs["sensitivity"]
     assert r["dpsi"] < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Extra observables (Sec. 4.3) and the Table 1 property set (Sec. 4.1)
+# --------------------------------------------------------------------------
+
+def _uniform_state(nx, ny, psi, H, **over):
+    """An oracle state with the given psi and enthalpy fields (f_0 = psi,
+    g_0 = H, other populations zero, lagged sources zero)."""
+    o = oracle.Oracle(W.params(nx=nx, ny=ny, **over))
+    o.init_psi(np.broadcast_to(psi, (ny, nx)).copy())
+    f = np.zeros((9, ny, nx))
+    f[0] = psi
+    g = np.zeros((9, ny, nx))
+    g[0] = H
+    o.set("f", f)
+    o.set("g", g)
+    for name in ("fs_prev", "mdot_prev", "Q_prev"):
+        o.set(name, np.zeros((ny, nx)))
+    return o
+
+
+@pytest.mark.parametrize("phase", ["gas", "liquid"])
+def test_heat_flux_is_fourier_law_exact_on_quadratic_profiles(phase):
+    """Sec. 4.3 (reading R24): Qdot = -k (4 T_1 - T_2 - 3 T_0) / 2 is exact
+    for T = a + b y + c y^2, giving -k b with k = rho C_p alpha of the phase
+    (gas: alpha_l / alpha_lg; liquid above the melting point: alpha_l)."""
+    nx, ny = 6, 8
+    a, b, c = 0.3, 0.07, -0.004
+    y = np.arange(ny, dtype=np.float64)[:, None] + np.zeros((1, nx))
+    T = a + b * y + c * y * y + 0.01 * np.arange(nx)[None, :]   # columns differ
+    p = W.params(nx=nx, ny=ny)
+    d = oracle.derive(p)
+    if phase == "gas":
+        psi, H, k = 0.0, d["cp"][2] * T, d["kth"][2]
+    else:
+        psi, H, k = 1.0, d["cp"][1] * T + d["L"], d["kth"][1]   # T > T_m: liquid branch
+    o = _uniform_state(nx, ny, psi, H)
+    assert np.abs(o.get("T") - T).max() < 1e-14
+    q = o.heat_flux()
+    assert np.abs(q + k * b).max() < 1e-14 * k * b + 1e-17
+    assert k == pytest.approx(p["rho_l"] * p["cp_l"] * (p["alpha_l"] if phase == "liquid" else
+                                                        p["alpha_l"] / p["alpha_lg"]) /
+                              (1.0 if phase == "liquid" else p["rho_lg"]))
+    assert o.observables()["Qdot"] == pytest.approx(q.sum(), rel=1e-14)
+
+
+def test_heat_flux_sign_cold_wall_draws_heat():
+    """A cold wall under a warmer layer: T rises with y, so Qdot < 0 in every
+    column (the sign of Fourier's law as printed)."""
+    o = oracle.Oracle(W.params(nx=8, ny=16, CaE=0.0))
+    o.init_psi(np.zeros((16, 8)))
+    o.step(50)
+    assert np.all(o.heat_flux() < 0)
+
+
+def test_peclet_number_of_known_velocity_fields():
+    """Sec. 4.3 (reading R25): Pe = 2 R0 u_d / alpha_l with u_d the mean of
+    |psi u| / psi weighted by the liquid content psi - f_s.  A droplet moving
+    as a whole at u0 gives 2 R0 |u0| / alpha_l; a solid region moving at
+    another speed does not count; no liquid gives 0."""
+    nx, ny, R0 = 24, 16, 6.0
+    p = W.params(nx=nx, ny=ny, R0=R0)
+    d = oracle.derive(p)
+    psi = W.droplet_psi(nx, ny, 5.0, nx / 2, 4.0, 4.0)
+    o = _uniform_state(nx, ny, psi, d["L"] * psi + 0.1, R0=R0)   # above melting: all liquid
+    u0 = np.array([0.003, -0.004])
+    o.set("psiux", psi * u0[0])
+    o.set("psiuy", psi * u0[1])
+    pe = o.observables()["Pe"]
+    assert pe == pytest.approx(2 * R0 * 0.005 / p["alpha_l"], rel=1e-12)
+    # right half frozen (H below the solid branch), moving at another speed
+    H = d["L"] * psi + 0.1
+    H[:, nx // 2:] = -0.5
+    o = _uniform_state(nx, ny, psi, H, R0=R0)
+    ux = np.where(np.arange(nx)[None, :] < nx // 2, u0[0], 0.05) * psi
+    o.set("psiux", ux)
+    o.set("psiuy", np.where(np.arange(nx)[None, :] < nx // 2, u0[1], 0.05) * psi)
+    fs = o.get("fsolid")
+    assert np.abs(fs[:, nx // 2:] - psi[:, nx // 2:]).max() < 1e-15
+    assert o.observables()["Pe"] == pytest.approx(2 * R0 * 0.005 / p["alpha_l"], rel=1e-12)
+    # no liquid anywhere
+    o = _uniform_state(nx, ny, 0.0, 0.0, R0=R0)
+    assert o.observables()["Pe"] == 0.0
+
+
+def test_table1_dimensionless_groups_match_the_printed_ones():
+    """Sec. 4.1: the water properties of Table 1 give the printed Ste = 0.13
+    and rho_s/rho_l = 0.92 (to the printed digits); the solid diffusivity
+    ratio follows alpha = k / (rho C_p)."""
+    g = GOLDEN["water_case"]
+    d = W.table1_dimensionless("water")
+    assert round(d["Ste"], 2) == g["Ste"]
+    assert round(d["rho_sl"], 2) == g["rho_sl"]
+    assert d["alpha_sl"] == pytest.approx((2.16 / (917 * 2100)) / (0.581 / (999 * 4220)))
+    h = W.table1_dimensionless("hexadecane")
+    assert h["rho_sl"] > 1 > d["rho_sl"]          # hexadecane shrinks, water expands
+    case = W.table1_case("water", precision=W.FP64, nx=64, ny=32)
+    assert case["params"]["theta_deg"] == g["theta_deg"]
+    dd = oracle.derive(case["params"])
+    a_s = dd["kth"][0] / (dd["rho"][0] * dd["cp"][0])
+    a_l = dd["kth"][1] / (dd["rho"][1] * dd["cp"][1])
+    assert a_s / a_l == pytest.approx(d["alpha_sl"])
