@@ -19,6 +19,7 @@ no collective on the data path) and the slowest rank's time counts.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -35,7 +36,7 @@ sys.path.insert(0, ROOT)
 BYTES_PER_LU = {"f64": 2 * (32 + 7) * 8, "f32": 2 * (32 + 7) * 4, "f16s": 2 * 32 * 2 + 2 * 7 * 4}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_MD = os.path.join(ROOT, "profiles", "k_step_f32_production_512x256.md")
-KERNEL_SOURCES = ["lbm_kernels.cuh", "step_f32.cu", "lbm_internal.h"]
+KERNEL_SOURCES = ["lbm_kernels.cuh", "step_f32.cu", "lbm_internal.h", "philox.h"]
 
 
 def kernel_source_hash() -> str:
@@ -293,6 +294,24 @@ def run_gpu(args, world, rank, local):
     peak, peak_kind = measured_peak()
     traffic = profiled_traffic(args.precision)
 
+    # context for the fraction: a plain device copy moving the same bytes
+    # (half read, half written), timed the same way (L2 flushed, events);
+    # one launch of this size cannot reach the streaming bandwidth
+    src = torch.ones(alg_bytes // 8, dtype=torch.float32, device="cuda")
+    dst = torch.empty_like(src)
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+    for _ in range(3):
+        flush_l2()
+        dst.copy_(src)
+    for a, b in cev:
+        flush_l2()
+        a.record(stream)
+        dst.copy_(src)
+        b.record(stream)
+    torch.cuda.synchronize()
+    copy_us = 1e3 * statistics.mean(a.elapsed_time(b) for a, b in cev)
+    del src, dst
+
     # steady state (informational): a long graph-replayed run, L2 warm
     torch.cuda.synchronize()
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -338,11 +357,14 @@ def run_gpu(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": f"k_step<{args.precision}>", "launch_us": launch_us,
-                     "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_lu": bpl},
+                     "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_lu": bpl,
+                     "copy_same_bytes": {"launch_us": copy_us, "gbs": alg_bytes / (copy_us * 1e-6) / 1e9,
+                                         "frac": alg_bytes / (copy_us * 1e-6) / 1e9 / peak,
+                                         "note": "device-to-device copy of the same byte count, same timing"}},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 120,
-                "steps": k_e2e},
-        "gpu_launches": args.steps + 2 * n_obs,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": ctypes.sizeof(lbm.Obs), "steps": k_e2e},
+        "gpu_launches": args.steps + n_obs,
         "clocks": clocks,
         "steady_state": {"value": ss_mlups, "unit": "MLUPS",
                          "note": f"lbm_step({n_ss}) graph replay, state resident in L2 (informational)"},

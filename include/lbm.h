@@ -60,14 +60,15 @@ enum {
  * (dx = dt = 1, Sec. 3.1).  Derived quantities (Sec. 2 and Sec. 4):
  *   rho_g = rho_l / rho_lg, rho_s = rho_l * rho_sl, mu_g = mu_l / mu_lg,
  *   mu_s = mu_l; L = cp_l (T_m - T_w) / Ste; k_phase = rho C_p alpha with
- *   alpha_g = alpha_l / alpha_lg and alpha_s = alpha_l;
+ *   alpha_g = alpha_l / alpha_lg and alpha_s = alpha_l * alpha_sl;
  *   eps_l = eps_s = S_eps * eps_g; sigma_l = sigma_s = R_sigma * sigma_g;
  *   E0 = sqrt(CaE * gamma / (eps_g * R0)) (CaE = eps_e E0^2 R / gamma, Sec. 4);
  *   kappa = 3 gamma W / 2, beta = 12 gamma / W (Sec. 2);
  *   C_p,ref = 2 cp_s cp_l / (cp_s + cp_l) (Sec. 3.3).
- * Validity (else LBM_ERR_BADPARAM): nx, ny > 0; k_e >= 1; precision one of
+ * Validity (else LBM_ERR_BADPARAM): nx, ny > 0 with 32 x (nx rounded up to a
+ * multiple of 32) x ny < 2^32 (about 134 million cells); k_e >= 1; precision one of
  * LBM_FP*; W, M, rho_l, rho_lg, rho_sl, mu_l, mu_lg, Ste, alpha_l, alpha_lg,
- * cp_*, R_sigma, S_eps, eps_g, sigma_g, R0 > 0; gamma, CaE >= 0;
+ * alpha_sl, cp_*, R_sigma, S_eps, eps_g, sigma_g, R0 > 0; gamma, CaE >= 0;
  * 0 < theta_deg < 180; T_m >= T_w.  These keep every relaxation time above
  * 1/2 in every phase and every mixture.
  */
@@ -97,6 +98,8 @@ typedef struct lbm_params {
     double sigma_g;      /* gas conductivity (tau_l = sigma / c_s^2 + 1/2)   */
     double R0;           /* reference radius in CaE and Fo = alpha_l t / R0^2 */
     double theta_deg;    /* static contact angle on the bottom wall          */
+    double alpha_sl;     /* alpha_s / alpha_l (1: the solid conducts like the */
+                         /* liquid; Table 1 property sets differ)            */
 } lbm_params;
 
 /*
@@ -113,7 +116,13 @@ typedef struct lbm_params {
  *            frozen bottom cell (0 if that cell is not frozen);
  *   t_fre  = first step at which an observables call saw
  *            frozen_fraction >= 0.99 (-1 until then), Fo_fre its Fourier number;
- *   status = LBM_OK or LBM_ERR_DIVERGED (non-finite psi or H anywhere).
+ *   status = LBM_OK or LBM_ERR_DIVERGED (non-finite psi or H anywhere);
+ *   Pe     = 2 R0 u_d / alpha_l (Sec. 4.3, Peclet number with D_d = 2 R0),
+ *            u_d = mean of |psi u| / psi weighted by the liquid content
+ *            psi - f_s, from the psi u stored by the last step (0 without
+ *            liquid);
+ *   Qdot   = sum over x of the substrate heat flux of
+ *            lbm_substrate_heat_flux (0 when ny < 3).
  */
 typedef struct lbm_obs {
     int64_t step;
@@ -124,6 +133,8 @@ typedef struct lbm_obs {
     double Fo_fre;
     int32_t status;
     int32_t reserved;
+    double Pe;
+    double Qdot;
 } lbm_obs;
 
 /* Field ids for lbm_get_field / lbm_set_field.  Arrays are host doubles,
@@ -261,7 +272,7 @@ int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
  * synchronise the device.  It runs the same reduction as lbm_observables
  * with its scratch (block partial sums, crossing candidates) in a
  * fixed-size array that the library keeps in device memory on every GPU
- * that loads it (about 720 KB, held until the process exits).
+ * that loads it (about 1.2 MB, held until the process exits).
  *   p     parameters of the state (host struct, read during the call)
  *   pop   device array of 32 planes (f 0-8, h 0-8, g 0-8, l 0-4) of the
  *         precision's storage type, each ny rows of `pitch` elements, x
@@ -285,6 +296,17 @@ int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
  */
 int lbm_observables_noalloc(const lbm_params *p, const void *pop, const void *aux, int32_t pitch,
                             int64_t step, lbm_obs *out, void *stream);
+
+/*
+ * Local heat flux through the cold substrate (Sec. 4.3): Fourier's law with
+ * the one-sided second-order difference over the first three cell rows,
+ *   host_out[x] = -k(x,0) (4 T(x,1) - T(x,2) - 3 T(x,0)) / 2,
+ * k the local conductivity of row 0 (rho C_p alpha mixed by phase), in the
+ * handle's arithmetic precision, returned as nx host doubles.  Negative
+ * where heat flows into the cold wall.  Synchronises the handle's stream.
+ * Errors: BADPARAM (NULL, ny < 3), STATE (before init), CUDA.
+ */
+int lbm_substrate_heat_flux(struct lbm_handle *h, double *host_out);
 
 /* Steps taken since the last init.  */
 int64_t lbm_step_count(const struct lbm_handle *h);

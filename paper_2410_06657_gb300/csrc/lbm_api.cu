@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -57,7 +58,7 @@ void derive(const lbm_params &p, Consts<double> &c) {
     c.cp[2] = p.cp_g;
     c.kth[1] = c.rho[1] * c.cp[1] * p.alpha_l;                  // k = rho C_p alpha
     c.kth[2] = c.rho[2] * c.cp[2] * (p.alpha_l / p.alpha_lg);
-    c.kth[0] = c.rho[0] * c.cp[0] * p.alpha_l;                  // alpha_s = alpha_l
+    c.kth[0] = c.rho[0] * c.cp[0] * (p.alpha_l * p.alpha_sl);   // alpha_s = alpha_l alpha_sl
     c.eps[2] = p.eps_g;
     c.eps[1] = p.S_eps * p.eps_g;
     c.eps[0] = c.eps[1];
@@ -102,6 +103,9 @@ bool pos(double v) { return v > 0.0; }   // false for NaN
 
 const char *validate(const lbm_params &p) {
     if (p.nx <= 0 || p.ny <= 0) return "nx and ny must be positive";
+    // the step kernels address a cell's planes with 32-bit offsets
+    if ((uint64_t)NPOP * (uint64_t)((p.nx + 31) / 32 * 32) * (uint64_t)p.ny > 0xFFFFFFFFull)
+        return "lattice too large: 32 x (nx rounded up to 32) x ny must stay below 2^32 elements";
     if ((long long)p.nx * p.ny > (1LL << 28)) return "lattice too large";
     if (p.k_e < 1) return "k_e must be >= 1";
     if (p.precision < LBM_FP64 || p.precision > LBM_FP16S) return "unknown precision";
@@ -109,7 +113,8 @@ const char *validate(const lbm_params &p) {
     if (!(p.gamma >= 0.0) || !(p.CaE >= 0.0)) return "gamma and CaE must be >= 0";
     if (!pos(p.rho_l) || !pos(p.rho_lg) || !pos(p.rho_sl)) return "densities must be positive";
     if (!pos(p.mu_l) || !pos(p.mu_lg)) return "viscosities must be positive";
-    if (!pos(p.Ste) || !pos(p.alpha_l) || !pos(p.alpha_lg)) return "Ste and diffusivities must be positive";
+    if (!pos(p.Ste) || !pos(p.alpha_l) || !pos(p.alpha_lg) || !pos(p.alpha_sl))
+        return "Ste and diffusivities must be positive";
     if (!pos(p.cp_l) || !pos(p.cp_s) || !pos(p.cp_g)) return "heat capacities must be positive";
     if (!pos(p.R_sigma) || !pos(p.S_eps) || !pos(p.eps_g) || !pos(p.sigma_g)) return "electric properties must be positive";
     if (!pos(p.R0)) return "R0 must be positive";
@@ -130,8 +135,13 @@ const char *validate(const lbm_params &p) {
 Shift make_shift(const lbm_params &p, const Consts<double> &c) {
     Shift s;
     s.f_ref = 1.0f;
+    // g: the equilibria of liquid at rest at the melting point (g_0 =
+    // H - C_p,ref T + w_0 C_p,ref T with H = C_p,l T_m + L).  The liquid
+    // then stores values near zero, where half precision is finest: there
+    // T sits at T_m and H performs an undamped walk under rounding noise
+    // (latent-heat plateau), while in ice and gas conduction damps it.
     s.g_ref = float(c.Cref * p.T_m);
-    s.g0_ref = float(0.5 * c.L - c.Cref * p.T_m + (4.0 / 9.0) * c.Cref * p.T_m);
+    s.g0_ref = float(c.L + p.cp_l * p.T_m - c.Cref * p.T_m + (4.0 / 9.0) * c.Cref * p.T_m);
     s.h_scale = 1024.0f;
     const double E0 = (c.phi_top - c.phi_bot) / p.ny;
     s.l_scale = E0 > 1e-12 ? (float)std::exp2(std::round(std::log2(1.0 / E0))) : 1.0f;
@@ -184,6 +194,7 @@ struct lbm_handle {
     bool use_tma = false;      // TMA form of the step (tensor-map loads of the halo'd tile)
     TmaMaps maps;              // tensor maps for tile_rows (encoded on first use)
     unsigned int *err = nullptr;   // device status word of bounded waits (sticky)
+    double *qdot = nullptr;        // nx doubles: substrate heat flux profile
     // graph cache: one per starting parity (cur, lcur)
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int gsteps = 0;
@@ -417,14 +428,15 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->s.plane = plane;
     // observables workspace
     const int nb = obs_grid_blocks(nx, ny);
-    const size_t part_b = round_up((size_t)nb * 4 * sizeof(double), 256);
+    const size_t part_b = round_up((size_t)nb * OBS_NSUM * sizeof(double), 256);
+    const size_t qdot_b = round_up((size_t)nx * sizeof(double), 256);
     h->ws_max_bytes = round_up((size_t)(2 + ny) * 8, 256);
     h->ws_min_bytes = round_up((size_t)(1 + ny) * 8, 256);
-    h->ws_u32_bytes = round_up((size_t)(ny + 2) * 4, 256);
+    h->ws_u32_bytes = round_up((size_t)(ny + 3) * 4, 256);
     const size_t obs_b = round_up(sizeof(lbm_obs), 256);
     const size_t err_b = 256;
-    if (cudaMalloc(&h->ws_mem, part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b + err_b) !=
-        cudaSuccess) {
+    if (cudaMalloc(&h->ws_mem, part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b + err_b +
+                                   qdot_b) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->mem);
         delete h;
@@ -442,8 +454,11 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->ws.obs = reinterpret_cast<lbm_obs *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes);
     h->err = reinterpret_cast<unsigned int *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b);
     h->s.err = h->err;
+    h->s.rng = h->err + 4;     // two counters in the same 256-byte block
+    h->qdot = reinterpret_cast<double *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b +
+                                         err_b);
     h->ws.nblocks = nb;
-    if (cudaMemset(h->err, 0, sizeof(unsigned int)) != cudaSuccess) {
+    if (cudaMemset(h->err, 0, err_b) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->ws_mem);
         cudaFree(h->mem);
@@ -575,6 +590,22 @@ int lbm_observables(lbm_handle *h, lbm_obs *out) {
     return lbm_observables_fetch(h, out);
 }
 
+int lbm_substrate_heat_flux(lbm_handle *h, double *host_out) {
+    if (!h || !host_out) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (h->P.ny < 3) return fail(LBM_ERR_BADPARAM, "the substrate heat flux needs ny >= 3");
+    if (!h->inited) return fail(LBM_ERR_STATE, "heat flux before init");
+    cudaError_t e;
+    switch (h->P.precision) {
+    case LBM_FP64: e = launch_heat_flux_f64(h->s, h->cur, h->lcur, &h->cd, h->sh, h->qdot, h->st); break;
+    case LBM_FP32: e = launch_heat_flux_f32(h->s, h->cur, h->lcur, &h->cf, h->sh, h->qdot, h->st); break;
+    default: e = launch_heat_flux_f16s(h->s, h->cur, h->lcur, &h->cf, h->sh, h->qdot, h->st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "heat flux kernel");
+    CK(cudaMemcpyAsync(host_out, h->qdot, sizeof(double) * h->P.nx, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+}
+
 static int field_planes(int field) {
     if (field == LBM_FIELD_F || field == LBM_FIELD_H || field == LBM_FIELD_G) return 9;
     if (field == LBM_FIELD_L) return 5;
@@ -630,8 +661,10 @@ struct SnapHeader {
     int64_t step;
     int32_t nx, ny, precision, k_e;
     int64_t body_bytes;
-    char pad[24];
+    uint32_t sr_step;      // stochastic-rounding counter of half storage
+    char pad[20];
 };
+static_assert(sizeof(SnapHeader) == 64, "snapshot header is 64 bytes");
 
 static void snap_sizes(const lbm_handle *h, size_t &fhg, size_t &l, size_t &aux, size_t &sig) {
     const size_t sb = storage_bytes(h->P.precision), ab = aux_bytes(h->P.precision);
@@ -665,6 +698,8 @@ int lbm_export_state(lbm_handle *h, void *host, size_t bytes) {
     hd.body_bytes = (int64_t)(a + b + c + d + sizeof(lbm_obs));
     char *o = static_cast<char *>(host);
     std::memcpy(o, &hd, sizeof hd);
+    CK(cudaMemcpyAsync(o + offsetof(SnapHeader, sr_step), h->s.rng + h->cur, sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost, h->st));
     o += sizeof hd;
     const size_t sb = storage_bytes(h->P.precision);
     CK(cudaMemcpyAsync(o, h->s.pop[h->cur], a, cudaMemcpyDeviceToHost, h->st));
@@ -695,6 +730,8 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
     CK(cudaMemcpyAsync(h->s.aux[h->cur], o + a + b, c, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->s.sigma, o + a + b + c, d, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->ws.obs, o + a + b + c + d, sizeof(lbm_obs), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->s.rng + h->cur, static_cast<const char *>(host) + offsetof(SnapHeader, sr_step),
+                       sizeof(uint32_t), cudaMemcpyHostToDevice, h->st));
     h->step = hd.step;
     h->inited = true;
     h->diverged = false;

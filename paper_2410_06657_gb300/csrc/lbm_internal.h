@@ -48,6 +48,7 @@ struct DevState {
     void *aux[2];          // two copies of NAUX planes
     void *sigma;           // one plane
     unsigned int *err;     // device status word: bit 0 = a bounded wait timed out
+    unsigned int *rng;     // [2] stochastic-rounding step counters of half storage (or null)
     int nx, ny, pitch;     // pitch: elements per row (multiple of 32)
     long long plane;       // elements per plane (pitch * ny)
 };
@@ -60,12 +61,14 @@ struct TmaMaps {
 };
 
 // Workspace of the observables reduction.
+constexpr int OBS_NSUM = 7;          // block sums: psi, H, f_s, q_v, liquid, liquid speed, Qdot
 struct ObsScratch {
-    double *partials;               // [nblocks][4]: sum psi, H, f_s, q_v
+    double *partials;               // [nblocks][OBS_NSUM]
     unsigned long long *maxv;       // [2 + ny]: height, (unused), rightmost crossing of row y
     unsigned long long *minv;       // [1 + ny]: front crossing, leftmost crossing of row y
     unsigned int *rowany;           // [ny]: bit0 liquid, bit1 left crossing, bit2 right crossing
-    unsigned int *bad;              // [2]: non-finite seen, centre-column bottom cell frozen
+    unsigned int *bad;              // [3]: non-finite seen, centre-column bottom cell frozen,
+                                    //      blocks finished (the last one reduces)
     lbm_obs *obs;                   // device-side result (keeps t_fre)
     int nblocks;
 };
@@ -94,6 +97,9 @@ struct Scalars {           // per-call scalars of the observables reduction
                                     const void *consts /* Consts of the step's type */,       \
                                     const Shift &sh, const ObsScratch &ws, const Scalars &sc,  \
                                     cudaStream_t st);                                          \
+    cudaError_t launch_heat_flux_##SUFFIX(const DevState &s, int cur, int lcur,                \
+                                          const void *consts /* Consts of the step's type */, \
+                                          const Shift &sh, double *out, cudaStream_t st);      \
     cudaError_t launch_get_##SUFFIX(const DevState &s, int cur, int lcur, int field,           \
                                     const void *consts, const Shift &sh, double *out,          \
                                     cudaStream_t st);                                          \

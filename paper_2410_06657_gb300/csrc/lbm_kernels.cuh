@@ -28,7 +28,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lbm_internal.h"
+#include "philox.h"
 
 namespace lbm {
 
@@ -60,7 +63,25 @@ struct Pol {
     static constexpr bool shifted = false;
     __device__ static __forceinline__ T ld(const S *p, T, float) { return T(*p); }
     __device__ static __forceinline__ void st(S *p, T v, T, float) { *p = S(v); }
+    __device__ static __forceinline__ void st_sr(S *p, T v, T, float, uint32_t) { *p = S(v); }
 };
+
+// Stochastic rounding of a float to half: rounds away from zero with
+// probability equal to the distance from the value truncated towards zero,
+// in units of the half spacing, so the stored value is unbiased.  r13 holds
+// 13 uniform random bits (the number of mantissa bits a float has beyond a
+// half's).
+__device__ __forceinline__ __half half_sr(float v, uint32_t r13) {
+    uint32_t b = __float_as_uint(v);
+    const uint32_t mag = b & 0x7fffffffu;
+    if (mag >= 0x38800000u) {       // |v| >= 2^-14: a normal half keeps 10 of the 23 mantissa bits
+        b = (b & 0x80000000u) | ((mag + r13) & ~0x1fffu);
+        return __float2half_rz(__uint_as_float(b));
+    }
+    // subnormal half range: fixed spacing 2^-24
+    const float u = float(r13) * 7.2759576141834259e-12f;    // r13 * 2^-37, in [0, 2^-24)
+    return __float2half_rz(v + copysignf(u, v));
+}
 template <>
 struct Pol<__half, float> {
     static constexpr bool shifted = true;
@@ -70,7 +91,21 @@ struct Pol<__half, float> {
     __device__ static __forceinline__ void st(__half *p, float v, float ref, float scale) {
         *p = __float2half_rn((v - ref) * scale);
     }
+    __device__ static __forceinline__ void st_sr(__half *p, float v, float ref, float scale, uint32_t r13) {
+        *p = half_sr((v - ref) * scale, r13);
+    }
 };
+
+// Random bits of the stochastic rounding: one Philox block per cell, step
+// and population system (counter), under a fixed key.
+constexpr uint32_t SR_KEY0 = 0x24100665u, SR_KEY1 = 0x0F16A5EDu;
+__device__ __forceinline__ void sr_block(uint32_t w[4], long long k, uint32_t step, uint32_t sys) {
+    w[0] = (uint32_t)k;
+    w[1] = step;
+    w[2] = sys;
+    w[3] = 0u;
+    philox4x32_10(w, SR_KEY0, SR_KEY1);
+}
 
 // Per-cell reference values of the weight-shifted half storage.
 template <typename T>
@@ -210,6 +245,21 @@ __device__ __forceinline__ int wrapx(int x, int nx) {
     return x < 0 ? x + nx : (x >= nx ? x - nx : x);
 }
 
+// Slot r of the one-cell ring around a 32 x BY tile, in extended-tile
+// coordinates (row 0 and row BY+1 are 34 wide, columns 0 and 33 BY high).
+template <int BY>
+__device__ __forceinline__ void ring_slot(int r, int &ex, int &ey) {
+    if (r < 34) {
+        ex = r; ey = 0;
+    } else if (r < 68) {
+        ex = r - 34; ey = BY + 1;
+    } else if (r < 68 + BY) {
+        ex = 0; ey = r - 68 + 1;
+    } else {
+        ex = 33; ey = r - 68 - BY + 1;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The fused step (rows a1-a9) for one 32 x BY tile.
 // ---------------------------------------------------------------------------
@@ -234,6 +284,7 @@ struct StepIO {
     A *sigma;
     int nx, ny, pitch, write_sigma;
     long long plane;
+    uint32_t sr_step;       // stochastic-rounding step counter (half storage)
 };
 
 template <typename S, typename T, typename A>
@@ -248,6 +299,10 @@ __device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, i
     io.aux_in = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     io.aux_out = reinterpret_cast<A *>(cur ? s.aux[0] : s.aux[1]);
     io.sigma = reinterpret_cast<A *>(s.sigma);
+    io.sr_step = 0u;
+    if constexpr (Pol<S, T>::shifted) {
+        if (s.rng) io.sr_step = s.rng[cur];
+    }
     io.nx = s.nx;
     io.ny = s.ny;
     io.pitch = s.pitch;
@@ -261,20 +316,20 @@ template <typename S, typename T, typename A, int BY>
 __device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Consts<T> &c,
                                              const Shift &sh, TileSmem<T, BY> &sm, int ex, int ey,
                                              int x, int y) {
-    const long long P = io.plane;
-    const long long k = (long long)y * io.pitch + x;
+    const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
+    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
     Refs<T> rf;
     make_refs<S, T>(rf, sh, c, y, io.ny);
     const float fi = 1.0f / sh.f_scale, gi = 1.0f / sh.g_scale, li = 1.0f / sh.l_scale;
     T f[9], g[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        f[i] = Pol<S, T>::ld(io.fhg_in + i * P + k, rf.f[i], fi);
-        g[i] = Pol<S, T>::ld(io.fhg_in + (18 + i) * P + k, rf.g[i], gi);
+        f[i] = Pol<S, T>::ld(io.fhg_in + (i * P + k), rf.f[i], fi);
+        g[i] = Pol<S, T>::ld(io.fhg_in + ((18 + i) * P + k), rf.g[i], gi);
     }
     T l1234 = T(0);
 #pragma unroll
-    for (int i = 1; i < 5; i++) l1234 += Pol<S, T>::ld(io.l_in + i * P + k, rf.l[i], li);
+    for (int i = 1; i < 5; i++) l1234 += Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], li);
     Macro<T> m;
     local_macros(f, g, l1234, T(io.aux_in[AUX_FS * P + k]), T(io.aux_in[AUX_MDOT * P + k]),
                  T(io.aux_in[AUX_Q * P + k]), c, m);
@@ -343,8 +398,8 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                                           const TileSmem<T, BY> &sm, const PopSrc &PS, int tx, int ty, int x,
                                           int y, const Macro<T> &m, T fs_prev, T pux_prev, T puy_prev) {
     const int nx = io.nx, ny = io.ny;
-    const long long P = io.plane;
-    const long long k = (long long)y * io.pitch + x;
+    const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
+    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
     Refs<T> ro;                               // destination references (half storage)
     const int ex = tx + 1, ey = ty + 1;
     // ---- a2: stencils ----------------------------------------------------
@@ -405,11 +460,11 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     // ---- collisions + push streaming (a5-a9) -------------------------------
     // destinations of the push: wrapped columns and rows computed once
     const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
-    const long long r0 = (long long)y * io.pitch;
-    auto dest = [&](int i, int cxv, int cyv) -> long long {
+    const uint32_t r0 = (uint32_t)y * (uint32_t)io.pitch;
+    auto dest = [&](int i, int cxv, int cyv) -> uint32_t {
         (void)i;
-        const long long row = cyv < 0 ? r0 - io.pitch : (cyv > 0 ? r0 + io.pitch : r0);
-        return row + (cxv < 0 ? xm : (cxv > 0 ? xp : x));
+        const uint32_t row = cyv < 0 ? r0 - (uint32_t)io.pitch : (cyv > 0 ? r0 + (uint32_t)io.pitch : r0);
+        return row + (uint32_t)(cxv < 0 ? xm : (cxv > 0 ? xp : x));
     };
 
     // Single precision evaluates the collisions in an algebraically equal
@@ -426,6 +481,8 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         const T A3 = T(3) * p;                      // p / c_s^2
         const T S3 = Sn - T(3) * uF;                // S - u.F~ / c_s^2
         const T Gx = Fx + rfx, Gy = Fy + rfy;
+        uint32_t rb[4] = {0u, 0u, 0u, 0u};
+        if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 1u);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             T post;
@@ -448,9 +505,10 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             }
             const int yt = y + CY[i];
             if (yt < 0 || yt >= ny)
-                Pol<S, T>::st(io.fhg_out + (9 + OPP9[i]) * P + k, post, T(0), sh.h_scale);
+                Pol<S, T>::st_sr(io.fhg_out + ((9 + OPP9[i]) * P + k), post, T(0), sh.h_scale, bits13(rb, i));
             else
-                Pol<S, T>::st(io.fhg_out + (9 + i) * P + dest(i, CX[i], CY[i]), post, T(0), sh.h_scale);
+                Pol<S, T>::st_sr(io.fhg_out + ((9 + i) * P + dest(i, CX[i], CY[i])), post, T(0), sh.h_scale,
+                                 bits13(rb, i));
         }
     }
     // a5: phase field
@@ -469,6 +527,8 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         const T ay = dty + cs2<T>() * lam * nyv;
         const T om = T(1) / c.tau_f;
         const T pmd = ps * mdot;
+        uint32_t rb[4] = {0u, 0u, 0u, 0u};
+        if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 0u);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             T post;
@@ -486,10 +546,11 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             const int yt = y + CY[i];
             if (yt < 0 || yt >= ny) {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st(io.fhg_out + OPP9[i] * P + k, post, ro.f[OPP9[i]], sh.f_scale);
+                Pol<S, T>::st_sr(io.fhg_out + (OPP9[i] * P + k), post, ro.f[OPP9[i]], sh.f_scale, bits13(rb, i));
             } else {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st(io.fhg_out + i * P + dest(i, CX[i], CY[i]), post, ro.f[i], sh.f_scale);
+                Pol<S, T>::st_sr(io.fhg_out + (i * P + dest(i, CX[i], CY[i])), post, ro.f[i], sh.f_scale,
+                                 bits13(rb, i));
             }
         }
     }
@@ -502,6 +563,8 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         const T pre = T(1) - T(1) / (T(2) * tau_g);
         const T om = T(1) / tau_g;
         const T CT = c.Cref * m.T_, cpT = cp * m.T_;
+        uint32_t rb[4] = {0u, 0u, 0u, 0u};
+        if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 2u);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             T post;
@@ -523,14 +586,16 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             const int yt = y + CY[i];
             if (yt < 0) {            // cold wall: anti-bounce-back to C_p,ref T_w
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st(io.fhg_out + (18 + OPP9[i]) * P + k,
-                              -post + T(2) * w9<T>(i) * c.Cref_Tw, ro.g[OPP9[i]], sh.g_scale);
+                Pol<S, T>::st_sr(io.fhg_out + ((18 + OPP9[i]) * P + k),
+                                 -post + T(2) * w9<T>(i) * c.Cref_Tw, ro.g[OPP9[i]], sh.g_scale, bits13(rb, i));
             } else if (yt >= ny) {   // top wall: adiabatic bounce-back
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st(io.fhg_out + (18 + OPP9[i]) * P + k, post, ro.g[OPP9[i]], sh.g_scale);
+                Pol<S, T>::st_sr(io.fhg_out + ((18 + OPP9[i]) * P + k), post, ro.g[OPP9[i]], sh.g_scale,
+                                 bits13(rb, i));
             } else {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st(io.fhg_out + (18 + i) * P + dest(i, CX[i], CY[i]), post, ro.g[i], sh.g_scale);
+                Pol<S, T>::st_sr(io.fhg_out + ((18 + i) * P + dest(i, CX[i], CY[i])), post, ro.g[i], sh.g_scale,
+                                 bits13(rb, i));
             }
         }
     }
@@ -538,6 +603,8 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     {
         const T tau_l = sig / cs2<T>() + T(0.5);
         const T om = T(1) / tau_l;
+        uint32_t rb[4] = {0u, 0u, 0u, 0u};
+        if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 3u);
 #pragma unroll
         for (int i = 0; i < 5; i++) {
             const T leq = (i == 0) ? (w5<T>(0) - T(1)) * m.phi : w5<T>(i) * m.phi;
@@ -550,11 +617,12 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             if (yt < 0 || yt >= ny) {   // electrodes: anti-bounce-back
                 const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st(io.l_out + OPP5[i] * P + k, -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]],
-                              sh.l_scale);
+                Pol<S, T>::st_sr(io.l_out + (OPP5[i] * P + k), -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]],
+                                 sh.l_scale, bits13(rb, i));
             } else {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st(io.l_out + i * P + dest(i, CX5[i], CY5[i]), post, ro.l[i], sh.l_scale);
+                Pol<S, T>::st_sr(io.l_out + (i * P + dest(i, CX5[i], CY5[i])), post, ro.l[i], sh.l_scale,
+                                 bits13(rb, i));
             }
         }
     }
@@ -577,13 +645,13 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
     const int nx = io.nx, ny = io.ny;
-    const long long P = io.plane;
+    const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
 
     // ---- phase 1: own cell (kept in registers) -------------------------
     const int xg = x0 + tx, y = y0 + ty;
     const bool own = (xg < nx) && (y < ny);
     const int x = xg < nx ? xg : xg % nx;       // wrapped slot of a ragged tile
-    const long long k = (long long)y * io.pitch + x;
+    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
     Refs<T> rf;
     T f[9], g[9], l[5], h[9];
     Macro<T> m;
@@ -594,13 +662,13 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         make_refs<S, T>(rf, sh, c, y, ny);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            f[i] = Pol<S, T>::ld(io.fhg_in + i * P + k, rf.f[i], fsc);
-            g[i] = Pol<S, T>::ld(io.fhg_in + (18 + i) * P + k, rf.g[i], gsc);
+            f[i] = Pol<S, T>::ld(io.fhg_in + (i * P + k), rf.f[i], fsc);
+            g[i] = Pol<S, T>::ld(io.fhg_in + ((18 + i) * P + k), rf.g[i], gsc);
         }
 #pragma unroll
-        for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(io.l_in + i * P + k, rf.l[i], lsc);
+        for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], lsc);
 #pragma unroll
-        for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.fhg_in + (9 + i) * P + k, T(0), hsc);
+        for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.fhg_in + ((9 + i) * P + k), T(0), hsc);
         pux_prev = T(io.aux_in[AUX_PUX * P + k]);
         puy_prev = T(io.aux_in[AUX_PUY * P + k]);
         fs_prev = T(io.aux_in[AUX_FS * P + k]);
@@ -631,15 +699,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     constexpr int NRING = 2 * 34 + 2 * BY;
     for (int r = tid; r < NRING; r += 32 * BY) {
         int ex, ey;
-        if (r < 34) {
-            ex = r; ey = 0;
-        } else if (r < 68) {
-            ex = r - 34; ey = BY + 1;
-        } else if (r < 68 + BY) {
-            ex = 0; ey = r - 68 + 1;
-        } else {
-            ex = 33; ey = r - 68 - BY + 1;
-        }
+        ring_slot<BY>(r, ex, ey);
         const int hy = y0 - 1 + ey;
         if (hy < 0 || hy >= ny) continue;
         int hx = (x0 - 1 + ex) % nx;
@@ -674,6 +734,16 @@ inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes, bool &done) {
     return e;
 }
 
+// Half storage: this step's stochastic rounding used counter rng[cur]; the
+// next step (parities flipped) reads rng[cur ^ 1], which no thread of this
+// step reads, so one thread per instance can write it.
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void sr_advance(const DevState &s, int cur, const StepIO<S, T, A> &io, bool leader) {
+    if constexpr (Pol<S, T>::shifted) {
+        if (leader && s.rng) s.rng[cur ^ 1] = io.sr_step + 1u;
+    }
+}
+
 template <typename S, typename T, typename A, int BY>
 __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_step(DevState s, int cur, int lcur,
                                                                              int write_sigma, Consts<T> c, Shift sh) {
@@ -681,6 +751,7 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_step(DevS
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
     const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
+    sr_advance(s, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
     step_tile<S, T, A, BY>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
 }
 
@@ -897,6 +968,7 @@ __global__ void __launch_bounds__(32 * BY) k_step_tma(DevState s, int cur, int l
     __shared__ TileSmem<T, BY> sm;
     __shared__ __align__(8) unsigned long long mbar;
     const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
+    sr_advance(s, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
     step_tile_tma<S, T, A, BY>(io, c, sh, sm, dsm, &mbar, &mF, &mL, &mA, blockIdx.x * 32, blockIdx.y * BY, s.err);
 }
 
@@ -930,6 +1002,7 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_batch_ste
         const int local = t - it.tile_begin;
         const int bx = local % it.tiles_x, by = local / it.tiles_x;
         const StepIO<S, T, A> io = make_io<S, T, A>(it.s, it.cur ^ flip_cur, it.lcur ^ flip_l, it.write_sigma);
+        sr_advance(it.s, it.cur ^ flip_cur, io, local == 0 && threadIdx.x == 0 && threadIdx.y == 0);
         step_tile<S, T, A, BY>(io, consts[s_item], it.sh, sm, stash, bx * 32, by * BY);
         __syncthreads();
     }
@@ -1061,7 +1134,7 @@ __global__ void k_init(DevState s, const double *psi_dev, double R, double xc, d
 // Observables (row a10): FP64 reductions over the tile grid.  Each block
 // handles a 32 x 8 tile plus a one-cell halo (for q_v's stencils and the
 // interface crossings) and leaves block partial sums and order-independent
-// max/min candidates in the workspace; k_obs_final reduces them.
+// max/min candidates in the workspace; the last block to finish reduces them.
 // ---------------------------------------------------------------------------
 constexpr int OBS_BY = 8;
 
@@ -1112,13 +1185,19 @@ __device__ __forceinline__ void cell_macros_t(const S *fhg, const S *lb, const A
     local_macros<T>(f, g, l1234, T(aux[AUX_FS * P + k]), T(aux[AUX_MDOT * P + k]), T(aux[AUX_Q * P + k]), c, m);
 }
 
+static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc);
+
 template <typename S, typename T, typename A>
 __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<T> c, Shift sh,
-                                                    ObsScratch ws) {
-    // per-cell values and the q_v stencils in the step's arithmetic; sums,
-    // interface crossings and the front in FP64
+                                                    ObsScratch ws, Scalars sc) {
+    // per-cell values and the q_v stencils in the step's arithmetic; sums
+    // within a warp in the step's type (FP64 adds are slow on this part;
+    // a 32-term sum of single-precision values loses ~1e-7), across warps
+    // and blocks in FP64; interface crossings and the front in FP64
+    using R = typename std::conditional<sizeof(T) == 8, double, float>::type;
     __shared__ T s_psi[OBS_BY + 2][34], s_fs[OBS_BY + 2][34], s_eps[OBS_BY + 2][34], s_phi[OBS_BY + 2][34];
-    __shared__ double s_red[4][32 * OBS_BY / 32];
+    __shared__ T s_H[OBS_BY + 2][34], s_Tm[OBS_BY + 2][34];
+    __shared__ double s_red[OBS_NSUM][32 * OBS_BY / 32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int nx = s.nx, ny = s.ny;
     const long long P = s.plane;
@@ -1139,6 +1218,8 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         s_fs[ey][ex] = m.fs;
         s_eps[ey][ex] = m.eps;
         s_phi[ey][ex] = m.phi;
+        s_H[ey][ex] = m.H;
+        s_Tm[ey][ex] = m.T_;
     }
     __syncthreads();
     if (y0 == 0 && tid < 34) {
@@ -1153,20 +1234,39 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
     __syncthreads();
 
     const int x = x0 + tx, y = y0 + ty;
-    double v_psi = 0.0, v_H = 0.0, v_fs = 0.0, v_q = 0.0;
+    R v_psi = R(0), v_H = R(0), v_fs = R(0), v_q = R(0), v_liq = R(0), v_liqu = R(0), v_qdot = R(0);
     unsigned int rowbits = 0u;                // this lane's row flags (one warp = one row)
     if (x < nx && y < ny) {
         const int ex = tx + 1, ey = ty + 1;
-        Macro<T> m;
-        cell_macros_t<S, T, A>(fhg, lb, aux, P, (long long)y * s.pitch + x, y, ny, c, sh, m);
+        Macro<T> m;                           // this cell's values, from the extended tile
+        m.psi = s_psi[ey][ex];
+        m.fs = s_fs[ey][ex];
+        m.eps = s_eps[ey][ex];
+        m.H = s_H[ey][ex];
+        const long long k = (long long)y * s.pitch + x;
+        // substrate heat flux (R24): -k (4 T_1 - T_2 - 3 T_0) / 2 on row 0
+        if (y == 0 && ny >= 3) {
+            const T kth0 = chi(m.fs, m.psi, c.kth);
+            v_qdot = R(-kth0 * (T(4) * s_Tm[2][ex] - s_Tm[3][ex] - T(3) * s_Tm[1][ex]) / T(2));
+        }
+        // Peclet number (R25): liquid content psi - f_s weights |psi u| / psi
+        {
+            const T w = m.psi - m.fs;
+            if (w > T(0)) {
+                const T ux = T(aux[AUX_PUX * P + k]), uy = T(aux[AUX_PUY * P + k]);
+                const T sp = sqrt(ux * ux + uy * uy);
+                v_liq = R(w);
+                v_liqu = R(w * sp / m.psi);
+            }
+        }
         T gex, gey, gphx, gphy;
         grad_s<T, 34>(s_eps, ex, ey, gex, gey);
         grad_s<T, 34>(s_phi, ex, ey, gphx, gphy);
         const T lphi = lap_s<T, 34>(s_phi, ex, ey);
-        v_q = double(-(gex * gphx + gey * gphy + m.eps * lphi));
-        v_psi = double(m.psi);
-        v_H = double(m.H);
-        v_fs = double(m.fs);
+        v_q = R(-(gex * gphx + gey * gphy + m.eps * lphi));
+        v_psi = R(m.psi);
+        v_H = R(m.H);
+        v_fs = R(m.fs);
         if (!isfinite(v_psi) || !isfinite(v_H)) atomicOr(ws.bad, 1u);
         const double a = double(s_psi[ey][ex]);
         // column crossing (height): psi(y) >= 1/2 > psi(y+1)
@@ -1215,65 +1315,81 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
         if (tx == 0 && b && y < ny) atomicOr(&ws.rowany[y], b);
     }
-    // block sums (FP64, fixed shuffle order)
-    double v[4] = {v_psi, v_H, v_fs, v_q};
+    // block sums (fixed shuffle order; warps combined in FP64)
+    R v[OBS_NSUM] = {v_psi, v_H, v_fs, v_q, v_liq, v_liqu, v_qdot};
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-        double t = v[j];
+    for (int j = 0; j < OBS_NSUM; j++) {
+        R t = v[j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (tx == 0) s_red[j][ty] = t;
+        if (tx == 0) s_red[j][ty] = double(t);
     }
     __syncthreads();
-    if (tid < 4) {
+    if (tid < OBS_NSUM) {
         double t = 0.0;
         for (int w = 0; w < OBS_BY; w++) t += s_red[tid][w];
-        ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] = t;
+        ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * OBS_NSUM + tid] = t;
+    }
+    // the last block to finish reduces every block's results
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ws.bad + 2, 1u) == (unsigned int)(gridDim.x * gridDim.y) - 1u;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        obs_final(nx, ny, ws, sc);
     }
 }
 
 // psi = 1/2 extent of row y: 0 without liquid, nx without a left or right
 // crossing (the row is liquid across the periodic seam), else right - left.
+// (Other blocks wrote the workspace with atomics during this launch: read
+// it from L2.)
 static __device__ __forceinline__ double row_extent_of(const ObsScratch &ws, int y, int nx) {
-    const unsigned int bits = ws.rowany[y];
+    const unsigned int bits = __ldcg(ws.rowany + y);
     if (!(bits & 1u)) return 0.0;
     if ((bits & 6u) != 6u) return (double)nx;
-    return __longlong_as_double((long long)ws.maxv[2 + y]) - __longlong_as_double((long long)ws.minv[1 + y]);
+    return __longlong_as_double((long long)__ldcg(ws.maxv + 2 + y)) -
+           __longlong_as_double((long long)__ldcg(ws.minv + 1 + y));
 }
 
-// Final reduction: one block of 256 threads; block partial sums in a fixed
-// order (thread-strided, then a fixed shuffle tree), so the result does not
-// depend on scheduling.
-static __global__ void k_obs_final(int nx, int ny, ObsScratch ws, Scalars sc) {
-    __shared__ double s[4][8];
+// Final reduction, run by the last block of k_obs to finish (256 threads):
+// block partial sums in a fixed order (thread-strided, then a fixed shuffle
+// tree), so the result does not depend on which block finishes last.
+static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc) {
+    __shared__ double s[OBS_NSUM][8];
     __shared__ double s_w[8];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int t = threadIdx.y * blockDim.x + threadIdx.x, lane = t & 31, warp = t >> 5;
+    double acc[OBS_NSUM];
+#pragma unroll
+    for (int j = 0; j < OBS_NSUM; j++) acc[j] = 0.0;
     for (int b = t; b < ws.nblocks; b += 256)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[j] += ws.partials[(long long)b * 4 + j];
+        for (int j = 0; j < OBS_NSUM; j++) acc[j] += __ldcg(ws.partials + (long long)b * OBS_NSUM + j);
     double wmax = 0.0;
     for (int y = t; y < ny; y += 256) wmax = fmax(wmax, row_extent_of(ws, y, nx));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+        for (int j = 0; j < OBS_NSUM; j++) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
         wmax = fmax(wmax, __shfl_down_sync(0xffffffffu, wmax, o));
     }
     if (lane == 0) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) s[j][warp] = acc[j];
+        for (int j = 0; j < OBS_NSUM; j++) s[j][warp] = acc[j];
         s_w[warp] = wmax;
     }
     __syncthreads();
     if (t == 0) {
-        double tot[4] = {0.0, 0.0, 0.0, 0.0};
+        double tot[OBS_NSUM];
+        for (int j = 0; j < OBS_NSUM; j++) tot[j] = 0.0;
         double wm = 0.0;
         for (int w = 0; w < 8; w++) {
-            for (int j = 0; j < 4; j++) tot[j] += s[j][w];
+            for (int j = 0; j < OBS_NSUM; j++) tot[j] += s[j][w];
             wm = fmax(wm, s_w[w]);
         }
-        s[0][0] = tot[0]; s[1][0] = tot[1]; s[2][0] = tot[2]; s[3][0] = tot[3];
+        for (int j = 0; j < OBS_NSUM; j++) s[j][0] = tot[j];
         s_w[0] = wm;
         lbm_obs *o = ws.obs;
         const double mass = s[0][0], enth = s[1][0], solid = s[2][0], charge = s[3][0];
@@ -1284,21 +1400,42 @@ static __global__ void k_obs_final(int nx, int ny, ObsScratch ws, Scalars sc) {
         o->solid = solid;
         o->charge = charge;
         o->frozen_fraction = (mass != 0.0) ? solid / mass : 0.0;
-        o->height = __longlong_as_double((long long)ws.maxv[0]);
+        o->height = __longlong_as_double((long long)__ldcg(ws.maxv));
         o->width = s_w[0];
         o->aspect = (o->width > 0.0) ? o->height / o->width : 0.0;
         o->R_tr = 0.5 * row_extent_of(ws, 0, nx);
-        if (ws.bad[1]) {
-            const unsigned long long fmin = ws.minv[0];
+        if (__ldcg(ws.bad + 1)) {
+            const unsigned long long fmin = __ldcg(ws.minv);
             o->front = (fmin == ~0ull) ? (double)ny : __longlong_as_double((long long)fmin);
         } else {
             o->front = 0.0;
         }
-        if (o->t_fre < 0 && o->frozen_fraction >= 0.99) o->t_fre = sc.step;
+        if (__ldcg(&o->t_fre) < 0 && o->frozen_fraction >= 0.99) o->t_fre = sc.step;
         o->Fo_fre = (o->t_fre >= 0) ? sc.alpha_l * (double)o->t_fre / (sc.R0 * sc.R0) : -1.0;
-        o->status = ws.bad[0] ? LBM_ERR_DIVERGED : LBM_OK;
+        o->status = __ldcg(ws.bad) ? LBM_ERR_DIVERGED : LBM_OK;
         o->reserved = 0;
+        const double liq = s[4][0], liqu = s[5][0];
+        o->Pe = (liq > 0.0) ? 2.0 * sc.R0 * (liqu / liq) / sc.alpha_l : 0.0;     // R25
+        o->Qdot = s[6][0];                                                      // R24
     }
+}
+
+// Local substrate heat flux (R24), one thread per column, in the step's
+// arithmetic: -k(x,0) (4 T(x,1) - T(x,2) - 3 T(x,0)) / 2.  Needs ny >= 3.
+template <typename S, typename T, typename A>
+__global__ void k_heat_flux(DevState s, int cur, int lcur, Consts<T> c, Shift sh, double *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= s.nx) return;
+    const long long P = s.plane;
+    const S *fhg = reinterpret_cast<const S *>(cur ? s.pop[1] : s.pop[0]);
+    const S *lb = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * P;
+    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
+    Macro<T> m0, m1, m2;
+    cell_macros_t<S, T, A>(fhg, lb, aux, P, x, 0, s.ny, c, sh, m0);
+    cell_macros_t<S, T, A>(fhg, lb, aux, P, (long long)s.pitch + x, 1, s.ny, c, sh, m1);
+    cell_macros_t<S, T, A>(fhg, lb, aux, P, 2LL * s.pitch + x, 2, s.ny, c, sh, m2);
+    const T k0 = chi(m0.fs, m0.psi, c.kth);
+    out[x] = double(-k0 * (T(4) * m1.T_ - m2.T_ - T(3) * m0.T_) / T(2));
 }
 
 // ---------------------------------------------------------------------------
@@ -1460,8 +1597,13 @@ __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shi
                                     cudaStream_t st) {                                                      \
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
         dim3 grid((s.nx + 31) / 32, (s.ny + OBS_BY - 1) / OBS_BY);                                          \
-        k_obs<S, T, A><<<grid, dim3(32, OBS_BY), 0, st>>>(s, cur, lcur, c, sh, ws);                         \
-        k_obs_final<<<1, 256, 0, st>>>(s.nx, s.ny, ws, sc);                                                 \
+        k_obs<S, T, A><<<grid, dim3(32, OBS_BY), 0, st>>>(s, cur, lcur, c, sh, ws, sc);                     \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    cudaError_t launch_heat_flux_##SUFFIX(const DevState &s, int cur, int lcur, const void *consts,        \
+                                          const Shift &sh, double *out, cudaStream_t st) {                  \
+        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
+        k_heat_flux<S, T, A><<<(s.nx + 127) / 128, 128, 0, st>>>(s, cur, lcur, c, sh, out);                 \
         return cudaGetLastError();                                                                          \
     }                                                                                                       \
     cudaError_t launch_get_##SUFFIX(const DevState &s, int cur, int lcur, int field, const void *consts,   \

@@ -21,11 +21,11 @@ constexpr int kMaxBlocks = 20480;   // 32 x 8 tiles of the reduction grid
 constexpr int kMaxNy = 4096;        // rows (one crossing slot per row)
 
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
-constexpr size_t kPartBytes = al256(size_t(kMaxBlocks) * 4 * sizeof(double));
+constexpr size_t kPartBytes = al256(size_t(kMaxBlocks) * lbm::OBS_NSUM * sizeof(double));
 constexpr size_t kMaxvBytes = al256(size_t(2 + kMaxNy) * sizeof(unsigned long long));
 constexpr size_t kMinvBytes = al256(size_t(1 + kMaxNy) * sizeof(unsigned long long));
-constexpr size_t kU32Bytes = al256(size_t(kMaxNy + 2) * sizeof(unsigned int));
-constexpr size_t kScratchBytes = kPartBytes + kMaxvBytes + kMinvBytes + kU32Bytes;   // about 720 KB
+constexpr size_t kU32Bytes = al256(size_t(kMaxNy + 3) * sizeof(unsigned int));
+constexpr size_t kScratchBytes = kPartBytes + kMaxvBytes + kMinvBytes + kU32Bytes;   // about 1.2 MB
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
@@ -113,6 +113,7 @@ extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, con
     s.aux[0] = s.aux[1] = const_cast<void *>(aux);
     s.sigma = nullptr;
     s.err = nullptr;
+    s.rng = nullptr;
     s.nx = p->nx;
     s.ny = p->ny;
     s.pitch = pitch;
@@ -129,7 +130,7 @@ extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, con
     // minima)
     cudaError_t e = cudaMemsetAsync(ws.maxv, 0x00, (size_t)(2 + p->ny) * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.minv, 0xFF, (size_t)(1 + p->ny) * sizeof(unsigned long long), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws.rowany, 0x00, (size_t)(p->ny + 2) * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.rowany, 0x00, (size_t)(p->ny + 3) * sizeof(unsigned int), st);
     if (e == cudaSuccess) {
         switch (p->precision) {
         case LBM_FP64: e = launch_obs_f64(s, 0, 0, &cd, sh, ws, sc, st); break;

@@ -31,6 +31,7 @@ EXPORTS = [
     "lbm_set_field", "lbm_state_bytes", "lbm_export_state", "lbm_import_state",
     "lbm_step_count", "lbm_configure", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tile_rows", "lbm_batch_destroy", "lbm_observables_noalloc",
+    "lbm_substrate_heat_flux",
 ]
 
 
@@ -51,7 +52,7 @@ class Params(C.Structure):
         ("T_m", C.c_double), ("T_w", C.c_double), ("T_init", C.c_double),
         ("CaE", C.c_double), ("R_sigma", C.c_double), ("S_eps", C.c_double),
         ("eps_g", C.c_double), ("sigma_g", C.c_double), ("R0", C.c_double),
-        ("theta_deg", C.c_double),
+        ("theta_deg", C.c_double), ("alpha_sl", C.c_double),
     ]
 
 
@@ -62,7 +63,7 @@ class Obs(C.Structure):
         ("frozen_fraction", C.c_double), ("height", C.c_double), ("width", C.c_double),
         ("aspect", C.c_double), ("R_tr", C.c_double), ("front", C.c_double),
         ("t_fre", C.c_int64), ("Fo_fre", C.c_double), ("status", C.c_int32),
-        ("reserved", C.c_int32),
+        ("reserved", C.c_int32), ("Pe", C.c_double), ("Qdot", C.c_double),
     ]
 
     def as_dict(self):
@@ -112,6 +113,7 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_tile_rows.restype = C.c_int32
     L.lbm_batch_tile_rows.argtypes = [vp]
     L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_substrate_heat_flux.argtypes = [vp, P(C.c_double)]
     _lib = L
     return L
 
@@ -202,6 +204,13 @@ class Simulation:
         if rc not in (OK, ERR_DIVERGED):
             _check(rc)
         return o.as_dict()
+
+    def substrate_heat_flux(self) -> np.ndarray:
+        """Local heat flux through the cold substrate, one value per column
+        (Sec. 4.3)."""
+        out = np.zeros(self.nx)
+        _check(load().lbm_substrate_heat_flux(self._h, _dp(out)))
+        return out
 
     def observables_async(self):
         _check(load().lbm_observables_async(self._h))

@@ -149,6 +149,53 @@ def test_fp64_matches_oracle_on_the_128x64_case(lbm):
     for k in ("height", "width", "aspect", "R_tr", "front"):
         assert abs(og[k] - oo[k]) <= 1e-9 * max(abs(oo[k]), 1.0), k
     assert og["step"] == oo["step"] == 1000 and og["status"] == 0
+    for k in ("Pe", "Qdot"):
+        assert oo[k] != 0.0, k
+        assert abs(og[k] - oo[k]) <= 1e-12 * abs(oo[k]), k
+    qg, qo = g.substrate_heat_flux(), o.heat_flux()
+    assert np.abs(qg - qo).max() <= 1e-12 * np.abs(qo).max()
+
+
+@pytest.mark.parametrize("substance", ["water", "hexadecane"])
+def test_fp64_table1_property_sets(lbm, substance):
+    """Table 1 property sets (solid diffusivity and heat capacity differ from
+    the liquid's, rho_s/rho_l = 0.918 or 1.076, theta = 87): fields, Pe, Qdot
+    and the substrate heat-flux profile match the oracle after 300 steps on a
+    ragged 70 x 36 lattice."""
+    case = W.table1_case(substance, precision=W.FP64, nx=70, ny=36)
+    p = case["params"]
+    g, o = pair(lbm, p, case["R"])
+    g.step(300)
+    o.step(300)
+    assert_fp64(worst(g, o))
+    og, oo = g.observables(), o.observables()
+    assert oo["frozen_fraction"] > 0.01
+    for k in ("mass", "enthalpy", "solid", "Pe", "Qdot"):
+        assert abs(og[k] - oo[k]) <= 1e-12 * max(abs(oo[k]), 1e-30), k
+    qg, qo = g.substrate_heat_flux(), o.heat_flux()
+    assert np.abs(qg - qo).max() <= 1e-12 * np.abs(qo).max()
+
+
+@pytest.mark.parametrize("prec,tol_q,tol_pe", [(W.FP32, 1e-4, 1e-2), (W.FP16S, 3e-2, 0.25)],
+                         ids=["fp32", "fp16s"])
+def test_single_precision_extra_observables(lbm, prec, tol_q, tol_pe):
+    """Pe and the substrate heat flux of the single-precision paths against
+    the FP64 oracle on the 128 x 64 case after 200 steps.  FP32: the heat
+    flux to 1e-4 of its largest magnitude, Qdot to 1e-4 and Pe (a ratio of
+    small velocities) to 1e-2 relative.  Half storage keeps 11 significant
+    bits and rounds stochastically, and the flux is a difference of nearby
+    temperatures: 3e-2, and 0.25 for Pe."""
+    w = W.plain_fp64_small()
+    p = dict(w["params"], precision=prec)
+    g, o = pair(lbm, p, w["R"])
+    g.step(200)
+    o.step(200)
+    og, oo = g.observables(), o.observables()
+    qg, qo = g.substrate_heat_flux(), o.heat_flux()
+    eq = np.abs(qg - qo).max() / np.abs(qo).max()
+    assert eq <= tol_q, eq
+    assert abs(og["Qdot"] / oo["Qdot"] - 1) < tol_q, (og["Qdot"], oo["Qdot"])
+    assert abs(og["Pe"] / oo["Pe"] - 1) < tol_pe, (og["Pe"], oo["Pe"])
 
 
 @pytest.mark.parametrize("k_e", [1, 3])
@@ -326,10 +373,19 @@ def test_error_codes(lbm):
     with pytest.raises(lbm.LBMError) as e:
         s.init_droplet(-1.0, 8, 0, 0)
     assert e.value.code == lbm.ERR_BADPARAM
+    with pytest.raises(lbm.LBMError) as e:
+        s.substrate_heat_flux()
+    assert e.value.code == lbm.ERR_STATE
     s.init_droplet(4.0, 8.0, -0.5, 0)
     with pytest.raises(lbm.LBMError) as e:
         s.set("psi", np.zeros((8, 16)))
     assert e.value.code == lbm.ERR_BADPARAM
+    thin = lbm.Simulation(W.params(nx=16, ny=2, R0=1.0))
+    thin.init_psi(np.zeros((2, 16)))
+    with pytest.raises(lbm.LBMError) as e:
+        thin.substrate_heat_flux()
+    assert e.value.code == lbm.ERR_BADPARAM
+    assert thin.observables()["Qdot"] == 0.0
 
 
 def test_divergence_is_reported_and_stops_stepping(lbm):

@@ -40,26 +40,28 @@ def reference():
     return run_to_freezing(lbm, W.FP64)
 
 
-FP16S_STAGNATES = pytest.mark.xfail(
+FP16S_EARLY = pytest.mark.xfail(
     strict=True,
-    reason="half storage of every population stagnates: the per-step change of the enthalpy "
-           "populations from heat conduction (~1e-6) and of the phase-field populations from slow "
-           "interface motion (~1e-5) is below half a half-precision spacing at their stored "
-           "magnitudes (~3e-5), so freezing stops near 57 % frozen")
+    reason="half storage with stochastic rounding freezes completely but 0.5-1.0 % early over five "
+           "rounding streams (aspect ratio within 0.5 %): rounding noise turned into bias by the "
+           "enthalpy inversion's clamps")
 
 
-@pytest.mark.parametrize("prec", [W.FP32, pytest.param(W.FP16S, marks=FP16S_STAGNATES)],
-                         ids=["fp32", "fp16s"])
+@pytest.mark.parametrize("prec", [W.FP32, pytest.param(W.FP16S, marks=FP16S_EARLY)], ids=["fp32", "fp16s"])
 def test_observables_to_freezing_match_fp64(reference, prec):
+    """Half storage rounds the post-collision populations stochastically:
+    with round-to-nearest the per-step change from heat conduction (about
+    1e-5 of an enthalpy population) is below half a half-precision spacing,
+    the stored values never move and freezing stops near 57 % frozen."""
     from paper_2410_06657_gb300 import lbm
     t64, h64 = reference
     t, h = run_to_freezing(lbm, prec)
-    assert abs(t - t64) / t64 <= 0.005, (t, t64)
     n = min(len(h), len(h64))
     # frozen fraction once freezing is under way (relative error of a
     # quantity that starts at zero is meaningless in the first steps)
     sel = h64[:n, 1] > 0.05
     ff_err = np.abs(h[:n, 1][sel] / h64[:n, 1][sel] - 1).max()
     asp_err = np.abs(h[:n, 2] / h64[:n, 2] - 1).max()
-    assert ff_err <= 0.005, ff_err
-    assert asp_err <= 0.01, asp_err
+    t_err = abs(t - t64) / t64
+    report = dict(t_fre=t, t_fre_fp64=t64, t_err=t_err, frozen_fraction_err=ff_err, aspect_err=asp_err)
+    assert t_err <= 0.005 and ff_err <= 0.005 and asp_err <= 0.01, report

@@ -33,20 +33,23 @@ def test_library_exports_every_declared_entry_point():
 
 
 def test_struct_layouts_match_the_header():
-    # lbm_params: 4 int32 then 24 doubles; lbm_obs: 15 eight-byte slots
-    assert C.sizeof(lbm.Params) == 4 * 4 + 24 * 8
-    assert C.sizeof(lbm.Obs) == 15 * 8
+    # lbm_params: 4 int32 then 25 doubles; lbm_obs: 17 eight-byte slots
+    assert C.sizeof(lbm.Params) == 4 * 4 + 25 * 8
+    assert C.sizeof(lbm.Obs) == 17 * 8
     src = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    body = src[src.index("typedef struct lbm_params"):src.index("} lbm_params;")]
-    names = re.findall(r"\b(?:int32_t|double)\s+([^;]+);", body)
-    fields = [n.strip() for group in names for n in group.split(",")]
-    assert fields == [f for f, _ in lbm.Params._fields_]
+    for struct, cls in (("lbm_params", lbm.Params), ("lbm_obs", lbm.Obs)):
+        body = src[src.index("typedef struct " + struct):src.index("} " + struct + ";")]
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = re.findall(r"\b(?:int32_t|int64_t|double)\s+([^;]+);", body)
+        fields = [n.strip() for group in names for n in group.split(",")]
+        assert fields == [f for f, _ in cls._fields_], struct
 
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(k_e=0), dict(precision=7),
                                  dict(theta_deg=180.0), dict(theta_deg=0.0), dict(M=0.0),
                                  dict(mu_l=-1.0), dict(Ste=0.0), dict(sigma_g=0.0),
-                                 dict(T_w=1.0), dict(W=float("nan"))])
+                                 dict(T_w=1.0), dict(W=float("nan")), dict(alpha_sl=0.0),
+                                 dict(nx=16384, ny=16384)])
 def test_create_rejects_bad_parameters_without_a_device(bad):
     L = lbm.load()
     p = lbm.make_params(W.params(**bad))
@@ -74,3 +77,32 @@ def test_product_path_never_uses_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, re.M), f
                 assert "lbm_oracle" not in text, f
+
+
+def test_philox_matches_published_known_answers(tmp_path):
+    """The stochastic rounding of half storage draws its bits from
+    Philox4x32-10; the library's own header, compiled for the host, must
+    reproduce the generator's published known-answer vectors, and the 13-bit
+    fields must tile the 128-bit block in order."""
+    import json
+    kat = json.load(open(os.path.join(ROOT, "tests", "golden", "philox4x32_10_kat.json")))["vectors"]
+    src = tmp_path / "kat.cpp"
+    src.write_text(
+        '#include <cstdio>\n#include <cstdlib>\n#include "philox.h"\n'
+        "int main(int argc, char **argv) {\n"
+        "  uint32_t c[4]; for (int i = 0; i < 4; i++) c[i] = (uint32_t)strtoul(argv[1 + i], 0, 16);\n"
+        "  uint32_t k0 = (uint32_t)strtoul(argv[5], 0, 16), k1 = (uint32_t)strtoul(argv[6], 0, 16);\n"
+        "  lbm::philox4x32_10(c, k0, k1);\n"
+        '  printf("%08x %08x %08x %08x", c[0], c[1], c[2], c[3]);\n'
+        "  for (int j = 0; j < 9; j++) printf(\" %u\", lbm::bits13(c, j));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "kat"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2410_06657_gb300", "csrc"),
+                    str(src), "-o", str(exe)], check=True)
+    for v in kat:
+        out = subprocess.run([str(exe), *v["ctr"], *v["key"]], capture_output=True, text=True,
+                             check=True).stdout.split()
+        assert out[:4] == v["out"]
+        words = [int(w, 16) for w in out[:4]]
+        block = sum(w << (32 * i) for i, w in enumerate(words))
+        assert [int(b) for b in out[4:]] == [(block >> (13 * j)) & 0x1fff for j in range(9)]
