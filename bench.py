@@ -33,7 +33,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_LU = {"f64": 2 * (32 + 7) * 8, "f32": 2 * (32 + 7) * 4, "f16s": 2 * 32 * 2 + 2 * 7 * 4}
+BYTES_PER_LU = {"f64": 2 * (32 + 7) * 8, "f32": 2 * (32 + 7) * 4, "f16s": 2 * (9 * 4 + 23 * 2) + 2 * 7 * 4}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_MD = os.path.join(ROOT, "profiles", "k_step_f32_production_512x256.md")
 KERNEL_SOURCES = ["lbm_kernels.cuh", "step_f32.cu", "lbm_internal.h", "philox.h"]

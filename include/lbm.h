@@ -39,8 +39,10 @@ extern "C" {
 enum {
     LBM_FP64 = 0,  /* populations and arithmetic in double                      */
     LBM_FP32 = 1,  /* populations and arithmetic in float                       */
-    LBM_FP16S = 2  /* populations stored as half after subtracting a reference  */
-                   /* state (weight-shifted), arithmetic in float               */
+    LBM_FP16S = 2  /* h, g, l stored as half after subtracting a reference      */
+                   /* state (weight-shifted) and rounded stochastically; the    */
+                   /* phase-field populations f stay in float; arithmetic in    */
+                   /* float                                                     */
 };
 
 /* Return codes. */
@@ -238,7 +240,8 @@ int lbm_set_field(struct lbm_handle *h, int32_t field, const double *host_in);
 
 /*
  * Whole-state snapshot for checkpoint/resume and host hand-over: the step
- * counter, t_fre and every stored array in the handle's storage precision.
+ * counter, the stochastic-rounding counter, t_fre and every stored array in
+ * the handle's storage precision.
  * lbm_state_bytes gives the size; export copies device -> host (synchronous),
  * import copies host -> device (enqueued on the stream; from pinned host
  * memory it is asynchronous, and the caller must keep the buffer alive and
@@ -256,10 +259,11 @@ int lbm_import_state(struct lbm_handle *h, const void *host, size_t bytes);
  *   variant LBM_STEP_DIRECT (default): every thread loads its cell from
  *     global memory and stashes it in shared memory for the collisions;
  *   variant LBM_STEP_TMA: tensor-memory-accelerator loads bring each tile
- *     with its halo into shared memory (faster on large lattices).
+ *     with its halo into shared memory (FP64 and FP32 only: the boxes
+ *     assume one storage type for f, h and g).
  *   tile_rows: 4, 8 or 16 lattice rows per 32-column tile (default 4 in
  *     single precision, 8 in FP64).
- * Errors: BADPARAM (unknown variant or height, NULL).
+ * Errors: BADPARAM (unknown variant or height, TMA with LBM_FP16S, NULL).
  */
 enum { LBM_STEP_TMA = 0, LBM_STEP_DIRECT = 1 };
 int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
@@ -274,10 +278,12 @@ int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
  * fixed-size array that the library keeps in device memory on every GPU
  * that loads it (about 1.2 MB, held until the process exits).
  *   p     parameters of the state (host struct, read during the call)
- *   pop   device array of 32 planes (f 0-8, h 0-8, g 0-8, l 0-4) of the
- *         precision's storage type, each ny rows of `pitch` elements, x
- *         fastest -- for example the body of an lbm_export_state snapshot
- *         after its 64-byte header (pitch = nx rounded up to 32)
+ *   pop   device array of 32 planes, f 0-8 then h 0-8, g 0-8, l 0-4, each
+ *         ny rows of `pitch` elements, x fastest: all in double for
+ *         LBM_FP64, all in float for LBM_FP32; for LBM_FP16S the 9 f planes
+ *         in float followed by the 23 others in half -- for example the body
+ *         of an lbm_export_state snapshot after its 64-byte header (pitch =
+ *         nx rounded up to 32)
  *   aux   device array of the 7 auxiliary planes that follow `pop` in such a
  *         snapshot (FP64 for LBM_FP64, else FP32), same plane layout
  *   pitch elements per row (>= nx); step: step number reported in out

@@ -44,6 +44,13 @@ size_t storage_bytes(int precision) {
     return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
 }
 size_t aux_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+// Population copy layout: 9 f planes, then h, g, l (9, 9, 5 planes) of the
+// storage type; half storage keeps f in single precision.
+size_t f_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+size_t pop_cell_bytes(int precision) { return 9 * f_bytes(precision) + (NPOP - 9) * storage_bytes(precision); }
+size_t l_offset_bytes(int precision, long long plane) {
+    return (size_t)plane * (9 * f_bytes(precision) + 18 * storage_bytes(precision));
+}
 
 // Lattice constants from the dimensionless parameters (Secs. 2-4).
 void derive(const lbm_params &p, Consts<double> &c) {
@@ -407,7 +414,8 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     const int pitch = (int)round_up(nx, 32);
     const long long plane = (long long)pitch * ny;
     const size_t sb = storage_bytes(p->precision), ab = aux_bytes(p->precision);
-    const size_t pop_b = round_up((size_t)NPOP * plane * sb, 256);
+    const size_t pop_b = round_up((size_t)plane * pop_cell_bytes(p->precision), 256);
+    (void)sb;
     const size_t aux_b = round_up((size_t)NAUX * plane * ab, 256);
     const size_t sig_b = round_up((size_t)plane * ab, 256);
     h->mem_bytes = 2 * pop_b + 2 * aux_b + sig_b;
@@ -668,7 +676,7 @@ static_assert(sizeof(SnapHeader) == 64, "snapshot header is 64 bytes");
 
 static void snap_sizes(const lbm_handle *h, size_t &fhg, size_t &l, size_t &aux, size_t &sig) {
     const size_t sb = storage_bytes(h->P.precision), ab = aux_bytes(h->P.precision);
-    fhg = (size_t)NFHG * h->s.plane * sb;
+    fhg = l_offset_bytes(h->P.precision, h->s.plane);
     l = (size_t)(NPOP - NFHG) * h->s.plane * sb;
     aux = (size_t)NAUX * h->s.plane * ab;
     sig = (size_t)h->s.plane * ab;
@@ -701,9 +709,8 @@ int lbm_export_state(lbm_handle *h, void *host, size_t bytes) {
     CK(cudaMemcpyAsync(o + offsetof(SnapHeader, sr_step), h->s.rng + h->cur, sizeof(uint32_t),
                        cudaMemcpyDeviceToHost, h->st));
     o += sizeof hd;
-    const size_t sb = storage_bytes(h->P.precision);
     CK(cudaMemcpyAsync(o, h->s.pop[h->cur], a, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(o + a, static_cast<char *>(h->s.pop[h->lcur]) + (size_t)NFHG * h->s.plane * sb, b,
+    CK(cudaMemcpyAsync(o + a, static_cast<char *>(h->s.pop[h->lcur]) + l_offset_bytes(h->P.precision, h->s.plane), b,
                        cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(o + a + b, h->s.aux[h->cur], c, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(o + a + b + c, h->s.sigma, d, cudaMemcpyDeviceToHost, h->st));
@@ -723,9 +730,8 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
     size_t a, b, c, d;
     snap_sizes(h, a, b, c, d);
     const char *o = static_cast<const char *>(host) + sizeof hd;
-    const size_t sb = storage_bytes(h->P.precision);
     CK(cudaMemcpyAsync(h->s.pop[h->cur], o, a, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(static_cast<char *>(h->s.pop[h->lcur]) + (size_t)NFHG * h->s.plane * sb, o + a, b,
+    CK(cudaMemcpyAsync(static_cast<char *>(h->s.pop[h->lcur]) + l_offset_bytes(h->P.precision, h->s.plane), o + a, b,
                        cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->s.aux[h->cur], o + a + b, c, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->s.sigma, o + a + b + c, d, cudaMemcpyHostToDevice, h->st));
@@ -743,6 +749,8 @@ int64_t lbm_step_count(const lbm_handle *h) { return h ? h->step : -1; }
 int lbm_configure(lbm_handle *h, int32_t variant, int32_t tile_rows) {
     if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
     if (variant != LBM_STEP_TMA && variant != LBM_STEP_DIRECT) return fail(LBM_ERR_BADPARAM, "unknown variant");
+    if (variant == LBM_STEP_TMA && h->P.precision == LBM_FP16S)
+        return fail(LBM_ERR_BADPARAM, "the TMA form needs one storage type for f, h and g (FP64 or FP32)");
     if (tile_rows != 4 && tile_rows != 8 && tile_rows != 16) return fail(LBM_ERR_BADPARAM, "tile_rows must be 4, 8 or 16");
     CK(cudaStreamSynchronize(h->st));
     h->use_tma = (variant == LBM_STEP_TMA);
@@ -812,8 +820,8 @@ static void free_list(WorkList &L) {
 
 // Device bytes a member's step touches (both copies of every plane).
 static size_t member_state_bytes(const lbm_handle *h) {
-    const size_t sb = storage_bytes(h->P.precision), ab = aux_bytes(h->P.precision);
-    return (size_t)h->s.plane * (2 * NPOP * sb + 2 * NAUX * ab + ab);
+    const size_t ab = aux_bytes(h->P.precision);
+    return (size_t)h->s.plane * (2 * pop_cell_bytes(h->P.precision) + 2 * NAUX * ab + ab);
 }
 
 static int build_list(lbm_batch *b, const std::vector<int> &idx, int tile_rows, int sms, WorkList &L) {

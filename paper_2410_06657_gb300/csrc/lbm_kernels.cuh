@@ -107,6 +107,31 @@ __device__ __forceinline__ void sr_block(uint32_t w[4], long long k, uint32_t st
     philox4x32_10(w, SR_KEY0, SR_KEY1);
 }
 
+// Population planes of one buffer copy: f (9 planes of type F), then h (9),
+// g (9) and l (5) of the storage type S.  Half storage keeps f in single
+// precision: with f in half, the rounding noise on psi in the cold gas
+// (where f is largest after the shift) becomes spurious solid through
+// f_s = psi (1 - f_l) (negative excursions count as no solid, positive ones
+// as solid), and the freezing time came out about 1 % early.
+template <typename S> struct FStore { using type = S; };
+template <> struct FStore<__half> { using type = float; };
+
+template <typename S>
+struct Planes {
+    using F = typename FStore<S>::type;
+    F *f;
+    S *h, *g, *l;
+    __host__ __device__ static Planes at(const void *base, long long P) {
+        Planes v;
+        char *b = const_cast<char *>(reinterpret_cast<const char *>(base));
+        v.f = reinterpret_cast<F *>(b);
+        v.h = reinterpret_cast<S *>(b + 9 * P * (long long)sizeof(F));
+        v.g = v.h + 9 * P;
+        v.l = v.h + 18 * P;
+        return v;
+    }
+};
+
 // Per-cell reference values of the weight-shifted half storage.
 template <typename T>
 struct Refs {
@@ -275,10 +300,11 @@ struct TileSmem {
 
 template <typename S, typename T, typename A>
 struct StepIO {
-    const S *fhg_in;
-    S *fhg_out;
-    const S *l_in;
-    S *l_out;
+    using F = typename FStore<S>::type;
+    const F *f_in;
+    F *f_out;
+    const S *h_in, *g_in, *l_in;
+    S *h_out, *g_out, *l_out;
     const A *aux_in;
     A *aux_out;
     A *sigma;
@@ -292,10 +318,16 @@ __device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, i
     StepIO<S, T, A> io;
     // select rather than index the parameter arrays (a dynamic index would
     // copy them to local memory)
-    io.fhg_in = reinterpret_cast<const S *>(cur ? s.pop[1] : s.pop[0]);
-    io.fhg_out = reinterpret_cast<S *>(cur ? s.pop[0] : s.pop[1]);
-    io.l_in = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * s.plane;
-    io.l_out = reinterpret_cast<S *>(lcur ? s.pop[0] : s.pop[1]) + (long long)NFHG * s.plane;
+    const Planes<S> pin = Planes<S>::at(cur ? s.pop[1] : s.pop[0], s.plane);
+    const Planes<S> pout = Planes<S>::at(cur ? s.pop[0] : s.pop[1], s.plane);
+    io.f_in = pin.f;
+    io.h_in = pin.h;
+    io.g_in = pin.g;
+    io.f_out = pout.f;
+    io.h_out = pout.h;
+    io.g_out = pout.g;
+    io.l_in = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], s.plane).l;
+    io.l_out = Planes<S>::at(lcur ? s.pop[0] : s.pop[1], s.plane).l;
     io.aux_in = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     io.aux_out = reinterpret_cast<A *>(cur ? s.aux[0] : s.aux[1]);
     io.sigma = reinterpret_cast<A *>(s.sigma);
@@ -324,8 +356,8 @@ __device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Co
     T f[9], g[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        f[i] = Pol<S, T>::ld(io.fhg_in + (i * P + k), rf.f[i], fi);
-        g[i] = Pol<S, T>::ld(io.fhg_in + ((18 + i) * P + k), rf.g[i], gi);
+        f[i] = Pol<typename FStore<S>::type, T>::ld(io.f_in + (i * P + k), rf.f[i], fi);
+        g[i] = Pol<S, T>::ld(io.g_in + (i * P + k), rf.g[i], gi);
     }
     T l1234 = T(0);
 #pragma unroll
@@ -505,9 +537,9 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             }
             const int yt = y + CY[i];
             if (yt < 0 || yt >= ny)
-                Pol<S, T>::st_sr(io.fhg_out + ((9 + OPP9[i]) * P + k), post, T(0), sh.h_scale, bits13(rb, i));
+                Pol<S, T>::st_sr(io.h_out + (OPP9[i] * P + k), post, T(0), sh.h_scale, bits13(rb, i));
             else
-                Pol<S, T>::st_sr(io.fhg_out + ((9 + i) * P + dest(i, CX[i], CY[i])), post, T(0), sh.h_scale,
+                Pol<S, T>::st_sr(io.h_out + (i * P + dest(i, CX[i], CY[i])), post, T(0), sh.h_scale,
                                  bits13(rb, i));
         }
     }
@@ -546,10 +578,12 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             const int yt = y + CY[i];
             if (yt < 0 || yt >= ny) {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st_sr(io.fhg_out + (OPP9[i] * P + k), post, ro.f[OPP9[i]], sh.f_scale, bits13(rb, i));
+                Pol<typename FStore<S>::type, T>::st_sr(io.f_out + (OPP9[i] * P + k), post, ro.f[OPP9[i]], sh.f_scale,
+                                                        bits13(rb, i));
             } else {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st_sr(io.fhg_out + (i * P + dest(i, CX[i], CY[i])), post, ro.f[i], sh.f_scale,
+                Pol<typename FStore<S>::type, T>::st_sr(io.f_out + (i * P + dest(i, CX[i], CY[i])), post, ro.f[i],
+                                                        sh.f_scale,
                                  bits13(rb, i));
             }
         }
@@ -586,15 +620,15 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             const int yt = y + CY[i];
             if (yt < 0) {            // cold wall: anti-bounce-back to C_p,ref T_w
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st_sr(io.fhg_out + ((18 + OPP9[i]) * P + k),
+                Pol<S, T>::st_sr(io.g_out + (OPP9[i] * P + k),
                                  -post + T(2) * w9<T>(i) * c.Cref_Tw, ro.g[OPP9[i]], sh.g_scale, bits13(rb, i));
             } else if (yt >= ny) {   // top wall: adiabatic bounce-back
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st_sr(io.fhg_out + ((18 + OPP9[i]) * P + k), post, ro.g[OPP9[i]], sh.g_scale,
+                Pol<S, T>::st_sr(io.g_out + (OPP9[i] * P + k), post, ro.g[OPP9[i]], sh.g_scale,
                                  bits13(rb, i));
             } else {
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st_sr(io.fhg_out + ((18 + i) * P + dest(i, CX[i], CY[i])), post, ro.g[i], sh.g_scale,
+                Pol<S, T>::st_sr(io.g_out + (i * P + dest(i, CX[i], CY[i])), post, ro.g[i], sh.g_scale,
                                  bits13(rb, i));
             }
         }
@@ -662,13 +696,13 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         make_refs<S, T>(rf, sh, c, y, ny);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            f[i] = Pol<S, T>::ld(io.fhg_in + (i * P + k), rf.f[i], fsc);
-            g[i] = Pol<S, T>::ld(io.fhg_in + ((18 + i) * P + k), rf.g[i], gsc);
+            f[i] = Pol<typename FStore<S>::type, T>::ld(io.f_in + (i * P + k), rf.f[i], fsc);
+            g[i] = Pol<S, T>::ld(io.g_in + (i * P + k), rf.g[i], gsc);
         }
 #pragma unroll
         for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], lsc);
 #pragma unroll
-        for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.fhg_in + ((9 + i) * P + k), T(0), hsc);
+        for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.h_in + (i * P + k), T(0), hsc);
         pux_prev = T(io.aux_in[AUX_PUX * P + k]);
         puy_prev = T(io.aux_in[AUX_PUY * P + k]);
         fs_prev = T(io.aux_in[AUX_FS * P + k]);
@@ -702,8 +736,9 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         ring_slot<BY>(r, ex, ey);
         const int hy = y0 - 1 + ey;
         if (hy < 0 || hy >= ny) continue;
-        int hx = (x0 - 1 + ex) % nx;
-        if (hx < 0) hx += nx;
+        // x0 - 1 + ex lies in [-1, nx + 32]: beyond nx only on a ragged last tile
+        int hx = x0 - 1 + ex;
+        hx = hx < 0 ? hx + nx : (hx >= nx ? (hx - nx < nx ? hx - nx : (hx - nx) % nx) : hx);
         cell_to_smem<S, T, A, BY>(io, c, sh, sm, ex, ey, hx, hy);
     }
     __syncthreads();
@@ -719,7 +754,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
 // with 4-row tiles, 7 blocks (28 warps) hold a 512 x 256 lattice in one wave.
 template <typename T, int BY>
 constexpr int step_min_blocks() {
-    return sizeof(T) == 8 ? 1 : (BY == 4 ? 7 : (BY == 8 ? 3 : 1));
+    return sizeof(T) == 8 ? 1 : (BY == 4 ? 7 : (BY == 8 ? 4 : 1));
 }
 
 template <typename T, int BY>
@@ -886,7 +921,7 @@ __device__ __forceinline__ void step_tile_tma(const StepIO<S, T, A> &io, const C
                 if (yy < 0 || yy >= ny) continue;
                 const long long kk = (long long)yy * io.pitch + srcx;
                 if (q < NFHG)
-                    bF[q * G::PL + r * G::BW + col] = io.fhg_in[q * P + kk];
+                    bF[q * G::PL + r * G::BW + col] = io.f_in[q * P + kk];   // uniform storage: f, h, g contiguous
                 else if (q < NPOP)
                     bL[(q - NFHG) * G::PL + r * G::BW + col] = io.l_in[(q - NFHG) * P + kk];
                 else
@@ -1050,8 +1085,8 @@ __global__ void k_sweep(DevState s, int lcur, Consts<T> c, Shift sh) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= s.nx || y >= s.ny) return;
-    const S *l_in = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * s.plane;
-    S *l_out = reinterpret_cast<S *>(lcur ? s.pop[0] : s.pop[1]) + (long long)NFHG * s.plane;
+    const S *l_in = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], s.plane).l;
+    S *l_out = Planes<S>::at(lcur ? s.pop[0] : s.pop[1], s.plane).l;
     sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(s.sigma), s.nx, s.ny, s.pitch, s.plane, c,
                         sh, x, y);
 }
@@ -1069,8 +1104,8 @@ __global__ void __launch_bounds__(256) k_batch_sweep(const BatchItem *__restrict
         const int y = (local / it.sweep_tiles_x) * 8 + threadIdx.y;
         if (x < it.s.nx && y < it.s.ny) {
             const int lc = it.lcur ^ flip_l;
-            const S *l_in = reinterpret_cast<const S *>(lc ? it.s.pop[1] : it.s.pop[0]) + (long long)NFHG * it.s.plane;
-            S *l_out = reinterpret_cast<S *>(lc ? it.s.pop[0] : it.s.pop[1]) + (long long)NFHG * it.s.plane;
+            const S *l_in = Planes<S>::at(lc ? it.s.pop[1] : it.s.pop[0], it.s.plane).l;
+            S *l_out = Planes<S>::at(lc ? it.s.pop[0] : it.s.pop[1], it.s.plane).l;
             sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(it.s.sigma), it.s.nx, it.s.ny,
                                 it.s.pitch, it.s.plane, consts[ii], it.sh, x, y);
         }
@@ -1104,7 +1139,7 @@ __global__ void k_init(DevState s, const double *psi_dev, double R, double xc, d
     const T rho0 = chi(T(0), ps, c.rho);
     Refs<T> rf;
     make_refs<S, T>(rf, sh, c, y, s.ny);
-    S *pop = reinterpret_cast<S *>(s.pop[0]);
+    const Planes<S> pl = Planes<S>::at(s.pop[0], P);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         const T feq = w9<T>(i) * ps * (T(1) + T(0) / cs2<T>());
@@ -1115,14 +1150,14 @@ __global__ void k_init(DevState s, const double *psi_dev, double R, double xc, d
             geq = H0 - c.Cref * T0 + w9<T>(0) * cpm * T0 * (c.Cref / cpm - T(0) / (T(2) * cs2<T>()));
         else
             geq = w9<T>(i) * cpm * T0 * (c.Cref / cpm + T(0) / cs2<T>() + (T(0) - T(0)) / (T(2) * cs2<T>() * cs2<T>()));
-        Pol<S, T>::st(pop + i * P + k, feq, rf.f[i], sh.f_scale);
-        Pol<S, T>::st(pop + (9 + i) * P + k, heq, T(0), sh.h_scale);
-        Pol<S, T>::st(pop + (18 + i) * P + k, geq, rf.g[i], sh.g_scale);
+        Pol<typename FStore<S>::type, T>::st(pl.f + i * P + k, feq, rf.f[i], sh.f_scale);
+        Pol<S, T>::st(pl.h + i * P + k, heq, T(0), sh.h_scale);
+        Pol<S, T>::st(pl.g + i * P + k, geq, rf.g[i], sh.g_scale);
     }
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         const T leq = (i == 0) ? (w5<T>(0) - T(1)) * phi0 : w5<T>(i) * phi0;
-        Pol<S, T>::st(pop + (NFHG + i) * P + k, leq, rf.l[i], sh.l_scale);
+        Pol<S, T>::st(pl.l + i * P + k, leq, rf.l[i], sh.l_scale);
     }
     A *aux = reinterpret_cast<A *>(s.aux[0]);
 #pragma unroll
@@ -1146,7 +1181,7 @@ static __device__ __forceinline__ void atomic_min_pos(unsigned long long *a, dou
 }
 
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void obs_macros(const S *fhg, const S *lb, const A *aux, long long P, long long k,
+__device__ __forceinline__ void obs_macros(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
                                            int y, int ny, const Consts<double> &c, const Shift &sh,
                                            Macro<double> &m) {
     Refs<T> rf;
@@ -1157,8 +1192,8 @@ __device__ __forceinline__ void obs_macros(const S *fhg, const S *lb, const A *a
     double f[9], g[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        f[i] = double(Pol<S, T>::ld(fhg + i * P + k, rf.f[i], 1.0f / sh.f_scale));
-        g[i] = double(Pol<S, T>::ld(fhg + (18 + i) * P + k, rf.g[i], 1.0f / sh.g_scale));
+        f[i] = double(Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale));
+        g[i] = double(Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale));
     }
     double l1234 = 0.0;
 #pragma unroll
@@ -1169,15 +1204,15 @@ __device__ __forceinline__ void obs_macros(const S *fhg, const S *lb, const A *a
 
 // Local macros of one cell in the arithmetic type T (the step's own type).
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void cell_macros_t(const S *fhg, const S *lb, const A *aux, long long P, long long k,
+__device__ __forceinline__ void cell_macros_t(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
                                               int y, int ny, const Consts<T> &c, const Shift &sh, Macro<T> &m) {
     Refs<T> rf;
     make_refs<S, T>(rf, sh, c, y, ny);
     T f[9], g[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        f[i] = Pol<S, T>::ld(fhg + i * P + k, rf.f[i], 1.0f / sh.f_scale);
-        g[i] = Pol<S, T>::ld(fhg + (18 + i) * P + k, rf.g[i], 1.0f / sh.g_scale);
+        f[i] = Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale);
+        g[i] = Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale);
     }
     T l1234 = T(0);
 #pragma unroll
@@ -1201,8 +1236,8 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int nx = s.nx, ny = s.ny;
     const long long P = s.plane;
-    const S *fhg = reinterpret_cast<const S *>(cur ? s.pop[1] : s.pop[0]);
-    const S *lb = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * P;
+    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
+    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
     const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * OBS_BY;
     // fill the extended tile (own + halo), ghost rows as in the step
@@ -1213,7 +1248,7 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         int xx = (x0 - 1 + ex) % nx;
         if (xx < 0) xx += nx;
         Macro<T> m;
-        cell_macros_t<S, T, A>(fhg, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, m);
+        cell_macros_t<S, T, A>(pc, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, m);
         s_psi[ey][ex] = m.psi;
         s_fs[ey][ex] = m.fs;
         s_eps[ey][ex] = m.eps;
@@ -1427,13 +1462,13 @@ __global__ void k_heat_flux(DevState s, int cur, int lcur, Consts<T> c, Shift sh
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= s.nx) return;
     const long long P = s.plane;
-    const S *fhg = reinterpret_cast<const S *>(cur ? s.pop[1] : s.pop[0]);
-    const S *lb = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * P;
+    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
+    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
     const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     Macro<T> m0, m1, m2;
-    cell_macros_t<S, T, A>(fhg, lb, aux, P, x, 0, s.ny, c, sh, m0);
-    cell_macros_t<S, T, A>(fhg, lb, aux, P, (long long)s.pitch + x, 1, s.ny, c, sh, m1);
-    cell_macros_t<S, T, A>(fhg, lb, aux, P, 2LL * s.pitch + x, 2, s.ny, c, sh, m2);
+    cell_macros_t<S, T, A>(pc, lb, aux, P, x, 0, s.ny, c, sh, m0);
+    cell_macros_t<S, T, A>(pc, lb, aux, P, (long long)s.pitch + x, 1, s.ny, c, sh, m1);
+    cell_macros_t<S, T, A>(pc, lb, aux, P, 2LL * s.pitch + x, 2, s.ny, c, sh, m2);
     const T k0 = chi(m0.fs, m0.psi, c.kth);
     out[x] = double(-k0 * (T(4) * m1.T_ - m2.T_ - T(3) * m0.T_) / T(2));
 }
@@ -1448,21 +1483,21 @@ __global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c
     if (x >= s.nx || y >= s.ny) return;
     const long long P = s.plane, k = (long long)y * s.pitch + x;
     const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
-    const S *fhg = reinterpret_cast<const S *>(cur ? s.pop[1] : s.pop[0]);
-    const S *lb = reinterpret_cast<const S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * P;
+    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
+    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
     const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     Refs<T> rf;
     Consts<T> ct;
     ct.phi_bot = T(c.phi_bot);
     ct.phi_top = T(c.phi_top);
     make_refs<S, T>(rf, sh, ct, y, s.ny);
-    if (field == LBM_FIELD_F || field == LBM_FIELD_H || field == LBM_FIELD_G) {
-        const int base = field * 9;
-        for (int i = 0; i < 9; i++) {
-            const T ref = field == LBM_FIELD_F ? rf.f[i] : (field == LBM_FIELD_G ? rf.g[i] : T(0));
-            const float sc = field == LBM_FIELD_F ? sh.f_scale : (field == LBM_FIELD_G ? sh.g_scale : sh.h_scale);
-            out[i * N + o] = double(Pol<S, T>::ld(fhg + (base + i) * P + k, ref, 1.0f / sc));
-        }
+    if (field == LBM_FIELD_F) {
+        for (int i = 0; i < 9; i++)
+            out[i * N + o] = double(Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale));
+    } else if (field == LBM_FIELD_H) {
+        for (int i = 0; i < 9; i++) out[i * N + o] = double(Pol<S, T>::ld(pc.h + i * P + k, T(0), 1.0f / sh.h_scale));
+    } else if (field == LBM_FIELD_G) {
+        for (int i = 0; i < 9; i++) out[i * N + o] = double(Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale));
     } else if (field == LBM_FIELD_L) {
         for (int i = 0; i < 5; i++) out[i * N + o] = double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
     } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
@@ -1471,7 +1506,7 @@ __global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c
         out[o] = double(reinterpret_cast<const A *>(s.sigma)[k]);
     } else {
         Macro<double> m;
-        obs_macros<S, T, A>(fhg, lb, aux, P, k, y, s.ny, c, sh, m);
+        obs_macros<S, T, A>(pc, lb, aux, P, k, y, s.ny, c, sh, m);
         out[o] = field == LBM_FIELD_PSI ? m.psi
                : field == LBM_FIELD_FSOLID ? m.fs
                : field == LBM_FIELD_T ? m.T_
@@ -1487,18 +1522,18 @@ __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shi
     if (x >= s.nx || y >= s.ny) return;
     const long long P = s.plane, k = (long long)y * s.pitch + x;
     const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
-    S *fhg = reinterpret_cast<S *>(cur ? s.pop[1] : s.pop[0]);
-    S *lb = reinterpret_cast<S *>(lcur ? s.pop[1] : s.pop[0]) + (long long)NFHG * P;
+    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
+    S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
     A *aux = reinterpret_cast<A *>(cur ? s.aux[1] : s.aux[0]);
     Refs<T> rf;
     make_refs<S, T>(rf, sh, c, y, s.ny);
-    if (field == LBM_FIELD_F || field == LBM_FIELD_H || field == LBM_FIELD_G) {
-        const int base = field * 9;
-        for (int i = 0; i < 9; i++) {
-            const T ref = field == LBM_FIELD_F ? rf.f[i] : (field == LBM_FIELD_G ? rf.g[i] : T(0));
-            const float sc = field == LBM_FIELD_F ? sh.f_scale : (field == LBM_FIELD_G ? sh.g_scale : sh.h_scale);
-            Pol<S, T>::st(fhg + (base + i) * P + k, T(in[i * N + o]), ref, sc);
-        }
+    if (field == LBM_FIELD_F) {
+        for (int i = 0; i < 9; i++)
+            Pol<typename FStore<S>::type, T>::st(pc.f + i * P + k, T(in[i * N + o]), rf.f[i], sh.f_scale);
+    } else if (field == LBM_FIELD_H) {
+        for (int i = 0; i < 9; i++) Pol<S, T>::st(pc.h + i * P + k, T(in[i * N + o]), T(0), sh.h_scale);
+    } else if (field == LBM_FIELD_G) {
+        for (int i = 0; i < 9; i++) Pol<S, T>::st(pc.g + i * P + k, T(in[i * N + o]), rf.g[i], sh.g_scale);
     } else if (field == LBM_FIELD_L) {
         for (int i = 0; i < 5; i++) Pol<S, T>::st(lb + i * P + k, T(in[i * N + o]), rf.l[i], sh.l_scale);
     } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
@@ -1554,18 +1589,22 @@ __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shi
     static cudaError_t launch_tma_by_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,        \
                                               const Consts<T> &c, const Shift &sh, const TmaMaps &m,        \
                                               cudaStream_t st) {                                            \
-        static bool ready = false;                                                                          \
-        if (!ready) {                                                                                       \
-            cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, T, A, BY>,                                   \
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,               \
-                                                 (int)TmaGeom<S, A, BY>::total + 128);                      \
-            if (e != cudaSuccess) return e;                                                                 \
-            ready = true;                                                                                   \
+        if constexpr (!std::is_same<typename FStore<S>::type, S>::value) {                                  \
+            return cudaErrorNotSupported;         /* the tensor boxes assume one storage type */            \
+        } else {                                                                                            \
+            static bool ready = false;                                                                      \
+            if (!ready) {                                                                                   \
+                cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, T, A, BY>,                               \
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                                     (int)TmaGeom<S, A, BY>::total + 128);                  \
+                if (e != cudaSuccess) return e;                                                             \
+                ready = true;                                                                               \
+            }                                                                                               \
+            dim3 grid((s.nx + 31) / 32, (s.ny + BY - 1) / BY);                                              \
+            k_step_tma<S, T, A, BY><<<grid, dim3(32, BY), TmaGeom<S, A, BY>::total + 128, st>>>(            \
+                s, cur, lcur, write_sigma, c, sh, m.fhg[cur], m.l[lcur], m.aux[cur]);                       \
+            return cudaGetLastError();                                                                      \
         }                                                                                                   \
-        dim3 grid((s.nx + 31) / 32, (s.ny + BY - 1) / BY);                                                  \
-        k_step_tma<S, T, A, BY><<<grid, dim3(32, BY), TmaGeom<S, A, BY>::total + 128, st>>>(                \
-            s, cur, lcur, write_sigma, c, sh, m.fhg[cur], m.l[lcur], m.aux[cur]);                           \
-        return cudaGetLastError();                                                                          \
     }                                                                                                       \
     cudaError_t launch_step_tma_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,             \
                                          const void *consts, const Shift &sh, const TmaMaps &m,             \

@@ -27,17 +27,18 @@ STORAGE_BYTES = {lbm.FP64: 8, lbm.FP32: 4, lbm.FP16S: 2}
 
 
 def footprint_bytes(params: dict) -> int:
-    """Device bytes of one instance: two population copies (32 planes), two
-    copies of the 7 auxiliary planes, sigma, and the reduction workspace,
-    rows padded to 32 elements."""
+    """Device bytes of one instance: two population copies (9 f planes and
+    23 h, g, l planes), two copies of the 7 auxiliary planes, sigma, and the
+    reduction workspace, rows padded to 32 elements."""
     nx, ny, prec = int(params["nx"]), int(params["ny"]), int(params["precision"])
     pitch = (nx + 31) // 32 * 32
     plane = pitch * ny
     sb = STORAGE_BYTES[prec]
+    fb = 8 if prec == lbm.FP64 else 4        # half storage keeps f in single precision
     ab = 8 if prec == lbm.FP64 else 4
     blocks = ((nx + 31) // 32) * ((ny + 7) // 8)
-    ws = blocks * 32 + (3 * ny + 8) * 8 + 4096
-    return 2 * 32 * plane * sb + 2 * 7 * plane * ab + plane * ab + ws
+    ws = blocks * 7 * 8 + (3 * ny + 8) * 8 + nx * 8 + 4096
+    return 2 * (9 * fb + 23 * sb) * plane + 2 * 7 * plane * ab + plane * ab + ws
 
 
 @dataclasses.dataclass

@@ -380,6 +380,10 @@ def test_error_codes(lbm):
     with pytest.raises(lbm.LBMError) as e:
         s.set("psi", np.zeros((8, 16)))
     assert e.value.code == lbm.ERR_BADPARAM
+    half = lbm.Simulation(W.params(nx=16, ny=8, R0=4.0, precision=W.FP16S))
+    with pytest.raises(lbm.LBMError) as e:
+        half.configure(lbm.STEP_TMA, 4)
+    assert e.value.code == lbm.ERR_BADPARAM
     thin = lbm.Simulation(W.params(nx=16, ny=2, R0=1.0))
     thin.init_psi(np.zeros((2, 16)))
     with pytest.raises(lbm.LBMError) as e:

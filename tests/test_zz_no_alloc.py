@@ -42,9 +42,10 @@ def test_noalloc_observables_match_lbm_observables(prec):
     sim.init_droplet(R, xc, yc, 5)
     pitch = (nx + 31) // 32 * 32
     elem = {W.FP64: 8, W.FP32: 4, W.FP16S: 2}[prec]
+    f_elem = 8 if prec == W.FP64 else 4      # half storage keeps f in single precision
     aux_elem = 8 if prec == W.FP64 else 4
     plane = pitch * ny
-    pop_bytes, aux_bytes = 32 * plane * elem, 7 * plane * aux_elem
+    pop_bytes, aux_bytes = 9 * plane * f_elem + 23 * plane * elem, 7 * plane * aux_elem
 
     out = torch.zeros(C.sizeof(lbm.Obs), dtype=torch.uint8, device="cuda")
     init = lbm.Obs()
