@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 BYTES_PER_LU = {"f64": 2 * (32 + 7) * 8, "f32": 2 * (32 + 7) * 4, "f16s": 2 * (9 * 4 + 23 * 2) + 2 * 7 * 4}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_MD = os.path.join(ROOT, "profiles", "k_step_f32_production_512x256.md")
-KERNEL_SOURCES = ["lbm_kernels.cuh", "step_f32.cu", "lbm_internal.h", "philox.h"]
+KERNEL_SOURCES = ["lbm_kernels.cuh", "lbm_launch.cuh", "step_f32.cu", "lbm_internal.h", "philox.h"]
 
 
 def kernel_source_hash() -> str:
@@ -57,10 +57,11 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(precision: str):
+def profiled_traffic(precision: str, workload: str):
     """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    if precision != "f32" or not os.path.exists(PROFILE_MD):
+    summary, if it was taken on the current kernel source (the summary
+    covers the FP32 production lattice only)."""
+    if precision != "f32" or workload != "production" or not os.path.exists(PROFILE_MD):
         return None
     text = open(PROFILE_MD).read()
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
@@ -292,7 +293,7 @@ def run_gpu(args, world, rank, local):
     alg_bytes = bpl * cells
     achieved = alg_bytes / (launch_us * 1e-6) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = profiled_traffic(args.precision)
+    traffic = profiled_traffic(args.precision, args.workload)
 
     # context for the fraction: a plain device copy moving the same bytes
     # (half read, half written), timed the same way (L2 flushed, events);
@@ -360,7 +361,10 @@ def run_gpu(args, world, rank, local):
                      "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_lu": bpl,
                      "copy_same_bytes": {"launch_us": copy_us, "gbs": alg_bytes / (copy_us * 1e-6) / 1e9,
                                          "frac": alg_bytes / (copy_us * 1e-6) / 1e9 / peak,
-                                         "note": "device-to-device copy of the same byte count, same timing"}},
+                                         "note": "device-to-device copy of the same byte count, same timing"},
+                     **({"note": "FP64 arithmetic runs at a small fraction of the FP32 rate on this part: "
+                                 "the FP64 step is arithmetic-bound, far from the HBM roofline"}
+                        if args.precision == "f64" else {})},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": ctypes.sizeof(lbm.Obs), "steps": k_e2e},

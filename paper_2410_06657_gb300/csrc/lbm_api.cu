@@ -86,6 +86,10 @@ void derive(const lbm_params &p, Consts<double> &c) {
     c.one_m_rsl = 1.0 - c.rho[0] / c.rho[1];
     c.Cref_Tw = c.Cref * p.T_w;
     c.T_init = p.T_init;
+    c.om_f = 1.0 / c.tau_f;
+    c.pre_f = 1.0 - 0.5 / c.tau_f;
+    c.four_over_W = 4.0 / p.W;
+    c.three_over_Cref = 3.0 / c.Cref;          // 1 / (C_p,ref c_s^2)
 }
 
 template <typename T>
@@ -103,6 +107,8 @@ Consts<T> cast_consts(const Consts<double> &d) {
     c.tau_f = T(d.tau_f); c.phi_bot = T(d.phi_bot); c.phi_top = T(d.phi_top); c.wet = T(d.wet);
     c.T_m = T(d.T_m); c.W = T(d.W); c.one_m_rsl = T(d.one_m_rsl); c.Cref_Tw = T(d.Cref_Tw);
     c.T_init = T(d.T_init);
+    c.om_f = T(d.om_f); c.pre_f = T(d.pre_f); c.four_over_W = T(d.four_over_W);
+    c.three_over_Cref = T(d.three_over_Cref);
     return c;
 }
 
@@ -466,7 +472,9 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->qdot = reinterpret_cast<double *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b +
                                          err_b);
     h->ws.nblocks = nb;
-    if (cudaMemset(h->err, 0, err_b) != cudaSuccess) {
+    if (cudaMemset(h->err, 0, err_b) != cudaSuccess || cudaMemset(h->ws_max_base, 0x00, h->ws_max_bytes) != cudaSuccess ||
+        cudaMemset(h->ws_min_base, 0xFF, h->ws_min_bytes) != cudaSuccess ||
+        cudaMemset(h->ws_u32_base, 0x00, h->ws_u32_bytes) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->ws_mem);
         cudaFree(h->mem);
@@ -559,9 +567,8 @@ int lbm_step(lbm_handle *h, int64_t n) {
 int lbm_observables_async(lbm_handle *h) {
     if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
     if (!h->inited) return fail(LBM_ERR_STATE, "observables before init");
-    CK(cudaMemsetAsync(h->ws_max_base, 0x00, h->ws_max_bytes, h->st));
-    CK(cudaMemsetAsync(h->ws_min_base, 0xFF, h->ws_min_bytes, h->st));
-    CK(cudaMemsetAsync(h->ws_u32_base, 0x00, h->ws_u32_bytes, h->st));
+    // the workspace starts at the identities of its reductions (set at
+    // creation) and the reduction's last block restores them
     Scalars sc;
     sc.step = h->step;
     sc.alpha_l = h->P.alpha_l;

@@ -28,6 +28,8 @@ struct Consts {
     T one_m_rsl;     // 1 - rho_s / rho_l
     T Cref_Tw;       // C_p,ref T_w (anti-bounce-back value of g at the cold wall)
     T T_init;
+    // reciprocals of the single-precision collision form
+    T om_f, pre_f, four_over_W, three_over_Cref;
 };
 
 // Reference state subtracted before half-precision storage (weight-shifted

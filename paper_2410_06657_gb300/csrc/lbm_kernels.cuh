@@ -6,7 +6,8 @@
 // Included once by each precision's translation unit.
 //
 // Memory layout (all structure-of-arrays, x fastest, rows padded to `pitch`):
-//   pop[b]  : 32 planes  f_0..8 | h_0..8 | g_0..8 | l_0..4
+//   pop[b]  : 32 planes  f_0..8 | h_0..8 | g_0..8 | l_0..4 (half storage:
+//             the f planes in float, the others in half)
 //   aux[b]  : 7 planes   f_s, mdot, rho C_p T mdot, psi u_x, psi u_y, p, S
 //             of the previous step (read by the next step's stencils, so the
 //             step reads copy b and writes copy 1-b)
@@ -425,7 +426,9 @@ __device__ __forceinline__ void fill_ghosts(TileSmem<T, BY> &sm, const Consts<T>
 // Row a2-a9 for one own cell: stencils from the shared-memory tile, forces,
 // flow macros, the four collisions and the push into the other copy.  PS
 // supplies the cell's time-n populations (registers or shared memory).
-template <typename S, typename T, typename A, int BY, typename PopSrc>
+// EDGE: the tile touches a wall row, so destinations may leave the lattice;
+// interior tiles skip the per-direction wall tests.
+template <typename S, typename T, typename A, int BY, bool EDGE, typename PopSrc>
 __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
                                           const TileSmem<T, BY> &sm, const PopSrc &PS, int tx, int ty, int x,
                                           int y, const Macro<T> &m, T fs_prev, T pux_prev, T puy_prev) {
@@ -474,7 +477,14 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     const T mu = chi(m.fs, ps, c.mu), kth = chi(m.fs, ps, c.kth);
     const T sig = chi(m.fs, ps, c.sig), cp = chi(m.fs, ps, c.cp);
     const T mdot = c.one_m_rsl * (m.fs - fs_prev);                 // Eq. (ns1)
-    const T usx = (jx + T(0.5) * Fx) / r, usy = (jy + T(0.5) * Fy) / r;
+    // Single precision evaluates the collisions in an algebraically equal
+    // form with the 1/c_s^2 factors folded (c_s^2 = 1/3), shared terms
+    // hoisted and one reciprocal per divisor; double precision keeps the
+    // printed operation order.
+    constexpr bool FAST = sizeof(T) == 4;
+    const T ir = FAST ? T(1) / r : T(0);
+    const T usx = FAST ? (jx + T(0.5) * Fx) * ir : (jx + T(0.5) * Fx) / r;
+    const T usy = FAST ? (jy + T(0.5) * Fy) * ir : (jy + T(0.5) * Fy) / r;
     const T fx = m.fs * (T(0) - usx), fy = m.fs * (T(0) - usy);    // u_s = 0
     const T ux = usx + T(0.5) * fx, uy = usy + T(0.5) * fy;        // Eq. (Computed_u)
     const T rfx = r * fx, rfy = r * fy;
@@ -483,7 +493,7 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     const T Fty = Fy - gpy + cs2<T>() * grhoy + cs2<T>() * gSy;
     const T uF = ux * Ftx + uy * Fty;
     const T R0 = w9<T>(0) * (Sn - uF / cs2<T>());
-    const T tau_h = mu / r / cs2<T>() + T(0.5);
+    const T tau_h = FAST ? T(3) * mu * ir + T(0.5) : mu / r / cs2<T>() + T(0.5);
     T sh_ = T(0);
 #pragma unroll
     for (int i = 1; i < 9; i++) sh_ += PS.h(i);
@@ -499,17 +509,13 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         return row + (uint32_t)(cxv < 0 ? xm : (cxv > 0 ? xp : x));
     };
 
-    // Single precision evaluates the collisions in an algebraically equal
-    // form with the 1/c_s^2 factors folded (c_s^2 = 1/3) and the shared
-    // terms hoisted; double precision keeps the printed operation order.
-    constexpr bool FAST = sizeof(T) == 4;
     const T uu_ = ux * ux + uy * uy;
     const T B15 = T(1.5) * uu_;                    // u.u / (2 c_s^2)
 
     // a7: flow
     {
-        const T pre = T(1) - T(1) / (T(2) * tau_h);
         const T om = T(1) / tau_h;
+        const T pre = FAST ? T(1) - T(0.5) * om : T(1) - T(1) / (T(2) * tau_h);
         const T A3 = T(3) * p;                      // p / c_s^2
         const T S3 = Sn - T(3) * uF;                // S - u.F~ / c_s^2
         const T Gx = Fx + rfx, Gy = Fy + rfy;
@@ -536,7 +542,7 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                 post = PS.h(i) - (PS.h(i) - heq) / tau_h + pre * Ri;
             }
             const int yt = y + CY[i];
-            if (yt < 0 || yt >= ny)
+            if (EDGE && (yt < 0 || yt >= ny))
                 Pol<S, T>::st_sr(io.h_out + (OPP9[i] * P + k), post, T(0), sh.h_scale, bits13(rb, i));
             else
                 Pol<S, T>::st_sr(io.h_out + (i * P + dest(i, CX[i], CY[i])), post, T(0), sh.h_scale,
@@ -552,15 +558,17 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         puy_prev = puy;
         // interface normal, regularised where grad psi vanishes (Sec. 2)
         const T gn = sqrt(gpsix * gpsix + gpsiy * gpsiy);
-        const T nxv = gpsix / (gn + T(1e-4)), nyv = gpsiy / (gn + T(1e-4));
-        const T lam = T(4) * ps * (T(1) - ps) / c.W;
-        const T pre = T(1) - T(1) / (T(2) * c.tau_f);
+        const T ign = FAST ? T(1) / (gn + T(1e-4)) : T(0);
+        const T nxv = FAST ? gpsix * ign : gpsix / (gn + T(1e-4));
+        const T nyv = FAST ? gpsiy * ign : gpsiy / (gn + T(1e-4));
+        const T lam = FAST ? c.four_over_W * ps * (T(1) - ps) : T(4) * ps * (T(1) - ps) / c.W;
+        const T pre = FAST ? c.pre_f : T(1) - T(1) / (T(2) * c.tau_f);
         const T ax = dtx + cs2<T>() * lam * nxv;
         const T ay = dty + cs2<T>() * lam * nyv;
-        const T om = T(1) / c.tau_f;
+        const T om = FAST ? c.om_f : T(1) / c.tau_f;
         const T pmd = ps * mdot;
         uint32_t rb[4] = {0u, 0u, 0u, 0u};
-        if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 0u);
+        if constexpr (Pol<typename FStore<S>::type, T>::shifted) sr_block(rb, k, io.sr_step, 0u);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             T post;
@@ -576,26 +584,25 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                 post = PS.f(i) - (PS.f(i) - feq) / c.tau_f + pre * Fi;
             }
             const int yt = y + CY[i];
-            if (yt < 0 || yt >= ny) {
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
+            if (EDGE && (yt < 0 || yt >= ny)) {
+                if constexpr (Pol<typename FStore<S>::type, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
                 Pol<typename FStore<S>::type, T>::st_sr(io.f_out + (OPP9[i] * P + k), post, ro.f[OPP9[i]], sh.f_scale,
                                                         bits13(rb, i));
             } else {
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
+                if constexpr (Pol<typename FStore<S>::type, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
                 Pol<typename FStore<S>::type, T>::st_sr(io.f_out + (i * P + dest(i, CX[i], CY[i])), post, ro.f[i],
-                                                        sh.f_scale,
-                                 bits13(rb, i));
+                                                        sh.f_scale, bits13(rb, i));
             }
         }
     }
     // a8: enthalpy (Sec. 3.3)
     T Qn;
     {
-        const T tau_g = kth / (r * c.Cref * cs2<T>()) + T(0.5);
+        const T tau_g = FAST ? kth * ir * c.three_over_Cref + T(0.5) : kth / (r * c.Cref * cs2<T>()) + T(0.5);
         Qn = r * cp * m.T_ * mdot;
         const T uu = uu_;
-        const T pre = T(1) - T(1) / (T(2) * tau_g);
         const T om = T(1) / tau_g;
+        const T pre = FAST ? T(1) - T(0.5) * om : T(1) - T(1) / (T(2) * tau_g);
         const T CT = c.Cref * m.T_, cpT = cp * m.T_;
         uint32_t rb[4] = {0u, 0u, 0u, 0u};
         if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 2u);
@@ -618,11 +625,11 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                 post = PS.g(i) - (PS.g(i) - geq) / tau_g + pre * (w9<T>(i) * Qn);
             }
             const int yt = y + CY[i];
-            if (yt < 0) {            // cold wall: anti-bounce-back to C_p,ref T_w
+            if (EDGE && yt < 0) {    // cold wall: anti-bounce-back to C_p,ref T_w
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
                 Pol<S, T>::st_sr(io.g_out + (OPP9[i] * P + k),
                                  -post + T(2) * w9<T>(i) * c.Cref_Tw, ro.g[OPP9[i]], sh.g_scale, bits13(rb, i));
-            } else if (yt >= ny) {   // top wall: adiabatic bounce-back
+            } else if (EDGE && yt >= ny) {   // top wall: adiabatic bounce-back
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
                 Pol<S, T>::st_sr(io.g_out + (OPP9[i] * P + k), post, ro.g[OPP9[i]], sh.g_scale,
                                  bits13(rb, i));
@@ -635,7 +642,7 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     }
     // a6: potential (Sec. 3.4), one sweep inside the fused step
     {
-        const T tau_l = sig / cs2<T>() + T(0.5);
+        const T tau_l = FAST ? T(3) * sig + T(0.5) : sig / cs2<T>() + T(0.5);
         const T om = T(1) / tau_l;
         uint32_t rb[4] = {0u, 0u, 0u, 0u};
         if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 3u);
@@ -648,7 +655,7 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             else
                 post = PS.l(i) - (PS.l(i) - leq) / tau_l;
             const int yt = y + CY5[i];
-            if (yt < 0 || yt >= ny) {   // electrodes: anti-bounce-back
+            if (EDGE && (yt < 0 || yt >= ny)) {   // electrodes: anti-bounce-back
                 const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
                 if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
                 Pol<S, T>::st_sr(io.l_out + (OPP5[i] * P + k), -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]],
@@ -747,7 +754,10 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     __syncthreads();
     if (!own) return;
     const StashPops<T, BY> PS{stash, ty, tx};
-    step_cell<S, T, A, BY>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev);
+    if (y0 == 0 || y0 + BY >= ny)
+        step_cell<S, T, A, BY, true>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev);
+    else
+        step_cell<S, T, A, BY, false>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev);
 }
 
 // Blocks per SM the single-precision step asks the register allocator for:
@@ -990,8 +1000,11 @@ __device__ __forceinline__ void step_tile_tma(const StepIO<S, T, A> &io, const C
     const int oa = (ty + 1) * G::BWA + tx + G::PADA;
     BoxPops<S, T> PS{bF + o, bL + o, G::PL, {}, fsc, gsc, hsc, lsc};
     make_refs<S, T>(PS.rf, sh, c, y, ny);
-    step_cell<S, T, A, BY>(io, c, sh, sm, PS, tx, ty, xg, y, m, fs_prev, T(bA[AUX_PUX * G::PLA + oa]),
-                           T(bA[AUX_PUY * G::PLA + oa]));
+    const T pxp = T(bA[AUX_PUX * G::PLA + oa]), pyp = T(bA[AUX_PUY * G::PLA + oa]);
+    if (y0 == 0 || y0 + BY >= ny)
+        step_cell<S, T, A, BY, true>(io, c, sh, sm, PS, tx, ty, xg, y, m, fs_prev, pxp, pyp);
+    else
+        step_cell<S, T, A, BY, false>(io, c, sh, sm, PS, tx, ty, xg, y, m, fs_prev, pxp, pyp);
 }
 
 template <typename S, typename T, typename A, int BY>
@@ -1165,498 +1178,4 @@ __global__ void k_init(DevState s, const double *psi_dev, double R, double xc, d
     reinterpret_cast<A *>(s.sigma)[k] = A(chi(T(0), ps, c.sig));
 }
 
-// ---------------------------------------------------------------------------
-// Observables (row a10): FP64 reductions over the tile grid.  Each block
-// handles a 32 x 8 tile plus a one-cell halo (for q_v's stencils and the
-// interface crossings) and leaves block partial sums and order-independent
-// max/min candidates in the workspace; the last block to finish reduces them.
-// ---------------------------------------------------------------------------
-constexpr int OBS_BY = 8;
-
-static __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) {
-    atomicMax(a, (unsigned long long)__double_as_longlong(v));   // v >= 0: bits order like values
-}
-static __device__ __forceinline__ void atomic_min_pos(unsigned long long *a, double v) {
-    atomicMin(a, (unsigned long long)__double_as_longlong(v));
-}
-
-template <typename S, typename T, typename A>
-__device__ __forceinline__ void obs_macros(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
-                                           int y, int ny, const Consts<double> &c, const Shift &sh,
-                                           Macro<double> &m) {
-    Refs<T> rf;
-    Consts<T> ct;      // only phi_bot/phi_top/ny are used by make_refs
-    ct.phi_bot = T(c.phi_bot);
-    ct.phi_top = T(c.phi_top);
-    make_refs<S, T>(rf, sh, ct, y, ny);
-    double f[9], g[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        f[i] = double(Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale));
-        g[i] = double(Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale));
-    }
-    double l1234 = 0.0;
-#pragma unroll
-    for (int i = 1; i < 5; i++) l1234 += double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
-    local_macros<double>(f, g, l1234, double(aux[AUX_FS * P + k]), double(aux[AUX_MDOT * P + k]),
-                         double(aux[AUX_Q * P + k]), c, m);
-}
-
-// Local macros of one cell in the arithmetic type T (the step's own type).
-template <typename S, typename T, typename A>
-__device__ __forceinline__ void cell_macros_t(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
-                                              int y, int ny, const Consts<T> &c, const Shift &sh, Macro<T> &m) {
-    Refs<T> rf;
-    make_refs<S, T>(rf, sh, c, y, ny);
-    T f[9], g[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        f[i] = Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale);
-        g[i] = Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale);
-    }
-    T l1234 = T(0);
-#pragma unroll
-    for (int i = 1; i < 5; i++) l1234 += Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale);
-    local_macros<T>(f, g, l1234, T(aux[AUX_FS * P + k]), T(aux[AUX_MDOT * P + k]), T(aux[AUX_Q * P + k]), c, m);
-}
-
-static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc);
-
-template <typename S, typename T, typename A>
-__global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<T> c, Shift sh,
-                                                    ObsScratch ws, Scalars sc) {
-    // per-cell values and the q_v stencils in the step's arithmetic; sums
-    // within a warp in the step's type (FP64 adds are slow on this part;
-    // a 32-term sum of single-precision values loses ~1e-7), across warps
-    // and blocks in FP64; interface crossings and the front in FP64
-    using R = typename std::conditional<sizeof(T) == 8, double, float>::type;
-    __shared__ T s_psi[OBS_BY + 2][34], s_fs[OBS_BY + 2][34], s_eps[OBS_BY + 2][34], s_phi[OBS_BY + 2][34];
-    __shared__ T s_H[OBS_BY + 2][34], s_Tm[OBS_BY + 2][34];
-    __shared__ double s_red[OBS_NSUM][32 * OBS_BY / 32];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int nx = s.nx, ny = s.ny;
-    const long long P = s.plane;
-    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
-    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
-    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * OBS_BY;
-    // fill the extended tile (own + halo), ghost rows as in the step
-    for (int r = tid; r < 34 * (OBS_BY + 2); r += 32 * OBS_BY) {
-        const int ex = r % 34, ey = r / 34;
-        const int yy = y0 - 1 + ey;
-        if (yy < 0 || yy >= ny) continue;
-        int xx = (x0 - 1 + ex) % nx;
-        if (xx < 0) xx += nx;
-        Macro<T> m;
-        cell_macros_t<S, T, A>(pc, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, m);
-        s_psi[ey][ex] = m.psi;
-        s_fs[ey][ex] = m.fs;
-        s_eps[ey][ex] = m.eps;
-        s_phi[ey][ex] = m.phi;
-        s_H[ey][ex] = m.H;
-        s_Tm[ey][ex] = m.T_;
-    }
-    __syncthreads();
-    if (y0 == 0 && tid < 34) {
-        s_eps[0][tid] = s_eps[1][tid];
-        s_phi[0][tid] = T(2) * c.phi_bot - s_phi[1][tid];
-    }
-    const int et = ny - y0 + 1;
-    if (et >= 1 && et <= OBS_BY + 1 && tid >= 64 && tid < 98) {
-        s_eps[et][tid - 64] = s_eps[et - 1][tid - 64];
-        s_phi[et][tid - 64] = T(2) * c.phi_top - s_phi[et - 1][tid - 64];
-    }
-    __syncthreads();
-
-    const int x = x0 + tx, y = y0 + ty;
-    R v_psi = R(0), v_H = R(0), v_fs = R(0), v_q = R(0), v_liq = R(0), v_liqu = R(0), v_qdot = R(0);
-    unsigned int rowbits = 0u;                // this lane's row flags (one warp = one row)
-    if (x < nx && y < ny) {
-        const int ex = tx + 1, ey = ty + 1;
-        Macro<T> m;                           // this cell's values, from the extended tile
-        m.psi = s_psi[ey][ex];
-        m.fs = s_fs[ey][ex];
-        m.eps = s_eps[ey][ex];
-        m.H = s_H[ey][ex];
-        const long long k = (long long)y * s.pitch + x;
-        // substrate heat flux (R24): -k (4 T_1 - T_2 - 3 T_0) / 2 on row 0
-        if (y == 0 && ny >= 3) {
-            const T kth0 = chi(m.fs, m.psi, c.kth);
-            v_qdot = R(-kth0 * (T(4) * s_Tm[2][ex] - s_Tm[3][ex] - T(3) * s_Tm[1][ex]) / T(2));
-        }
-        // Peclet number (R25): liquid content psi - f_s weights |psi u| / psi
-        {
-            const T w = m.psi - m.fs;
-            if (w > T(0)) {
-                const T ux = T(aux[AUX_PUX * P + k]), uy = T(aux[AUX_PUY * P + k]);
-                const T sp = sqrt(ux * ux + uy * uy);
-                v_liq = R(w);
-                v_liqu = R(w * sp / m.psi);
-            }
-        }
-        T gex, gey, gphx, gphy;
-        grad_s<T, 34>(s_eps, ex, ey, gex, gey);
-        grad_s<T, 34>(s_phi, ex, ey, gphx, gphy);
-        const T lphi = lap_s<T, 34>(s_phi, ex, ey);
-        v_q = R(-(gex * gphx + gey * gphy + m.eps * lphi));
-        v_psi = R(m.psi);
-        v_H = R(m.H);
-        v_fs = R(m.fs);
-        if (!isfinite(v_psi) || !isfinite(v_H)) atomicOr(ws.bad, 1u);
-        const double a = double(s_psi[ey][ex]);
-        // column crossing (height): psi(y) >= 1/2 > psi(y+1)
-        if (a >= 0.5) {
-            rowbits |= 1u;
-            if (y == ny - 1) {
-                atomic_max_pos(&ws.maxv[0], (double)ny);
-            } else {
-                const double b = double(s_psi[ey + 1][ex]);
-                if (b < 0.5) atomic_max_pos(&ws.maxv[0], y + (a - 0.5) / (a - b) + 0.5);
-            }
-            // row crossings (width): left edge needs x >= 1, right edge x <= nx - 2
-            if (x >= 1) {
-                const double bl = double(s_psi[ey][ex - 1]);
-                if (bl < 0.5) {
-                    atomic_min_pos(&ws.minv[1 + y], (x - 1) + (0.5 - bl) / (a - bl));
-                    rowbits |= 2u;
-                }
-            }
-            if (x + 1 < nx) {
-                const double br = double(s_psi[ey][ex + 1]);
-                if (br < 0.5) {
-                    atomic_max_pos(&ws.maxv[2 + y], x + (a - 0.5) / (a - br));
-                    rowbits |= 4u;
-                }
-            }
-        }
-        // freezing front on the centre column (lowest f_s = 1/2 crossing)
-        if (x == nx / 2) {
-            const double fa = double(s_fs[ey][ex]);
-            if (y == 0 && fa >= 0.5) atomicOr(ws.bad + 1, 1u);
-            if (fa >= 0.5) {
-                if (y == ny - 1) {
-                    atomic_min_pos(&ws.minv[0], (double)ny);
-                } else {
-                    const double fb = double(s_fs[ey + 1][ex]);
-                    if (fb < 0.5) atomic_min_pos(&ws.minv[0], y + (fa - 0.5) / (fa - fb) + 0.5);
-                }
-            }
-        }
-    }
-    // row flags: OR across the warp (all lanes share the row), one atomic
-    {
-        unsigned int b = rowbits;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
-        if (tx == 0 && b && y < ny) atomicOr(&ws.rowany[y], b);
-    }
-    // block sums (fixed shuffle order; warps combined in FP64)
-    R v[OBS_NSUM] = {v_psi, v_H, v_fs, v_q, v_liq, v_liqu, v_qdot};
-#pragma unroll
-    for (int j = 0; j < OBS_NSUM; j++) {
-        R t = v[j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (tx == 0) s_red[j][ty] = double(t);
-    }
-    __syncthreads();
-    if (tid < OBS_NSUM) {
-        double t = 0.0;
-        for (int w = 0; w < OBS_BY; w++) t += s_red[tid][w];
-        ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * OBS_NSUM + tid] = t;
-    }
-    // the last block to finish reduces every block's results
-    __shared__ bool s_last;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(ws.bad + 2, 1u) == (unsigned int)(gridDim.x * gridDim.y) - 1u;
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        obs_final(nx, ny, ws, sc);
-    }
-}
-
-// psi = 1/2 extent of row y: 0 without liquid, nx without a left or right
-// crossing (the row is liquid across the periodic seam), else right - left.
-// (Other blocks wrote the workspace with atomics during this launch: read
-// it from L2.)
-static __device__ __forceinline__ double row_extent_of(const ObsScratch &ws, int y, int nx) {
-    const unsigned int bits = __ldcg(ws.rowany + y);
-    if (!(bits & 1u)) return 0.0;
-    if ((bits & 6u) != 6u) return (double)nx;
-    return __longlong_as_double((long long)__ldcg(ws.maxv + 2 + y)) -
-           __longlong_as_double((long long)__ldcg(ws.minv + 1 + y));
-}
-
-// Final reduction, run by the last block of k_obs to finish (256 threads):
-// block partial sums in a fixed order (thread-strided, then a fixed shuffle
-// tree), so the result does not depend on which block finishes last.
-static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc) {
-    __shared__ double s[OBS_NSUM][8];
-    __shared__ double s_w[8];
-    const int t = threadIdx.y * blockDim.x + threadIdx.x, lane = t & 31, warp = t >> 5;
-    double acc[OBS_NSUM];
-#pragma unroll
-    for (int j = 0; j < OBS_NSUM; j++) acc[j] = 0.0;
-    for (int b = t; b < ws.nblocks; b += 256)
-#pragma unroll
-        for (int j = 0; j < OBS_NSUM; j++) acc[j] += __ldcg(ws.partials + (long long)b * OBS_NSUM + j);
-    double wmax = 0.0;
-    for (int y = t; y < ny; y += 256) wmax = fmax(wmax, row_extent_of(ws, y, nx));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int j = 0; j < OBS_NSUM; j++) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
-        wmax = fmax(wmax, __shfl_down_sync(0xffffffffu, wmax, o));
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < OBS_NSUM; j++) s[j][warp] = acc[j];
-        s_w[warp] = wmax;
-    }
-    __syncthreads();
-    if (t == 0) {
-        double tot[OBS_NSUM];
-        for (int j = 0; j < OBS_NSUM; j++) tot[j] = 0.0;
-        double wm = 0.0;
-        for (int w = 0; w < 8; w++) {
-            for (int j = 0; j < OBS_NSUM; j++) tot[j] += s[j][w];
-            wm = fmax(wm, s_w[w]);
-        }
-        for (int j = 0; j < OBS_NSUM; j++) s[j][0] = tot[j];
-        s_w[0] = wm;
-        lbm_obs *o = ws.obs;
-        const double mass = s[0][0], enth = s[1][0], solid = s[2][0], charge = s[3][0];
-        o->step = sc.step;
-        o->Fo = sc.alpha_l * (double)sc.step / (sc.R0 * sc.R0);
-        o->mass = mass;
-        o->enthalpy = enth;
-        o->solid = solid;
-        o->charge = charge;
-        o->frozen_fraction = (mass != 0.0) ? solid / mass : 0.0;
-        o->height = __longlong_as_double((long long)__ldcg(ws.maxv));
-        o->width = s_w[0];
-        o->aspect = (o->width > 0.0) ? o->height / o->width : 0.0;
-        o->R_tr = 0.5 * row_extent_of(ws, 0, nx);
-        if (__ldcg(ws.bad + 1)) {
-            const unsigned long long fmin = __ldcg(ws.minv);
-            o->front = (fmin == ~0ull) ? (double)ny : __longlong_as_double((long long)fmin);
-        } else {
-            o->front = 0.0;
-        }
-        if (__ldcg(&o->t_fre) < 0 && o->frozen_fraction >= 0.99) o->t_fre = sc.step;
-        o->Fo_fre = (o->t_fre >= 0) ? sc.alpha_l * (double)o->t_fre / (sc.R0 * sc.R0) : -1.0;
-        o->status = __ldcg(ws.bad) ? LBM_ERR_DIVERGED : LBM_OK;
-        o->reserved = 0;
-        const double liq = s[4][0], liqu = s[5][0];
-        o->Pe = (liq > 0.0) ? 2.0 * sc.R0 * (liqu / liq) / sc.alpha_l : 0.0;     // R25
-        o->Qdot = s[6][0];                                                      // R24
-    }
-}
-
-// Local substrate heat flux (R24), one thread per column, in the step's
-// arithmetic: -k(x,0) (4 T(x,1) - T(x,2) - 3 T(x,0)) / 2.  Needs ny >= 3.
-template <typename S, typename T, typename A>
-__global__ void k_heat_flux(DevState s, int cur, int lcur, Consts<T> c, Shift sh, double *out) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= s.nx) return;
-    const long long P = s.plane;
-    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
-    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
-    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
-    Macro<T> m0, m1, m2;
-    cell_macros_t<S, T, A>(pc, lb, aux, P, x, 0, s.ny, c, sh, m0);
-    cell_macros_t<S, T, A>(pc, lb, aux, P, (long long)s.pitch + x, 1, s.ny, c, sh, m1);
-    cell_macros_t<S, T, A>(pc, lb, aux, P, 2LL * s.pitch + x, 2, s.ny, c, sh, m2);
-    const T k0 = chi(m0.fs, m0.psi, c.kth);
-    out[x] = double(-k0 * (T(4) * m1.T_ - m2.T_ - T(3) * m0.T_) / T(2));
-}
-
-// ---------------------------------------------------------------------------
-// Field access for tests and hand-over: stored planes <-> host doubles.
-// ---------------------------------------------------------------------------
-template <typename S, typename T, typename A>
-__global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c, Shift sh, double *out) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= s.nx || y >= s.ny) return;
-    const long long P = s.plane, k = (long long)y * s.pitch + x;
-    const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
-    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
-    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
-    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
-    Refs<T> rf;
-    Consts<T> ct;
-    ct.phi_bot = T(c.phi_bot);
-    ct.phi_top = T(c.phi_top);
-    make_refs<S, T>(rf, sh, ct, y, s.ny);
-    if (field == LBM_FIELD_F) {
-        for (int i = 0; i < 9; i++)
-            out[i * N + o] = double(Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale));
-    } else if (field == LBM_FIELD_H) {
-        for (int i = 0; i < 9; i++) out[i * N + o] = double(Pol<S, T>::ld(pc.h + i * P + k, T(0), 1.0f / sh.h_scale));
-    } else if (field == LBM_FIELD_G) {
-        for (int i = 0; i < 9; i++) out[i * N + o] = double(Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale));
-    } else if (field == LBM_FIELD_L) {
-        for (int i = 0; i < 5; i++) out[i * N + o] = double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
-    } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
-        out[o] = double(aux[(field - LBM_FIELD_FS_PREV) * P + k]);
-    } else if (field == LBM_FIELD_SIGMA) {
-        out[o] = double(reinterpret_cast<const A *>(s.sigma)[k]);
-    } else {
-        Macro<double> m;
-        obs_macros<S, T, A>(pc, lb, aux, P, k, y, s.ny, c, sh, m);
-        out[o] = field == LBM_FIELD_PSI ? m.psi
-               : field == LBM_FIELD_FSOLID ? m.fs
-               : field == LBM_FIELD_T ? m.T_
-               : field == LBM_FIELD_PHI ? m.phi
-               : m.H;
-    }
-}
-
-template <typename S, typename T, typename A>
-__global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shift sh, const double *in) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= s.nx || y >= s.ny) return;
-    const long long P = s.plane, k = (long long)y * s.pitch + x;
-    const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
-    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
-    S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
-    A *aux = reinterpret_cast<A *>(cur ? s.aux[1] : s.aux[0]);
-    Refs<T> rf;
-    make_refs<S, T>(rf, sh, c, y, s.ny);
-    if (field == LBM_FIELD_F) {
-        for (int i = 0; i < 9; i++)
-            Pol<typename FStore<S>::type, T>::st(pc.f + i * P + k, T(in[i * N + o]), rf.f[i], sh.f_scale);
-    } else if (field == LBM_FIELD_H) {
-        for (int i = 0; i < 9; i++) Pol<S, T>::st(pc.h + i * P + k, T(in[i * N + o]), T(0), sh.h_scale);
-    } else if (field == LBM_FIELD_G) {
-        for (int i = 0; i < 9; i++) Pol<S, T>::st(pc.g + i * P + k, T(in[i * N + o]), rf.g[i], sh.g_scale);
-    } else if (field == LBM_FIELD_L) {
-        for (int i = 0; i < 5; i++) Pol<S, T>::st(lb + i * P + k, T(in[i * N + o]), rf.l[i], sh.l_scale);
-    } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
-        aux[(field - LBM_FIELD_FS_PREV) * P + k] = A(in[o]);
-    } else if (field == LBM_FIELD_SIGMA) {
-        reinterpret_cast<A *>(s.sigma)[k] = A(in[o]);
-    }
-}
-
 }  // namespace lbm
-
-// ---------------------------------------------------------------------------
-// Launchers for one (S, T, A) triple; SUFFIX names the precision.
-// ---------------------------------------------------------------------------
-#define LBM_DEFINE_LAUNCHERS(SUFFIX, S, T, A)                                                              \
-    namespace lbm {                                                                                         \
-    cudaError_t launch_step_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,                 \
-                                     const void *consts, const Shift &sh, int tile_rows, cudaStream_t st) { \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        dim3 grid((s.nx + 31) / 32, (s.ny + tile_rows - 1) / tile_rows);                                   \
-        static bool r4 = false, r8 = false, r16 = false;                                                    \
-        cudaError_t e = cudaSuccess;                                                                        \
-        switch (tile_rows) {                                                                                \
-        case 4:                                                                                             \
-            e = allow_dynamic_smem(k_step<S, T, A, 4>, stash_bytes<T, 4>(), r4);                            \
-            if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
-            break;                                                                                          \
-        case 8:                                                                                             \
-            e = allow_dynamic_smem(k_step<S, T, A, 8>, stash_bytes<T, 8>(), r8);                            \
-            if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
-            break;                                                                                          \
-        case 16:                                                                                            \
-            e = allow_dynamic_smem(k_step<S, T, A, 16>, stash_bytes<T, 16>(), r16);                         \
-            if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
-            break;                                                                                          \
-        default: return cudaErrorInvalidValue;                                                              \
-        }                                                                                                   \
-        if (e != cudaSuccess) return e;                                                                     \
-        return cudaGetLastError();                                                                          \
-    }                                                                                                       \
-    size_t tma_smem_##SUFFIX(int tile_rows) {                                                              \
-        switch (tile_rows) {                                                                                \
-        case 4: return TmaGeom<S, A, 4>::total + 128;                                                       \
-        case 8: return TmaGeom<S, A, 8>::total + 128;                                                       \
-        case 16: return TmaGeom<S, A, 16>::total + 128;                                                     \
-        default: return 0;                                                                                  \
-        }                                                                                                   \
-    }                                                                                                       \
-    template <int BY>                                                                                       \
-    static cudaError_t launch_tma_by_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,        \
-                                              const Consts<T> &c, const Shift &sh, const TmaMaps &m,        \
-                                              cudaStream_t st) {                                            \
-        if constexpr (!std::is_same<typename FStore<S>::type, S>::value) {                                  \
-            return cudaErrorNotSupported;         /* the tensor boxes assume one storage type */            \
-        } else {                                                                                            \
-            static bool ready = false;                                                                      \
-            if (!ready) {                                                                                   \
-                cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, T, A, BY>,                               \
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,           \
-                                                     (int)TmaGeom<S, A, BY>::total + 128);                  \
-                if (e != cudaSuccess) return e;                                                             \
-                ready = true;                                                                               \
-            }                                                                                               \
-            dim3 grid((s.nx + 31) / 32, (s.ny + BY - 1) / BY);                                              \
-            k_step_tma<S, T, A, BY><<<grid, dim3(32, BY), TmaGeom<S, A, BY>::total + 128, st>>>(            \
-                s, cur, lcur, write_sigma, c, sh, m.fhg[cur], m.l[lcur], m.aux[cur]);                       \
-            return cudaGetLastError();                                                                      \
-        }                                                                                                   \
-    }                                                                                                       \
-    cudaError_t launch_step_tma_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,             \
-                                         const void *consts, const Shift &sh, const TmaMaps &m,             \
-                                         cudaStream_t st) {                                                 \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        switch (m.by) {                                                                                     \
-        case 4: return launch_tma_by_##SUFFIX<4>(s, cur, lcur, write_sigma, c, sh, m, st);                  \
-        case 8: return launch_tma_by_##SUFFIX<8>(s, cur, lcur, write_sigma, c, sh, m, st);                  \
-        case 16: return launch_tma_by_##SUFFIX<16>(s, cur, lcur, write_sigma, c, sh, m, st);                \
-        default: return cudaErrorInvalidValue;                                                              \
-        }                                                                                                   \
-    }                                                                                                       \
-    cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, const void *consts, const Shift &sh,    \
-                                      cudaStream_t st) {                                                    \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
-        k_sweep<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, lcur, c, sh);                                     \
-        return cudaGetLastError();                                                                          \
-    }                                                                                                       \
-    cudaError_t launch_init_##SUFFIX(const DevState &s, const double *psi_dev, double R, double xc,        \
-                                     double yc, const void *consts, const Shift &sh, cudaStream_t st) {    \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
-        k_init<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, psi_dev, R, xc, yc, double(c.W), c, sh);           \
-        return cudaGetLastError();                                                                          \
-    }                                                                                                       \
-    cudaError_t launch_obs_##SUFFIX(const DevState &s, int cur, int lcur, const void *consts,              \
-                                    const Shift &sh, const ObsScratch &ws, const Scalars &sc,               \
-                                    cudaStream_t st) {                                                      \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        dim3 grid((s.nx + 31) / 32, (s.ny + OBS_BY - 1) / OBS_BY);                                          \
-        k_obs<S, T, A><<<grid, dim3(32, OBS_BY), 0, st>>>(s, cur, lcur, c, sh, ws, sc);                     \
-        return cudaGetLastError();                                                                          \
-    }                                                                                                       \
-    cudaError_t launch_heat_flux_##SUFFIX(const DevState &s, int cur, int lcur, const void *consts,        \
-                                          const Shift &sh, double *out, cudaStream_t st) {                  \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        k_heat_flux<S, T, A><<<(s.nx + 127) / 128, 128, 0, st>>>(s, cur, lcur, c, sh, out);                 \
-        return cudaGetLastError();                                                                          \
-    }                                                                                                       \
-    cudaError_t launch_get_##SUFFIX(const DevState &s, int cur, int lcur, int field, const void *consts,   \
-                                    const Shift &sh, double *out, cudaStream_t st) {                        \
-        const Consts<double> &c = *reinterpret_cast<const Consts<double> *>(consts);                      \
-        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
-        k_get<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, field, c, sh, out);                      \
-        return cudaGetLastError();                                                                          \
-    }                                                                                                       \
-    cudaError_t launch_set_##SUFFIX(const DevState &s, int cur, int lcur, int field, const void *consts,   \
-                                    const Shift &sh, const double *in, cudaStream_t st) {                   \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
-        k_set<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, field, c, sh, in);                       \
-        return cudaGetLastError();                                                                          \
-    }                                                                                                       \
-    }

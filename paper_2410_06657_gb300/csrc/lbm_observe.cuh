@@ -1,0 +1,446 @@
+// Observables (row a10), the substrate heat flux and field access of the
+// phase-field LB electrofreezing step (arXiv 2410.06657), templated like
+// the step kernels in lbm_kernels.cuh (storage type S, arithmetic type T,
+// auxiliary type A).  Included once by each precision's translation unit,
+// after lbm_kernels.cuh.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Observables (row a10): FP64 reductions over the tile grid.  Each block
+// handles a 32 x 8 tile plus a one-cell halo (for q_v's stencils and the
+// interface crossings) and leaves block partial sums and order-independent
+// max/min candidates in the workspace; the last block to finish reduces them.
+// ---------------------------------------------------------------------------
+constexpr int OBS_BY = 8;
+
+static __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) {
+    atomicMax(a, (unsigned long long)__double_as_longlong(v));   // v >= 0: bits order like values
+}
+static __device__ __forceinline__ void atomic_min_pos(unsigned long long *a, double v) {
+    atomicMin(a, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void obs_macros(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
+                                           int y, int ny, const Consts<double> &c, const Shift &sh,
+                                           Macro<double> &m) {
+    Refs<T> rf;
+    Consts<T> ct;      // only phi_bot/phi_top/ny are used by make_refs
+    ct.phi_bot = T(c.phi_bot);
+    ct.phi_top = T(c.phi_top);
+    make_refs<S, T>(rf, sh, ct, y, ny);
+    double f[9], g[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        f[i] = double(Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale));
+        g[i] = double(Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale));
+    }
+    double l1234 = 0.0;
+#pragma unroll
+    for (int i = 1; i < 5; i++) l1234 += double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
+    local_macros<double>(f, g, l1234, double(aux[AUX_FS * P + k]), double(aux[AUX_MDOT * P + k]),
+                         double(aux[AUX_Q * P + k]), c, m);
+}
+
+// The stored values one cell's macros need, in the arithmetic type T.
+template <typename T>
+struct CellLoad {
+    T f[9], g[9], l1234, fs_prev, mdot_prev, Q_prev;
+};
+
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void load_cell(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
+                                          int y, int ny, const Consts<T> &c, const Shift &sh, CellLoad<T> &o) {
+    Refs<T> rf;
+    make_refs<S, T>(rf, sh, c, y, ny);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        o.f[i] = Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale);
+        o.g[i] = Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale);
+    }
+    o.l1234 = T(0);
+#pragma unroll
+    for (int i = 1; i < 5; i++) o.l1234 += Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale);
+    o.fs_prev = T(aux[AUX_FS * P + k]);
+    o.mdot_prev = T(aux[AUX_MDOT * P + k]);
+    o.Q_prev = T(aux[AUX_Q * P + k]);
+}
+
+// Local macros of one cell in the arithmetic type T (the step's own type).
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void cell_macros_t(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
+                                              int y, int ny, const Consts<T> &c, const Shift &sh, Macro<T> &m) {
+    Refs<T> rf;
+    make_refs<S, T>(rf, sh, c, y, ny);
+    T f[9], g[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        f[i] = Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale);
+        g[i] = Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale);
+    }
+    T l1234 = T(0);
+#pragma unroll
+    for (int i = 1; i < 5; i++) l1234 += Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale);
+    local_macros<T>(f, g, l1234, T(aux[AUX_FS * P + k]), T(aux[AUX_MDOT * P + k]), T(aux[AUX_Q * P + k]), c, m);
+}
+
+static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc);
+
+template <typename S, typename T, typename A>
+__global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<T> c, Shift sh,
+                                                    ObsScratch ws, Scalars sc) {
+    // per-cell values and the q_v stencils in the step's arithmetic; sums
+    // within a warp in the step's type (FP64 adds are slow on this part;
+    // a 32-term sum of single-precision values loses ~1e-7), across warps
+    // and blocks in FP64; interface crossings and the front in FP64
+    using R = typename std::conditional<sizeof(T) == 8, double, float>::type;
+    __shared__ T s_psi[OBS_BY + 2][34], s_fs[OBS_BY + 2][34], s_eps[OBS_BY + 2][34], s_phi[OBS_BY + 2][34];
+    __shared__ T s_H[OBS_BY + 2][34], s_Tm[OBS_BY + 2][34];
+    __shared__ double s_red[OBS_NSUM][32 * OBS_BY / 32];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int nx = s.nx, ny = s.ny;
+    const long long P = s.plane;
+    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
+    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
+    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * OBS_BY;
+    // fill the extended tile (own + halo), ghost rows as in the step: each
+    // thread takes at most two of the 34 x (OBS_BY + 2) cells and issues the
+    // loads of both before evaluating either
+    static_assert(34 * (OBS_BY + 2) <= 2 * 32 * OBS_BY, "two cells per thread");
+    {
+        CellLoad<T> ld[2];
+        int slot_ex[2], slot_ey[2];
+        bool valid[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int r = tid + q * 32 * OBS_BY;
+            slot_ex[q] = r % 34;
+            slot_ey[q] = r / 34;
+            const int yy = y0 - 1 + slot_ey[q];
+            valid[q] = r < 34 * (OBS_BY + 2) && yy >= 0 && yy < ny;
+            if (valid[q]) {
+                int xx = x0 - 1 + slot_ex[q];
+                xx = xx < 0 ? xx + nx : (xx >= nx ? (xx - nx < nx ? xx - nx : (xx - nx) % nx) : xx);
+                load_cell<S, T, A>(pc, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, ld[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            if (!valid[q]) continue;
+            Macro<T> m;
+            local_macros<T>(ld[q].f, ld[q].g, ld[q].l1234, ld[q].fs_prev, ld[q].mdot_prev, ld[q].Q_prev, c, m);
+            const int ex = slot_ex[q], ey = slot_ey[q];
+            s_psi[ey][ex] = m.psi;
+            s_fs[ey][ex] = m.fs;
+            s_eps[ey][ex] = m.eps;
+            s_phi[ey][ex] = m.phi;
+            s_H[ey][ex] = m.H;
+            s_Tm[ey][ex] = m.T_;
+        }
+    }
+    __syncthreads();
+    if (y0 == 0 && tid < 34) {
+        s_eps[0][tid] = s_eps[1][tid];
+        s_phi[0][tid] = T(2) * c.phi_bot - s_phi[1][tid];
+    }
+    const int et = ny - y0 + 1;
+    if (et >= 1 && et <= OBS_BY + 1 && tid >= 64 && tid < 98) {
+        s_eps[et][tid - 64] = s_eps[et - 1][tid - 64];
+        s_phi[et][tid - 64] = T(2) * c.phi_top - s_phi[et - 1][tid - 64];
+    }
+    __syncthreads();
+
+    const int x = x0 + tx, y = y0 + ty;
+    R v_psi = R(0), v_H = R(0), v_fs = R(0), v_q = R(0), v_liq = R(0), v_liqu = R(0), v_qdot = R(0);
+    unsigned int rowbits = 0u;                // this lane's row flags (one warp = one row)
+    if (x < nx && y < ny) {
+        const int ex = tx + 1, ey = ty + 1;
+        Macro<T> m;                           // this cell's values, from the extended tile
+        m.psi = s_psi[ey][ex];
+        m.fs = s_fs[ey][ex];
+        m.eps = s_eps[ey][ex];
+        m.H = s_H[ey][ex];
+        const long long k = (long long)y * s.pitch + x;
+        // substrate heat flux (R24): -k (4 T_1 - T_2 - 3 T_0) / 2 on row 0
+        if (y == 0 && ny >= 3) {
+            const T kth0 = chi(m.fs, m.psi, c.kth);
+            v_qdot = R(-kth0 * (T(4) * s_Tm[2][ex] - s_Tm[3][ex] - T(3) * s_Tm[1][ex]) / T(2));
+        }
+        // Peclet number (R25): liquid content psi - f_s weights |psi u| / psi
+        {
+            const T w = m.psi - m.fs;
+            if (w > T(0)) {
+                const T ux = T(aux[AUX_PUX * P + k]), uy = T(aux[AUX_PUY * P + k]);
+                const T sp = sqrt(ux * ux + uy * uy);
+                v_liq = R(w);
+                v_liqu = R(w * sp / m.psi);
+            }
+        }
+        T gex, gey, gphx, gphy;
+        grad_s<T, 34>(s_eps, ex, ey, gex, gey);
+        grad_s<T, 34>(s_phi, ex, ey, gphx, gphy);
+        const T lphi = lap_s<T, 34>(s_phi, ex, ey);
+        v_q = R(-(gex * gphx + gey * gphy + m.eps * lphi));
+        v_psi = R(m.psi);
+        v_H = R(m.H);
+        v_fs = R(m.fs);
+        if (!isfinite(v_psi) || !isfinite(v_H)) atomicOr(ws.bad, 1u);
+        const double a = double(s_psi[ey][ex]);
+        // column crossing (height): psi(y) >= 1/2 > psi(y+1)
+        if (a >= 0.5) {
+            rowbits |= 1u;
+            if (y == ny - 1) {
+                atomic_max_pos(&ws.maxv[0], (double)ny);
+            } else {
+                const double b = double(s_psi[ey + 1][ex]);
+                if (b < 0.5) atomic_max_pos(&ws.maxv[0], y + (a - 0.5) / (a - b) + 0.5);
+            }
+            // row crossings (width): left edge needs x >= 1, right edge x <= nx - 2
+            if (x >= 1) {
+                const double bl = double(s_psi[ey][ex - 1]);
+                if (bl < 0.5) {
+                    atomic_min_pos(&ws.minv[1 + y], (x - 1) + (0.5 - bl) / (a - bl));
+                    rowbits |= 2u;
+                }
+            }
+            if (x + 1 < nx) {
+                const double br = double(s_psi[ey][ex + 1]);
+                if (br < 0.5) {
+                    atomic_max_pos(&ws.maxv[2 + y], x + (a - 0.5) / (a - br));
+                    rowbits |= 4u;
+                }
+            }
+        }
+        // freezing front on the centre column (lowest f_s = 1/2 crossing)
+        if (x == nx / 2) {
+            const double fa = double(s_fs[ey][ex]);
+            if (y == 0 && fa >= 0.5) atomicOr(ws.bad + 1, 1u);
+            if (fa >= 0.5) {
+                if (y == ny - 1) {
+                    atomic_min_pos(&ws.minv[0], (double)ny);
+                } else {
+                    const double fb = double(s_fs[ey + 1][ex]);
+                    if (fb < 0.5) atomic_min_pos(&ws.minv[0], y + (fa - 0.5) / (fa - fb) + 0.5);
+                }
+            }
+        }
+    }
+    // row flags: OR across the warp (all lanes share the row), one atomic
+    {
+        unsigned int b = rowbits;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
+        if (tx == 0 && b && y < ny) atomicOr(&ws.rowany[y], b);
+    }
+    // block sums (fixed shuffle order; warps combined in FP64)
+    R v[OBS_NSUM] = {v_psi, v_H, v_fs, v_q, v_liq, v_liqu, v_qdot};
+#pragma unroll
+    for (int j = 0; j < OBS_NSUM; j++) {
+        R t = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (tx == 0) s_red[j][ty] = double(t);
+    }
+    __syncthreads();
+    if (tid < OBS_NSUM) {
+        double t = 0.0;
+        for (int w = 0; w < OBS_BY; w++) t += s_red[tid][w];
+        ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * OBS_NSUM + tid] = t;
+    }
+    // the last block to finish reduces every block's results
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ws.bad + 2, 1u) == (unsigned int)(gridDim.x * gridDim.y) - 1u;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        obs_final(nx, ny, ws, sc);
+    }
+}
+
+// psi = 1/2 extent of row y: 0 without liquid, nx without a left or right
+// crossing (the row is liquid across the periodic seam), else right - left.
+// (Other blocks wrote the workspace with atomics during this launch: read
+// it from L2.)
+static __device__ __forceinline__ double row_extent_of(const ObsScratch &ws, int y, int nx) {
+    const unsigned int bits = __ldcg(ws.rowany + y);
+    if (!(bits & 1u)) return 0.0;
+    if ((bits & 6u) != 6u) return (double)nx;
+    return __longlong_as_double((long long)__ldcg(ws.maxv + 2 + y)) -
+           __longlong_as_double((long long)__ldcg(ws.minv + 1 + y));
+}
+
+// Final reduction, run by the last block of k_obs to finish (256 threads):
+// block partial sums in a fixed order (thread-strided, then a fixed binary
+// tree in shared memory, which needs a fifth of the FP64 adds of a shuffle
+// tree on every lane), so the result does not depend on which block
+// finishes last.
+static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc) {
+    __shared__ double s_acc[OBS_NSUM][256];
+    __shared__ double s_wx[256];
+    __shared__ double s_height, s_rtr, s_front;
+    __shared__ unsigned int s_bad;
+    __shared__ long long s_tfre;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    // the single values, one warp each, while the sums are gathered
+    if (t == 32) s_height = __longlong_as_double((long long)__ldcg(ws.maxv));
+    if (t == 64) s_rtr = 0.5 * row_extent_of(ws, 0, nx);
+    if (t == 96) {
+        const unsigned long long fmin = __ldcg(ws.minv);
+        s_front = __ldcg(ws.bad + 1) ? ((fmin == ~0ull) ? (double)ny : __longlong_as_double((long long)fmin)) : 0.0;
+    }
+    if (t == 128) s_bad = __ldcg(ws.bad);
+    if (t == 160) s_tfre = (long long)__ldcg(&ws.obs->t_fre);
+    double acc[OBS_NSUM];
+#pragma unroll
+    for (int j = 0; j < OBS_NSUM; j++) acc[j] = 0.0;
+    for (int b = t; b < ws.nblocks; b += 256)
+#pragma unroll
+        for (int j = 0; j < OBS_NSUM; j++) acc[j] += __ldcg(ws.partials + (long long)b * OBS_NSUM + j);
+    double wmax = 0.0;
+    for (int y = t; y < ny; y += 256) wmax = fmax(wmax, row_extent_of(ws, y, nx));
+#pragma unroll
+    for (int j = 0; j < OBS_NSUM; j++) s_acc[j][t] = acc[j];
+    s_wx[t] = wmax;
+    __syncthreads();
+#pragma unroll
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) {
+#pragma unroll
+            for (int j = 0; j < OBS_NSUM; j++) s_acc[j][t] += s_acc[j][t + h];
+            s_wx[t] = fmax(s_wx[t], s_wx[t + h]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        // everything from registers and shared memory; the stores below do
+        // not wait for one another
+        const double mass = s_acc[0][0], enth = s_acc[1][0], solid = s_acc[2][0], charge = s_acc[3][0];
+        const double liq = s_acc[4][0], liqu = s_acc[5][0], qdot = s_acc[6][0];
+        const double width = s_wx[0], height = s_height;
+        const double ff = (mass != 0.0) ? solid / mass : 0.0;
+        long long t_fre = s_tfre;
+        if (t_fre < 0 && ff >= 0.99) t_fre = sc.step;
+        lbm_obs *o = ws.obs;
+        o->step = sc.step;
+        o->Fo = sc.alpha_l * (double)sc.step / (sc.R0 * sc.R0);
+        o->mass = mass;
+        o->enthalpy = enth;
+        o->solid = solid;
+        o->charge = charge;
+        o->frozen_fraction = ff;
+        o->height = height;
+        o->width = width;
+        o->aspect = (width > 0.0) ? height / width : 0.0;
+        o->R_tr = s_rtr;
+        o->front = s_front;
+        o->t_fre = t_fre;
+        o->Fo_fre = (t_fre >= 0) ? sc.alpha_l * (double)t_fre / (sc.R0 * sc.R0) : -1.0;
+        o->status = s_bad ? LBM_ERR_DIVERGED : LBM_OK;
+        o->reserved = 0;
+        o->Pe = (liq > 0.0) ? 2.0 * sc.R0 * (liqu / liq) / sc.alpha_l : 0.0;     // R25
+        o->Qdot = qdot;                                                         // R24
+    }
+    // leave the workspace at the identities of its reductions for the next
+    // call (0 for maxima and flags, all ones for minima)
+    __syncthreads();
+    for (int i = t; i < ny + 2; i += 256) ws.maxv[i] = 0ull;
+    for (int i = t; i < ny + 1; i += 256) ws.minv[i] = ~0ull;
+    for (int i = t; i < ny + 3; i += 256) ws.rowany[i] = 0u;     // rowany[ny], then bad[0..2]
+}
+
+// Local substrate heat flux (R24), one thread per column, in the step's
+// arithmetic: -k(x,0) (4 T(x,1) - T(x,2) - 3 T(x,0)) / 2.  Needs ny >= 3.
+template <typename S, typename T, typename A>
+__global__ void k_heat_flux(DevState s, int cur, int lcur, Consts<T> c, Shift sh, double *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= s.nx) return;
+    const long long P = s.plane;
+    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
+    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
+    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
+    Macro<T> m0, m1, m2;
+    cell_macros_t<S, T, A>(pc, lb, aux, P, x, 0, s.ny, c, sh, m0);
+    cell_macros_t<S, T, A>(pc, lb, aux, P, (long long)s.pitch + x, 1, s.ny, c, sh, m1);
+    cell_macros_t<S, T, A>(pc, lb, aux, P, 2LL * s.pitch + x, 2, s.ny, c, sh, m2);
+    const T k0 = chi(m0.fs, m0.psi, c.kth);
+    out[x] = double(-k0 * (T(4) * m1.T_ - m2.T_ - T(3) * m0.T_) / T(2));
+}
+
+// ---------------------------------------------------------------------------
+// Field access for tests and hand-over: stored planes <-> host doubles.
+// ---------------------------------------------------------------------------
+template <typename S, typename T, typename A>
+__global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c, Shift sh, double *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= s.nx || y >= s.ny) return;
+    const long long P = s.plane, k = (long long)y * s.pitch + x;
+    const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
+    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
+    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
+    const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
+    Refs<T> rf;
+    Consts<T> ct;
+    ct.phi_bot = T(c.phi_bot);
+    ct.phi_top = T(c.phi_top);
+    make_refs<S, T>(rf, sh, ct, y, s.ny);
+    if (field == LBM_FIELD_F) {
+        for (int i = 0; i < 9; i++)
+            out[i * N + o] = double(Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale));
+    } else if (field == LBM_FIELD_H) {
+        for (int i = 0; i < 9; i++) out[i * N + o] = double(Pol<S, T>::ld(pc.h + i * P + k, T(0), 1.0f / sh.h_scale));
+    } else if (field == LBM_FIELD_G) {
+        for (int i = 0; i < 9; i++) out[i * N + o] = double(Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale));
+    } else if (field == LBM_FIELD_L) {
+        for (int i = 0; i < 5; i++) out[i * N + o] = double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
+    } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
+        out[o] = double(aux[(field - LBM_FIELD_FS_PREV) * P + k]);
+    } else if (field == LBM_FIELD_SIGMA) {
+        out[o] = double(reinterpret_cast<const A *>(s.sigma)[k]);
+    } else {
+        Macro<double> m;
+        obs_macros<S, T, A>(pc, lb, aux, P, k, y, s.ny, c, sh, m);
+        out[o] = field == LBM_FIELD_PSI ? m.psi
+               : field == LBM_FIELD_FSOLID ? m.fs
+               : field == LBM_FIELD_T ? m.T_
+               : field == LBM_FIELD_PHI ? m.phi
+               : m.H;
+    }
+}
+
+template <typename S, typename T, typename A>
+__global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shift sh, const double *in) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= s.nx || y >= s.ny) return;
+    const long long P = s.plane, k = (long long)y * s.pitch + x;
+    const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
+    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
+    S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
+    A *aux = reinterpret_cast<A *>(cur ? s.aux[1] : s.aux[0]);
+    Refs<T> rf;
+    make_refs<S, T>(rf, sh, c, y, s.ny);
+    if (field == LBM_FIELD_F) {
+        for (int i = 0; i < 9; i++)
+            Pol<typename FStore<S>::type, T>::st(pc.f + i * P + k, T(in[i * N + o]), rf.f[i], sh.f_scale);
+    } else if (field == LBM_FIELD_H) {
+        for (int i = 0; i < 9; i++) Pol<S, T>::st(pc.h + i * P + k, T(in[i * N + o]), T(0), sh.h_scale);
+    } else if (field == LBM_FIELD_G) {
+        for (int i = 0; i < 9; i++) Pol<S, T>::st(pc.g + i * P + k, T(in[i * N + o]), rf.g[i], sh.g_scale);
+    } else if (field == LBM_FIELD_L) {
+        for (int i = 0; i < 5; i++) Pol<S, T>::st(lb + i * P + k, T(in[i * N + o]), rf.l[i], sh.l_scale);
+    } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
+        aux[(field - LBM_FIELD_FS_PREV) * P + k] = A(in[o]);
+    } else if (field == LBM_FIELD_SIGMA) {
+        reinterpret_cast<A *>(s.sigma)[k] = A(in[o]);
+    }
+}
+
+}  // namespace lbm

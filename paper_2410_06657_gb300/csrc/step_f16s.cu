@@ -1,5 +1,5 @@
-// Kernels of the f16s storage precision (populations __half, arithmetic float, auxiliary fields float).
-#include "lbm_kernels.cuh"
+// Kernels of the f16s storage precision (f in float, h, g, l in __half; arithmetic float; auxiliary fields float).
+#include "lbm_launch.cuh"
 
 LBM_DEFINE_LAUNCHERS(f16s, __half, float, float)
 

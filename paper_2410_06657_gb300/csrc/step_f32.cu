@@ -1,5 +1,5 @@
 // Kernels of the f32 storage precision (populations float, arithmetic float, auxiliary fields float).
-#include "lbm_kernels.cuh"
+#include "lbm_launch.cuh"
 
 LBM_DEFINE_LAUNCHERS(f32, float, float, float)
 
