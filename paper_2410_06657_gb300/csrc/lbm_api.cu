@@ -218,6 +218,7 @@ struct lbm_handle {
 struct WorkList {
     BatchItem *items_dev = nullptr;
     void *consts_dev = nullptr;
+    int *tile_item_dev = nullptr;      // member of every step tile
     int n = 0;
     int total_tiles = 0, total_sweep_tiles = 0, grid = 0, sweep_grid = 0;
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -780,13 +781,16 @@ static cudaError_t list_steps(const lbm_batch *b, const WorkList &L, int64_t n, 
         cudaError_t e;
         switch (b->precision) {
         case LBM_FP64:
-            e = launch_batch_step_f64(L.items_dev, L.consts_dev, L.n, L.total_tiles, b->tile_rows, L.grid, fc, fl, st);
+            e = launch_batch_step_f64(L.items_dev, L.consts_dev, L.tile_item_dev, L.total_tiles, b->tile_rows, L.grid,
+                                       fc, fl, st);
             break;
         case LBM_FP32:
-            e = launch_batch_step_f32(L.items_dev, L.consts_dev, L.n, L.total_tiles, b->tile_rows, L.grid, fc, fl, st);
+            e = launch_batch_step_f32(L.items_dev, L.consts_dev, L.tile_item_dev, L.total_tiles, b->tile_rows, L.grid,
+                                       fc, fl, st);
             break;
         default:
-            e = launch_batch_step_f16s(L.items_dev, L.consts_dev, L.n, L.total_tiles, b->tile_rows, L.grid, fc, fl, st);
+            e = launch_batch_step_f16s(L.items_dev, L.consts_dev, L.tile_item_dev, L.total_tiles, b->tile_rows, L.grid,
+                                       fc, fl, st);
             break;
         }
         if (e != cudaSuccess) return e;
@@ -821,8 +825,10 @@ static void free_list(WorkList &L) {
             }
     cudaFree(L.items_dev);
     cudaFree(L.consts_dev);
+    cudaFree(L.tile_item_dev);
     L.items_dev = nullptr;
     L.consts_dev = nullptr;
+    L.tile_item_dev = nullptr;
 }
 
 // Device bytes a member's step touches (both copies of every plane).
@@ -857,13 +863,25 @@ static int build_list(lbm_batch *b, const std::vector<int> &idx, int tile_rows, 
     L.n = (int)idx.size();
     L.total_tiles = tiles;
     L.total_sweep_tiles = sweeps;
-    const int per_sm = tile_rows == 16 ? 2 : (tile_rows == 8 ? 4 : 8);
+    std::vector<int> tile_item(tiles);
+    for (size_t j = 0; j < items.size(); j++)
+        for (int t = 0; t < items[j].tiles_x * items[j].tiles_y; t++) tile_item[items[j].tile_begin + t] = (int)j;
+    // persistent grid = the blocks the device holds at once
+    const int per_sm = b->precision == LBM_FP64 ? batch_blocks_per_sm_f64(tile_rows)
+                     : b->precision == LBM_FP32 ? batch_blocks_per_sm_f32(tile_rows)
+                                                : batch_blocks_per_sm_f16s(tile_rows);
+    if (per_sm < 1) return fail(LBM_ERR_CUDA, "occupancy query of the batched step failed");
     L.grid = std::min(tiles, sms * per_sm);
     L.sweep_grid = std::min(sweeps, sms * 8);
     CK(cudaMalloc(&L.items_dev, items.size() * sizeof(BatchItem)));
     CK(cudaMalloc(&L.consts_dev, cs.size()));
+    CK(cudaMalloc(&L.tile_item_dev, sizeof(int) * (size_t)std::max(tiles, 1)));
     CK(cudaMemcpyAsync(L.items_dev, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, b->st));
     CK(cudaMemcpyAsync(L.consts_dev, cs.data(), cs.size(), cudaMemcpyHostToDevice, b->st));
+    CK(cudaMemcpyAsync(L.tile_item_dev, tile_item.data(), sizeof(int) * tile_item.size(), cudaMemcpyHostToDevice,
+                       b->st));
+    // the host vectors go out of scope on return: finish the copies first
+    CK(cudaStreamSynchronize(b->st));
     return LBM_OK;
 }
 

@@ -128,9 +128,11 @@ struct BatchItem {
     Shift sh;
 };
 #define LBM_DECLARE_BATCH(SUFFIX)                                                                  \
+    int batch_blocks_per_sm_##SUFFIX(int tile_rows);   /* resident blocks of the batched step */   \
     cudaError_t launch_batch_step_##SUFFIX(const BatchItem *items_dev, const void *consts_dev,     \
-                                           int n_items, int total_tiles, int tile_rows, int grid,  \
-                                           int flip_cur, int flip_l, cudaStream_t st);             \
+                                           const int *tile_item_dev, int total_tiles,              \
+                                           int tile_rows, int grid, int flip_cur, int flip_l,      \
+                                           cudaStream_t st);                                       \
     cudaError_t launch_batch_sweep_##SUFFIX(const BatchItem *items_dev, const void *consts_dev,    \
                                             int n_items, int total_tiles, int grid, int flip_l,    \
                                             cudaStream_t st);

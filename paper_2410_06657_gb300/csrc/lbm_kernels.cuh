@@ -1037,21 +1037,25 @@ __device__ __forceinline__ int find_item(const BatchItem *__restrict__ items, in
 template <typename S, typename T, typename A, int BY>
 __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_batch_step(const BatchItem *__restrict__ items,
                                                         const Consts<T> *__restrict__ consts,
-                                                        int n_items, int total_tiles, int flip_cur,
-                                                        int flip_l) {
+                                                        const int *__restrict__ tile_item, int total_tiles,
+                                                        int flip_cur, int flip_l) {
     __shared__ TileSmem<T, BY> sm;
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
-    __shared__ int s_item;
+    __shared__ Consts<T> s_c;          // the member's constants, staged once per tile
+    constexpr int NC = int(sizeof(Consts<T>) / sizeof(T));
+    static_assert(sizeof(Consts<T>) == NC * sizeof(T), "Consts holds only T");
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) s_item = find_item<false>(items, n_items, t);
+        const int item = tile_item[t];
+        if (tid < NC) reinterpret_cast<T *>(&s_c)[tid] = reinterpret_cast<const T *>(consts + item)[tid];
         __syncthreads();
-        const BatchItem &it = items[s_item];
+        const BatchItem &it = items[item];
         const int local = t - it.tile_begin;
         const int bx = local % it.tiles_x, by = local / it.tiles_x;
         const StepIO<S, T, A> io = make_io<S, T, A>(it.s, it.cur ^ flip_cur, it.lcur ^ flip_l, it.write_sigma);
-        sr_advance(it.s, it.cur ^ flip_cur, io, local == 0 && threadIdx.x == 0 && threadIdx.y == 0);
-        step_tile<S, T, A, BY>(io, consts[s_item], it.sh, sm, stash, bx * 32, by * BY);
+        sr_advance(it.s, it.cur ^ flip_cur, io, local == 0 && tid == 0);
+        step_tile<S, T, A, BY>(io, s_c, it.sh, sm, stash, bx * 32, by * BY);
         __syncthreads();
     }
 }

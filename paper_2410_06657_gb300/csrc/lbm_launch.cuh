@@ -5,6 +5,81 @@
 #include "lbm_kernels.cuh"
 #include "lbm_observe.cuh"
 
+namespace lbm {
+
+// Resident blocks per SM of the batched step: the persistent grid is exactly
+// the device's resident capacity, so every block starts at once and the
+// round-robin tile share is even.
+template <typename S, typename T, typename A, int BY>
+int batch_blocks_per_sm_by() {
+    int n = 0;
+    static bool ready = false;
+    if (allow_dynamic_smem(k_batch_step<S, T, A, BY>, stash_bytes<T, BY>(), ready) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<S, T, A, BY>, 32 * BY,
+                                                      stash_bytes<T, BY>()) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <typename S, typename T, typename A>
+int batch_blocks_per_sm_t(int tile_rows) {
+    switch (tile_rows) {
+    case 4: return batch_blocks_per_sm_by<S, T, A, 4>();
+    case 8: return batch_blocks_per_sm_by<S, T, A, 8>();
+    case 16: return batch_blocks_per_sm_by<S, T, A, 16>();
+    default: return 0;
+    }
+}
+
+template <typename S, typename T, typename A, int BY>
+cudaError_t launch_batch_step_by(const BatchItem *items, const Consts<T> *c, const int *tile_item, int total_tiles,
+                                 int grid, int flip_cur, int flip_l, cudaStream_t st) {
+    static bool ready = false;
+    cudaError_t e = allow_dynamic_smem(k_batch_step<S, T, A, BY>, stash_bytes<T, BY>(), ready);
+    if (e != cudaSuccess) return e;
+    k_batch_step<S, T, A, BY><<<grid, dim3(32, BY), stash_bytes<T, BY>(), st>>>(items, c, tile_item, total_tiles,
+                                                                                flip_cur, flip_l);
+    return cudaGetLastError();
+}
+
+template <typename S, typename T, typename A>
+cudaError_t launch_batch_step_t(const BatchItem *items, const void *consts, const int *tile_item, int total_tiles,
+                                int tile_rows, int grid, int flip_cur, int flip_l, cudaStream_t st) {
+    const Consts<T> *c = reinterpret_cast<const Consts<T> *>(consts);
+    switch (tile_rows) {
+    case 4: return launch_batch_step_by<S, T, A, 4>(items, c, tile_item, total_tiles, grid, flip_cur, flip_l, st);
+    case 8: return launch_batch_step_by<S, T, A, 8>(items, c, tile_item, total_tiles, grid, flip_cur, flip_l, st);
+    case 16: return launch_batch_step_by<S, T, A, 16>(items, c, tile_item, total_tiles, grid, flip_cur, flip_l, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename S, typename T, typename A>
+cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int n_items, int total_tiles, int grid,
+                                 int flip_l, cudaStream_t st) {
+    const Consts<T> *c = reinterpret_cast<const Consts<T> *>(consts);
+    k_batch_sweep<S, T, A><<<grid, dim3(32, 8), 0, st>>>(items, c, n_items, total_tiles, flip_l);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+// Batched-step entry points of one precision.
+#define LBM_DEFINE_BATCH(SUFFIX, S, T, A)                                                                   \
+    namespace lbm {                                                                                         \
+    int batch_blocks_per_sm_##SUFFIX(int tile_rows) { return batch_blocks_per_sm_t<S, T, A>(tile_rows); }   \
+    cudaError_t launch_batch_step_##SUFFIX(const BatchItem *items_dev, const void *consts_dev,             \
+                                           const int *tile_item_dev, int total_tiles, int tile_rows,       \
+                                           int grid, int flip_cur, int flip_l, cudaStream_t st) {          \
+        return launch_batch_step_t<S, T, A>(items_dev, consts_dev, tile_item_dev, total_tiles, tile_rows,  \
+                                            grid, flip_cur, flip_l, st);                                   \
+    }                                                                                                       \
+    cudaError_t launch_batch_sweep_##SUFFIX(const BatchItem *items_dev, const void *consts_dev, int n_items,\
+                                            int total_tiles, int grid, int flip_l, cudaStream_t st) {       \
+        return launch_batch_sweep_t<S, T, A>(items_dev, consts_dev, n_items, total_tiles, grid, flip_l, st);\
+    }                                                                                                       \
+    }
+
 // ---------------------------------------------------------------------------
 // Launchers for one (S, T, A) triple; SUFFIX names the precision.
 // ---------------------------------------------------------------------------

@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
     }
     __syncthreads();
     if (tid < OBS_NSUM) {
-        double t = 0.0;
-        for (int w = 0; w < OBS_BY; w++) t += s_red[tid][w];
+        double t = s_red[tid][0];
+        for (int w = 1; w < OBS_BY; w++) t += s_red[tid][w];
         ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * OBS_NSUM + tid] = t;
     }
     // the last block to finish reduces every block's results
@@ -297,10 +297,12 @@ static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratc
     }
     if (t == 128) s_bad = __ldcg(ws.bad);
     if (t == 160) s_tfre = (long long)__ldcg(&ws.obs->t_fre);
+    // FP64 adds are scarce on this part: start from the first partial
+    // instead of adding it to zero
     double acc[OBS_NSUM];
 #pragma unroll
-    for (int j = 0; j < OBS_NSUM; j++) acc[j] = 0.0;
-    for (int b = t; b < ws.nblocks; b += 256)
+    for (int j = 0; j < OBS_NSUM; j++) acc[j] = t < ws.nblocks ? __ldcg(ws.partials + (long long)t * OBS_NSUM + j) : 0.0;
+    for (int b = t + 256; b < ws.nblocks; b += 256)
 #pragma unroll
         for (int j = 0; j < OBS_NSUM; j++) acc[j] += __ldcg(ws.partials + (long long)b * OBS_NSUM + j);
     double wmax = 0.0;
