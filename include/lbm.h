@@ -276,7 +276,7 @@ int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
  * synchronise the device.  It runs the same reduction as lbm_observables
  * with its scratch (block partial sums, crossing candidates) in a
  * fixed-size array that the library keeps in device memory on every GPU
- * that loads it (about 1.2 MB, held until the process exits).
+ * that loads it (about 1.3 MB, held until the process exits).
  *   p     parameters of the state (host struct, read during the call)
  *   pop   device array of 32 planes, f 0-8 then h 0-8, g 0-8, l 0-4, each
  *         ny rows of `pitch` elements, x fastest: all in double for

@@ -443,11 +443,12 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->s.plane = plane;
     // observables workspace
     const int nb = obs_grid_blocks(nx, ny);
-    const size_t part_b = round_up((size_t)nb * OBS_NSUM * sizeof(double), 256);
+    const int ng = (nb + OBS_GROUP - 1) / OBS_GROUP;
+    const size_t part_b = round_up((size_t)(nb + ng) * OBS_NSUM * sizeof(double), 256);
     const size_t qdot_b = round_up((size_t)nx * sizeof(double), 256);
     h->ws_max_bytes = round_up((size_t)(2 + ny) * 8, 256);
     h->ws_min_bytes = round_up((size_t)(1 + ny) * 8, 256);
-    h->ws_u32_bytes = round_up((size_t)(ny + 3) * 4, 256);
+    h->ws_u32_bytes = round_up((size_t)(ny + 3 + ng) * 4, 256);
     const size_t obs_b = round_up(sizeof(lbm_obs), 256);
     const size_t err_b = 256;
     if (cudaMalloc(&h->ws_mem, part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b + err_b +
@@ -466,6 +467,9 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->ws.minv = h->ws_min_base;
     h->ws.rowany = h->ws_u32_base;
     h->ws.bad = h->ws_u32_base + ny;
+    h->ws.gcount = h->ws_u32_base + ny + 3;
+    h->ws.gpartials = h->ws.partials + (size_t)nb * OBS_NSUM;
+    h->ws.ngroups = ng;
     h->ws.obs = reinterpret_cast<lbm_obs *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes);
     h->err = reinterpret_cast<unsigned int *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b);
     h->s.err = h->err;

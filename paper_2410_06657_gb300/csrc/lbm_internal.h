@@ -64,15 +64,18 @@ struct TmaMaps {
 
 // Workspace of the observables reduction.
 constexpr int OBS_NSUM = 7;          // block sums: psi, H, f_s, q_v, liquid, liquid speed, Qdot
+constexpr int OBS_GROUP = 32;        // blocks per first-level group of the final reduction
 struct ObsScratch {
     double *partials;               // [nblocks][OBS_NSUM]
+    double *gpartials;              // [ngroups][OBS_NSUM]: sums of each group of OBS_GROUP blocks
+    unsigned int *gcount;           // [ngroups]: blocks of each group finished
     unsigned long long *maxv;       // [2 + ny]: height, (unused), rightmost crossing of row y
     unsigned long long *minv;       // [1 + ny]: front crossing, leftmost crossing of row y
     unsigned int *rowany;           // [ny]: bit0 liquid, bit1 left crossing, bit2 right crossing
     unsigned int *bad;              // [3]: non-finite seen, centre-column bottom cell frozen,
                                     //      blocks finished (the last one reduces)
     lbm_obs *obs;                   // device-side result (keeps t_fre)
-    int nblocks;
+    int nblocks, ngroups;
 };
 
 struct Scalars {           // per-call scalars of the observables reduction

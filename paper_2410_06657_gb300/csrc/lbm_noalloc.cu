@@ -21,11 +21,12 @@ constexpr int kMaxBlocks = 20480;   // 32 x 8 tiles of the reduction grid
 constexpr int kMaxNy = 4096;        // rows (one crossing slot per row)
 
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
-constexpr size_t kPartBytes = al256(size_t(kMaxBlocks) * lbm::OBS_NSUM * sizeof(double));
+constexpr int kMaxGroups = (kMaxBlocks + lbm::OBS_GROUP - 1) / lbm::OBS_GROUP;
+constexpr size_t kPartBytes = al256(size_t(kMaxBlocks + kMaxGroups) * lbm::OBS_NSUM * sizeof(double));
 constexpr size_t kMaxvBytes = al256(size_t(2 + kMaxNy) * sizeof(unsigned long long));
 constexpr size_t kMinvBytes = al256(size_t(1 + kMaxNy) * sizeof(unsigned long long));
-constexpr size_t kU32Bytes = al256(size_t(kMaxNy + 3) * sizeof(unsigned int));
-constexpr size_t kScratchBytes = kPartBytes + kMaxvBytes + kMinvBytes + kU32Bytes;   // about 1.2 MB
+constexpr size_t kU32Bytes = al256(size_t(kMaxNy + 3 + kMaxGroups) * sizeof(unsigned int));
+constexpr size_t kScratchBytes = kPartBytes + kMaxvBytes + kMinvBytes + kU32Bytes;   // about 1.3 MB
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
@@ -105,6 +106,9 @@ extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, con
     ws.minv = reinterpret_cast<unsigned long long *>(b + kPartBytes + kMaxvBytes);
     ws.rowany = reinterpret_cast<unsigned int *>(b + kPartBytes + kMaxvBytes + kMinvBytes);
     ws.bad = ws.rowany + p->ny;
+    ws.gcount = ws.rowany + p->ny + 3;
+    ws.ngroups = (nblocks + OBS_GROUP - 1) / OBS_GROUP;
+    ws.gpartials = ws.partials + (size_t)nblocks * OBS_NSUM;
     ws.obs = out;
     ws.nblocks = nblocks;
 
@@ -130,7 +134,7 @@ extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, con
     // minima)
     cudaError_t e = cudaMemsetAsync(ws.maxv, 0x00, (size_t)(2 + p->ny) * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.minv, 0xFF, (size_t)(1 + p->ny) * sizeof(unsigned long long), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws.rowany, 0x00, (size_t)(p->ny + 3) * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.rowany, 0x00, (size_t)(p->ny + 3 + ws.ngroups) * sizeof(unsigned int), st);
     if (e == cudaSuccess) {
         switch (p->precision) {
         case LBM_FP64: e = launch_obs_f64(s, 0, 0, &cd, sh, ws, sc, st); break;

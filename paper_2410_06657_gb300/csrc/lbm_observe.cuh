@@ -90,6 +90,35 @@ __device__ __forceinline__ void cell_macros_t(const Planes<S> &pc, const S *lb, 
 
 static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc);
 
+// Sum of n values of quantity j at src[i * OBS_NSUM + j] (i < n), by one warp
+// (warp j of the block) in a fixed order: lane l adds i = l, l + 32, ...,
+// then a binary tree in shared memory.  Returns the sum in lane 0.
+static __device__ __forceinline__ double warp_sum_fixed(const double *src, int n, int j, double *scratch32) {
+    const int lane = threadIdx.x & 31;
+    double v = lane < n ? __ldcg(src + (long long)lane * OBS_NSUM + j) : 0.0;
+    for (int i = lane + 32; i < n; i += 32) v += __ldcg(src + (long long)i * OBS_NSUM + j);
+    scratch32[lane] = v;
+    __syncwarp();
+#pragma unroll
+    for (int h = 16; h > 0; h >>= 1) {
+        if (lane < h) scratch32[lane] += scratch32[lane + h];
+        __syncwarp();
+    }
+    return scratch32[0];
+}
+
+// First level: the last block of group g sums the group's block partials
+// (warp j sums quantity j) and restores the group's counter.
+static __device__ __forceinline__ void obs_group(const ObsScratch &ws, int g, int gsize) {
+    __shared__ double s_g[OBS_NSUM][32];
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp < OBS_NSUM) {
+        const double v = warp_sum_fixed(ws.partials + (long long)g * OBS_GROUP * OBS_NSUM, gsize, warp, s_g[warp]);
+        if (lane == 0) ws.gpartials[(long long)g * OBS_NSUM + warp] = v;
+    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) ws.gcount[g] = 0u;
+}
+
 template <typename S, typename T, typename A>
 __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<T> c, Shift sh,
                                                     ObsScratch ws, Scalars sc) {
@@ -252,11 +281,23 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         for (int w = 1; w < OBS_BY; w++) t += s_red[tid][w];
         ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * OBS_NSUM + tid] = t;
     }
-    // the last block to finish reduces every block's results
-    __shared__ bool s_last;
+    // Two-level finish.  FP64 adds run at a small fraction of the FP32 rate
+    // on this part, so they are spread over many SMs: the last block of each
+    // group of OBS_GROUP blocks sums its group, the last group to finish
+    // sums the groups.  Every sum runs in a fixed order.
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
+    const int grp = blk / OBS_GROUP, gsize = min(OBS_GROUP, nblk - grp * OBS_GROUP);
+    __shared__ bool s_glast, s_last;
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(ws.bad + 2, 1u) == (unsigned int)(gridDim.x * gridDim.y) - 1u;
+    if (tid == 0) s_glast = atomicAdd(ws.gcount + grp, 1u) == (unsigned int)gsize - 1u;
+    __syncthreads();
+    if (!s_glast) return;
+    __threadfence();
+    obs_group(ws, grp, gsize);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ws.bad + 2, 1u) == (unsigned int)ws.ngroups - 1u;
     __syncthreads();
     if (s_last) {
         __threadfence();
@@ -276,14 +317,10 @@ static __device__ __forceinline__ double row_extent_of(const ObsScratch &ws, int
            __longlong_as_double((long long)__ldcg(ws.minv + 1 + y));
 }
 
-// Final reduction, run by the last block of k_obs to finish (256 threads):
-// block partial sums in a fixed order (thread-strided, then a fixed binary
-// tree in shared memory, which needs a fifth of the FP64 adds of a shuffle
-// tree on every lane), so the result does not depend on which block
-// finishes last.
+// Final reduction, run by the last group to finish (256 threads): the group
+// sums in a fixed order, the widest row, the single values and the result,
+// so nothing depends on which block finishes last.
 static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc) {
-    __shared__ double s_acc[OBS_NSUM][256];
-    __shared__ double s_wx[256];
     __shared__ double s_height, s_rtr, s_front;
     __shared__ unsigned int s_bad;
     __shared__ long long s_tfre;
@@ -297,35 +334,35 @@ static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratc
     }
     if (t == 128) s_bad = __ldcg(ws.bad);
     if (t == 160) s_tfre = (long long)__ldcg(&ws.obs->t_fre);
-    // FP64 adds are scarce on this part: start from the first partial
-    // instead of adding it to zero
-    double acc[OBS_NSUM];
-#pragma unroll
-    for (int j = 0; j < OBS_NSUM; j++) acc[j] = t < ws.nblocks ? __ldcg(ws.partials + (long long)t * OBS_NSUM + j) : 0.0;
-    for (int b = t + 256; b < ws.nblocks; b += 256)
-#pragma unroll
-        for (int j = 0; j < OBS_NSUM; j++) acc[j] += __ldcg(ws.partials + (long long)b * OBS_NSUM + j);
-    double wmax = 0.0;
-    for (int y = t; y < ny; y += 256) wmax = fmax(wmax, row_extent_of(ws, y, nx));
-#pragma unroll
-    for (int j = 0; j < OBS_NSUM; j++) s_acc[j][t] = acc[j];
-    s_wx[t] = wmax;
-    __syncthreads();
-#pragma unroll
-    for (int h = 128; h > 0; h >>= 1) {
-        if (t < h) {
-#pragma unroll
-            for (int j = 0; j < OBS_NSUM; j++) s_acc[j][t] += s_acc[j][t + h];
-            s_wx[t] = fmax(s_wx[t], s_wx[t + h]);
-        }
-        __syncthreads();
+    // the group sums (warp j sums quantity j over the groups)
+    __shared__ double s_fin[OBS_NSUM][32];
+    {
+        const int warp = t >> 5;
+        if (warp < OBS_NSUM) warp_sum_fixed(ws.gpartials, ws.ngroups, warp, s_fin[warp]);
     }
+    // widest row: extents are non-negative doubles, so their bit patterns
+    // order like the values and the maximum is an integer one
+    __shared__ unsigned long long s_wb[8];
+    unsigned long long wb = 0ull;
+    for (int y = t; y < ny; y += 256) {
+        const unsigned long long e = (unsigned long long)__double_as_longlong(row_extent_of(ws, y, nx));
+        wb = e > wb ? e : wb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_down_sync(0xffffffffu, wb, o);
+        wb = other > wb ? other : wb;
+    }
+    if ((t & 31) == 0) s_wb[t >> 5] = wb;
+    __syncthreads();
     if (t == 0) {
         // everything from registers and shared memory; the stores below do
         // not wait for one another
-        const double mass = s_acc[0][0], enth = s_acc[1][0], solid = s_acc[2][0], charge = s_acc[3][0];
-        const double liq = s_acc[4][0], liqu = s_acc[5][0], qdot = s_acc[6][0];
-        const double width = s_wx[0], height = s_height;
+        const double mass = s_fin[0][0], enth = s_fin[1][0], solid = s_fin[2][0], charge = s_fin[3][0];
+        const double liq = s_fin[4][0], liqu = s_fin[5][0], qdot = s_fin[6][0];
+        unsigned long long wmax = s_wb[0];
+        for (int w = 1; w < 8; w++) wmax = s_wb[w] > wmax ? s_wb[w] : wmax;
+        const double width = __longlong_as_double((long long)wmax), height = s_height;
         const double ff = (mass != 0.0) ? solid / mass : 0.0;
         long long t_fre = s_tfre;
         if (t_fre < 0 && ff >= 0.99) t_fre = sc.step;
