@@ -249,6 +249,33 @@ __device__ __forceinline__ void grad_s(const T (*z)[W], int ex, int ey, T &gx, T
     gx = sx / cs2<T>();
     gy = sy / cs2<T>();
 }
+// The same stencils on the nine values v[i] = z(x + c_i) already loaded.
+template <typename T>
+__device__ __forceinline__ void grad_v(const T v[9], T &gx, T &gy) {
+    const T wa = T(1.0 / 9.0), wd = T(1.0 / 36.0);
+    T sx = wa * v[1];
+    sx = sx - wa * v[3];
+    sx = sx + wd * v[5];
+    sx = sx - wd * v[6];
+    sx = sx - wd * v[7];
+    sx = sx + wd * v[8];
+    T sy = wa * v[2];
+    sy = sy - wa * v[4];
+    sy = sy + wd * v[5];
+    sy = sy + wd * v[6];
+    sy = sy - wd * v[7];
+    sy = sy - wd * v[8];
+    gx = sx / cs2<T>();
+    gy = sy / cs2<T>();
+}
+template <typename T>
+__device__ __forceinline__ T lap_v(const T v[9]) {
+    T acc = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; i++) acc += T(2) * w9<T>(i) * (v[i] - v[0]);
+    return acc / cs2<T>();
+}
+
 template <typename T, int W>
 __device__ __forceinline__ T lap_s(const T (*z)[W], int ex, int ey) {
     const T z0 = z[ey][ex];
@@ -291,12 +318,12 @@ __device__ __forceinline__ void ring_slot(int r, int &ex, int &ey) {
 // ---------------------------------------------------------------------------
 template <typename T, int BY>
 struct TileSmem {
-    T psi[BY + 2][34];
-    T rho[BY + 2][34];
-    T eps[BY + 2][34];
-    T phi[BY + 2][34];
-    T p[BY + 2][34];
-    T S[BY + 2][34];
+    // per extended-tile cell, packed so a stencil reads each neighbour with
+    // one vector load: (psi, rho, eps, phi) and (p, S)
+    struct alignas(4 * sizeof(T)) Quad { T psi, rho, eps, phi; };
+    struct alignas(2 * sizeof(T)) Pair { T p, S; };
+    Quad q[BY + 2][34];
+    Pair ps[BY + 2][34];
 };
 
 template <typename S, typename T, typename A>
@@ -366,12 +393,8 @@ __device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Co
     Macro<T> m;
     local_macros(f, g, l1234, T(io.aux_in[AUX_FS * P + k]), T(io.aux_in[AUX_MDOT * P + k]),
                  T(io.aux_in[AUX_Q * P + k]), c, m);
-    sm.psi[ey][ex] = m.psi;
-    sm.rho[ey][ex] = m.rho;
-    sm.eps[ey][ex] = m.eps;
-    sm.phi[ey][ex] = m.phi;
-    sm.p[ey][ex] = T(io.aux_in[AUX_P * P + k]);
-    sm.S[ey][ex] = T(io.aux_in[AUX_S * P + k]);
+    sm.q[ey][ex] = {m.psi, m.rho, m.eps, m.phi};
+    sm.ps[ey][ex] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
 }
 
 // Population sources for step_cell.
@@ -403,23 +426,17 @@ struct RegPops {
 template <typename T, int BY>
 __device__ __forceinline__ void fill_ghosts(TileSmem<T, BY> &sm, const Consts<T> &c, int y0, int ny, int tid) {
     if (y0 == 0 && tid < 34) {              // bottom wall: wetting, copy, mirror
-        const T z = sm.psi[1][tid];
-        sm.psi[0][tid] = z + c.wet * z * (T(1) - z);
-        sm.rho[0][tid] = sm.rho[1][tid];
-        sm.eps[0][tid] = sm.eps[1][tid];
-        sm.phi[0][tid] = T(2) * c.phi_bot - sm.phi[1][tid];
-        sm.p[0][tid] = sm.p[1][tid];
-        sm.S[0][tid] = sm.S[1][tid];
+        const typename TileSmem<T, BY>::Quad a = sm.q[1][tid];
+        const T z = a.psi;
+        sm.q[0][tid] = {z + c.wet * z * (T(1) - z), a.rho, a.eps, T(2) * c.phi_bot - a.phi};
+        sm.ps[0][tid] = sm.ps[1][tid];
     }
     const int et = ny - y0 + 1;              // ext row of y = ny, if inside the tile
     if (et >= 1 && et <= BY + 1 && tid >= 64 && tid < 98) {
         const int e = tid - 64;              // top wall: neutral wetting, copy, mirror
-        sm.psi[et][e] = sm.psi[et - 1][e];
-        sm.rho[et][e] = sm.rho[et - 1][e];
-        sm.eps[et][e] = sm.eps[et - 1][e];
-        sm.phi[et][e] = T(2) * c.phi_top - sm.phi[et - 1][e];
-        sm.p[et][e] = sm.p[et - 1][e];
-        sm.S[et][e] = sm.S[et - 1][e];
+        const typename TileSmem<T, BY>::Quad a = sm.q[et - 1][e];
+        sm.q[et][e] = {a.psi, a.rho, a.eps, T(2) * c.phi_top - a.phi};
+        sm.ps[et][e] = sm.ps[et - 1][e];
     }
 }
 
@@ -438,15 +455,25 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     Refs<T> ro;                               // destination references (half storage)
     const int ex = tx + 1, ey = ty + 1;
     // ---- a2: stencils ----------------------------------------------------
-    T gpsix, gpsiy, grhox, grhoy, gepsx, gepsy, gphix, gphiy, gpx, gpy, gSx, gSy;
-    grad_s<T, 34>(sm.psi, ex, ey, gpsix, gpsiy);
-    const T lpsi = lap_s<T, 34>(sm.psi, ex, ey);
-    grad_s<T, 34>(sm.rho, ex, ey, grhox, grhoy);
-    grad_s<T, 34>(sm.eps, ex, ey, gepsx, gepsy);
-    grad_s<T, 34>(sm.phi, ex, ey, gphix, gphiy);
-    const T lphi = lap_s<T, 34>(sm.phi, ex, ey);
-    grad_s<T, 34>(sm.p, ex, ey, gpx, gpy);
-    grad_s<T, 34>(sm.S, ex, ey, gSx, gSy);
+    T gpsix, gpsiy, grhox, grhoy, gepsx, gepsy, gphix, gphiy, gpx, gpy, gSx, gSy, lpsi, lphi;
+    {
+        T vpsi[9], vrho[9], veps[9], vphi[9], vp[9], vS[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const typename TileSmem<T, BY>::Quad a = sm.q[ey + CY[i]][ex + CX[i]];
+            const typename TileSmem<T, BY>::Pair b = sm.ps[ey + CY[i]][ex + CX[i]];
+            vpsi[i] = a.psi; vrho[i] = a.rho; veps[i] = a.eps; vphi[i] = a.phi;
+            vp[i] = b.p; vS[i] = b.S;
+        }
+        grad_v<T>(vpsi, gpsix, gpsiy);
+        lpsi = lap_v<T>(vpsi);
+        grad_v<T>(vrho, grhox, grhoy);
+        grad_v<T>(veps, gepsx, gepsy);
+        grad_v<T>(vphi, gphix, gphiy);
+        lphi = lap_v<T>(vphi);
+        grad_v<T>(vp, gpx, gpy);
+        grad_v<T>(vS, gSx, gSy);
+    }
 
     // ---- a3: forces (Eq. Fs with the chemical potential of Sec. 2; Eq. Fe)
     const T ps = m.psi;
@@ -728,12 +755,8 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         }
 #pragma unroll
         for (int i = 0; i < 5; i++) stash[27 + i][ty][tx] = l[i];
-        sm.psi[ty + 1][tx + 1] = m.psi;
-        sm.rho[ty + 1][tx + 1] = m.rho;
-        sm.eps[ty + 1][tx + 1] = m.eps;
-        sm.phi[ty + 1][tx + 1] = m.phi;
-        sm.p[ty + 1][tx + 1] = T(io.aux_in[AUX_P * P + k]);
-        sm.S[ty + 1][tx + 1] = T(io.aux_in[AUX_S * P + k]);
+        sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
+        sm.ps[ty + 1][tx + 1] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
     }
 
     // ---- phase 1: halo ring, recomputed from the neighbours' populations
@@ -960,12 +983,8 @@ __device__ __forceinline__ void step_tile_tma(const StepIO<S, T, A> &io, const C
         for (int i = 1; i < 5; i++) l1234 += bp.l(i);
         fs_p = T(bA[AUX_FS * G::PLA + oa]);
         local_macros(f, g, l1234, fs_p, T(bA[AUX_MDOT * G::PLA + oa]), T(bA[AUX_Q * G::PLA + oa]), c, mm);
-        sm.psi[ey][ex] = mm.psi;
-        sm.rho[ey][ex] = mm.rho;
-        sm.eps[ey][ex] = mm.eps;
-        sm.phi[ey][ex] = mm.phi;
-        sm.p[ey][ex] = T(bA[AUX_P * G::PLA + oa]);
-        sm.S[ey][ex] = T(bA[AUX_S * G::PLA + oa]);
+        sm.q[ey][ex] = {mm.psi, mm.rho, mm.eps, mm.phi};
+        sm.ps[ey][ex] = {T(bA[AUX_P * G::PLA + oa]), T(bA[AUX_S * G::PLA + oa])};
     };
 
     // ---- phase 1: own cell, then the halo ring --------------------------
