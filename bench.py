@@ -483,6 +483,77 @@ def run_serving(args, world, rank, local):
         }))
 
 
+# ---------------------------------------------------------------------------
+# Regimes: the production droplet run to freezing with the field off, prolate
+# (PR+) and oblate (OB-); optionally the oracle on the 4x-coarsened lattice
+# (128 x 64, R = 20, same tau: 16x fewer steps for the same Fourier number)
+# ---------------------------------------------------------------------------
+
+def _freeze(sim, every, max_steps):
+    """Step until t_fre; return (t_fre, Fo_fre, aspect and height at t_fre, steps)."""
+    while sim.t < max_steps:
+        sim.step(every)
+        o = sim.observables()
+        if o["status"] != 0:
+            break
+        if o["t_fre"] >= 0:
+            return o
+    return sim.observables()
+
+
+def run_regimes(args, world, rank, local):
+    import torch
+    from paper_2410_06657_gb300 import lbm, workloads as W
+
+    torch.cuda.set_device(local)
+    lbm.load()
+    stream = torch.cuda.current_stream()
+    prec = W.PRECISIONS[args.precision]
+    cases = [("field off", None, 0.0), ("PR+", "PR+", 0.2), ("OB-", "OB-", 0.2)]
+    out, lu, t_gpu = [], 0, 0.0
+    for name, regime, ca in cases:
+        w = W.production(precision=prec, regime=regime, CaE=ca)
+        p = w["params"]
+        sim = lbm.Simulation(p, stream)
+        xc, yc = W.sessile_center(p["nx"], w["R"], p["theta_deg"])
+        sim.init_droplet(w["R"], xc, yc, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = _freeze(sim, 200, 400000)
+        torch.cuda.synchronize()
+        t_gpu += time.perf_counter() - t0
+        lu += p["nx"] * p["ny"] * sim.t
+        rec = {"case": name, "t_fre": o["t_fre"], "Fo_fre": o["Fo_fre"], "aspect": o["aspect"],
+               "height": o["height"], "frozen_fraction": o["frozen_fraction"]}
+        if args.with_oracle and rank == 0:
+            import oracle
+            pc = dict(p, nx=128, ny=64, R0=w["R"] / 4, precision=W.FP64)
+            orc = oracle.Oracle(pc)
+            xcc, ycc = W.sessile_center(128, w["R"] / 4, p["theta_deg"])
+            orc.init_droplet(w["R"] / 4, xcc, ycc, 0)
+            oo = orc.observables()
+            while orc.t < 400000 // 16 and oo["t_fre"] < 0:
+                orc.step(50)
+                oo = orc.observables()
+            rec["oracle_128x64"] = {"t_fre": oo["t_fre"], "Fo_fre": oo["Fo_fre"], "aspect": oo["aspect"],
+                                    "height_x4": 4 * oo["height"]}
+            if oo["Fo_fre"] > 0 and o["Fo_fre"] > 0:
+                rec["Fo_fre_rel_diff"] = o["Fo_fre"] / oo["Fo_fre"] - 1
+                rec["aspect_rel_diff"] = o["aspect"] / oo["aspect"] - 1
+        out.append(rec)
+        sim.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "MLUPS", "value": world * lu / t_gpu / 1e6, "unit": "MLUPS", "n_gpus": world,
+            "steps": int(lu), "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "production droplet 512x256 run to frozen fraction 0.99: field off, "
+                                   "PR+ (R_sigma=2, S=0.5), OB- (R_sigma=2, S=5), CaE=0.2",
+                       "observables_every": 200},
+            "cases": out,
+        }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -491,13 +562,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16s"])
     ap.add_argument("--workload", default="production",
-                    choices=["production", "precision", "batched", "serving"])
+                    choices=["production", "precision", "batched", "serving", "regimes"])
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--max-ny", type=int, default=128)
     ap.add_argument("--budget-gb", type=float, default=80.0)
     ap.add_argument("--obs-every", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--with-oracle", action="store_true",
+                    help="regimes: also run the oracle on the 4x-coarsened lattice")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -510,6 +583,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, world, rank, local)
+        return
+    if args.workload == "regimes":
+        run_regimes(args, world, rank, local)
         return
     run_gpu(args, world, rank, local)
 

@@ -397,6 +397,46 @@ __device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Co
     sm.ps[ey][ex] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
 }
 
+// The stored values one cell's macros need, in the arithmetic type T.
+template <typename T>
+struct CellLoad {
+    T f[9], g[9], l1234, fs_prev, mdot_prev, Q_prev;
+};
+
+// A ring cell's stored values and its (p, S), loaded into registers.
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void load_ring_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
+                                               uint32_t P, uint32_t k, int y, CellLoad<T> &o, T &pv, T &Sv) {
+    Refs<T> rf;
+    make_refs<S, T>(rf, sh, c, y, io.ny);
+    const float fi = 1.0f / sh.f_scale, gi = 1.0f / sh.g_scale, li = 1.0f / sh.l_scale;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        o.f[i] = Pol<typename FStore<S>::type, T>::ld(io.f_in + (i * P + k), rf.f[i], fi);
+        o.g[i] = Pol<S, T>::ld(io.g_in + (i * P + k), rf.g[i], gi);
+    }
+    o.l1234 = T(0);
+#pragma unroll
+    for (int i = 1; i < 5; i++) o.l1234 += Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], li);
+    o.fs_prev = T(io.aux_in[AUX_FS * P + k]);
+    o.mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
+    o.Q_prev = T(io.aux_in[AUX_Q * P + k]);
+    pv = T(io.aux_in[AUX_P * P + k]);
+    Sv = T(io.aux_in[AUX_S * P + k]);
+}
+
+// Asynchronous global -> shared copy of one 4- or 8-byte element.
+template <typename V>
+__device__ __forceinline__ void cp_async_elem(V *dst_smem, const V *src) {
+    static_assert(sizeof(V) == 4 || sizeof(V) == 8, "cp.async element size");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    if constexpr (sizeof(V) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Population sources for step_cell.
 template <typename T, int BY>
 struct StashPops {            // own cell's populations stashed in shared memory
@@ -706,7 +746,10 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
 }
 
 
-template <typename S, typename T, typename A, int BY>
+// ASYNC: the own cell's populations reach the stash by cp.async while the
+// ring cell's loads are in flight (single-instance kernels; the batched
+// kernel's extra live state would spill with it).
+template <typename S, typename T, typename A, int BY, bool ASYNC = false>
 __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Consts<T> &c,
                                           const Shift &sh, TileSmem<T, BY> &sm, T (*stash)[BY][32], int x0,
                                           int y0) {
@@ -715,63 +758,126 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     const int nx = io.nx, ny = io.ny;
     const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
 
-    // ---- phase 1: own cell (kept in registers) -------------------------
     const int xg = x0 + tx, y = y0 + ty;
     const bool own = (xg < nx) && (y < ny);
     const int x = xg < nx ? xg : xg % nx;       // wrapped slot of a ragged tile
     const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
-    Refs<T> rf;
-    T f[9], g[9], l[5], h[9];
     Macro<T> m;
     T fs_prev = T(0), mdot_prev = T(0), Q_prev = T(0), pux_prev = T(0), puy_prev = T(0);
-    const float fsc = 1.0f / sh.f_scale, gsc = 1.0f / sh.g_scale, lsc = 1.0f / sh.l_scale;
-    const float hsc = 1.0f / sh.h_scale;
-    if (y < ny) {
-        make_refs<S, T>(rf, sh, c, y, ny);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            f[i] = Pol<typename FStore<S>::type, T>::ld(io.f_in + (i * P + k), rf.f[i], fsc);
-            g[i] = Pol<S, T>::ld(io.g_in + (i * P + k), rf.g[i], gsc);
-        }
-#pragma unroll
-        for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], lsc);
-#pragma unroll
-        for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.h_in + (i * P + k), T(0), hsc);
-        pux_prev = T(io.aux_in[AUX_PUX * P + k]);
-        puy_prev = T(io.aux_in[AUX_PUY * P + k]);
-        fs_prev = T(io.aux_in[AUX_FS * P + k]);
-        mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
-        Q_prev = T(io.aux_in[AUX_Q * P + k]);
-        T l1234 = T(0);
-#pragma unroll
-        for (int i = 1; i < 5; i++) l1234 += l[i];
-        local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
-        // keep the populations for phase 2 in shared memory, not registers
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            stash[i][ty][tx] = f[i];
-            stash[9 + i][ty][tx] = h[i];
-            stash[18 + i][ty][tx] = g[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 5; i++) stash[27 + i][ty][tx] = l[i];
-        sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
-        sm.ps[ty + 1][tx + 1] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
-    }
-
-    // ---- phase 1: halo ring, recomputed from the neighbours' populations
     constexpr int NRING = 2 * 34 + 2 * BY;
-    for (int r = tid; r < NRING; r += 32 * BY) {
-        int ex, ey;
-        ring_slot<BY>(r, ex, ey);
-        const int hy = y0 - 1 + ey;
-        if (hy < 0 || hy >= ny) continue;
-        // x0 - 1 + ex lies in [-1, nx + 32]: beyond nx only on a ragged last tile
-        int hx = x0 - 1 + ex;
-        hx = hx < 0 ? hx + nx : (hx >= nx ? (hx - nx < nx ? hx - nx : (hx - nx) % nx) : hx);
-        cell_to_smem<S, T, A, BY>(io, c, sh, sm, ex, ey, hx, hy);
+    static_assert(NRING <= 32 * BY, "one ring cell per thread at most");
+    if constexpr (ASYNC && std::is_same<S, T>::value && std::is_same<typename FStore<S>::type, S>::value) {
+        // ---- phase 1, FP32/FP64: the own cell's populations go straight
+        // from global to the stash (cp.async, no registers), the ring cell's
+        // loads are issued meanwhile, so both wait for memory once
+        T pv = T(0), Sv = T(0);
+        if (y < ny) {
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                cp_async_elem(&stash[i][ty][tx], io.f_in + (i * P + k));
+                cp_async_elem(&stash[9 + i][ty][tx], io.h_in + (i * P + k));
+                cp_async_elem(&stash[18 + i][ty][tx], io.g_in + (i * P + k));
+            }
+#pragma unroll
+            for (int i = 0; i < 5; i++) cp_async_elem(&stash[27 + i][ty][tx], io.l_in + (i * P + k));
+            pux_prev = T(io.aux_in[AUX_PUX * P + k]);
+            puy_prev = T(io.aux_in[AUX_PUY * P + k]);
+            fs_prev = T(io.aux_in[AUX_FS * P + k]);
+            mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
+            Q_prev = T(io.aux_in[AUX_Q * P + k]);
+            pv = T(io.aux_in[AUX_P * P + k]);
+            Sv = T(io.aux_in[AUX_S * P + k]);
+        }
+        // the ring cell of this thread, if any
+        int rex = 0, rey = 0;
+        bool ring = false;
+        CellLoad<T> rl;
+        T rp = T(0), rS = T(0);
+        if (tid < NRING) {
+            ring_slot<BY>(tid, rex, rey);
+            const int hy = y0 - 1 + rey;
+            // x0 - 1 + ex lies in [-1, nx + 32]: beyond nx only on a ragged last tile
+            int hx = x0 - 1 + rex;
+            hx = hx < 0 ? hx + nx : (hx >= nx ? (hx - nx < nx ? hx - nx : (hx - nx) % nx) : hx);
+            ring = hy >= 0 && hy < ny;
+            if (ring)
+                load_ring_cell<S, T, A>(io, c, sh, P, (uint32_t)hy * (uint32_t)io.pitch + (uint32_t)hx, hy, rl, rp, rS);
+        }
+        if (y < ny) {
+            cp_async_wait_all();
+            T f[9], g[9];
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                f[i] = stash[i][ty][tx];
+                g[i] = stash[18 + i][ty][tx];
+            }
+            T l1234 = stash[28][ty][tx];
+            l1234 = l1234 + stash[29][ty][tx];
+            l1234 = l1234 + stash[30][ty][tx];
+            l1234 = l1234 + stash[31][ty][tx];
+            local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
+            sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
+            sm.ps[ty + 1][tx + 1] = {pv, Sv};
+        }
+        if (ring) {
+            Macro<T> mr;
+            local_macros<T>(rl.f, rl.g, rl.l1234, rl.fs_prev, rl.mdot_prev, rl.Q_prev, c, mr);
+            sm.q[rey][rex] = {mr.psi, mr.rho, mr.eps, mr.phi};
+            sm.ps[rey][rex] = {rp, rS};
+        }
+        __syncthreads();
+    } else {
+        // ---- phase 1: own cell (kept in registers) -------------------------
+        Refs<T> rf;
+        T f[9], g[9], l[5], h[9];
+        const float fsc = 1.0f / sh.f_scale, gsc = 1.0f / sh.g_scale, lsc = 1.0f / sh.l_scale;
+        const float hsc = 1.0f / sh.h_scale;
+        if (y < ny) {
+            make_refs<S, T>(rf, sh, c, y, ny);
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                f[i] = Pol<typename FStore<S>::type, T>::ld(io.f_in + (i * P + k), rf.f[i], fsc);
+                g[i] = Pol<S, T>::ld(io.g_in + (i * P + k), rf.g[i], gsc);
+            }
+#pragma unroll
+            for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], lsc);
+#pragma unroll
+            for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.h_in + (i * P + k), T(0), hsc);
+            pux_prev = T(io.aux_in[AUX_PUX * P + k]);
+            puy_prev = T(io.aux_in[AUX_PUY * P + k]);
+            fs_prev = T(io.aux_in[AUX_FS * P + k]);
+            mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
+            Q_prev = T(io.aux_in[AUX_Q * P + k]);
+            T l1234 = T(0);
+#pragma unroll
+            for (int i = 1; i < 5; i++) l1234 += l[i];
+            local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
+            // keep the populations for phase 2 in shared memory, not registers
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                stash[i][ty][tx] = f[i];
+                stash[9 + i][ty][tx] = h[i];
+                stash[18 + i][ty][tx] = g[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 5; i++) stash[27 + i][ty][tx] = l[i];
+            sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
+            sm.ps[ty + 1][tx + 1] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
+        }
+
+        // ---- phase 1: halo ring, recomputed from the neighbours' populations
+        for (int r = tid; r < NRING; r += 32 * BY) {
+            int ex, ey;
+            ring_slot<BY>(r, ex, ey);
+            const int hy = y0 - 1 + ey;
+            if (hy < 0 || hy >= ny) continue;
+            // x0 - 1 + ex lies in [-1, nx + 32]: beyond nx only on a ragged last tile
+            int hx = x0 - 1 + ex;
+            hx = hx < 0 ? hx + nx : (hx >= nx ? (hx - nx < nx ? hx - nx : (hx - nx) % nx) : hx);
+            cell_to_smem<S, T, A, BY>(io, c, sh, sm, ex, ey, hx, hy);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     fill_ghosts<T, BY>(sm, c, y0, ny, tid);
     __syncthreads();
@@ -820,7 +926,7 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_step(DevS
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
     const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
     sr_advance(s, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
-    step_tile<S, T, A, BY>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
+    step_tile<S, T, A, BY, true>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
 }
 
 // ---------------------------------------------------------------------------

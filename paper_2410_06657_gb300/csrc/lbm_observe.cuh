@@ -46,11 +46,6 @@ __device__ __forceinline__ void obs_macros(const Planes<S> &pc, const S *lb, con
                          double(aux[AUX_Q * P + k]), c, m);
 }
 
-// The stored values one cell's macros need, in the arithmetic type T.
-template <typename T>
-struct CellLoad {
-    T f[9], g[9], l1234, fs_prev, mdot_prev, Q_prev;
-};
 
 template <typename S, typename T, typename A>
 __device__ __forceinline__ void load_cell(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
