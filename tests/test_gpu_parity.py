@@ -2,7 +2,7 @@
 
 Fields are compared element by element on the same seeded inputs.  The FP64
 library is built without FMA contraction and follows the oracle's operation
-order, so its bar is the benchmark spec's tolerance: every stored field within
+order, so its bar is the required tolerance: every stored field within
 1e-12 of the oracle's in the max norm relative to the field's largest
 magnitude, after up to 1000 steps.  FP32 runs are held to tolerances derived
 from single-precision rounding (see test docstrings).
@@ -112,7 +112,7 @@ def test_fp64_matches_oracle_step_by_step(lbm, nx, ny, R, theta):
 
 @pytest.mark.parametrize("nx,ny", [(8, 6), (16, 8), (37, 19)])
 def test_fp64_matches_oracle_after_1000_steps(lbm, nx, ny):
-    """Spec bar: fields within 1e-12 (normwise) after 1000 steps, with
+    """Required bar: fields within 1e-12 (normwise) after 1000 steps, with
     two potential sweeps per step and a pre-solve."""
     R = 0.35 * ny
     p = W.params(nx=nx, ny=ny, R0=R, theta_deg=75.0, precision=W.FP64, k_e=2, Ste=0.3)
@@ -301,7 +301,7 @@ def test_batch_equals_members_stepped_alone(lbm, prec, tile):
     kernel form (no FMA contraction, same operation order).  In FP32 the
     members alone use the batch's tile height; the batched kernel and the
     single-instance kernel may still round differently; the
-    spec bar for single precision is on observables, so after 300
+    accuracy bar for single precision is on observables, so after 300
     steps the observables must agree to 1e-4 and the fields to 1e-3 (max
     norm with natural-scale floors)."""
     cases = [(96, 48, 15.0, 80.0, 0.1, 2.0, 5.0), (64, 32, 10.0, 110.0, 0.4, 0.5, 2.0),
@@ -452,7 +452,7 @@ def test_fp32_fields_track_the_oracle_over_a_short_horizon(lbm):
 
 
 def test_fp32_observables_over_2000_steps(lbm):
-    """Spec bar for FP32 runs: frozen fraction within 0.5 % and aspect
+    """Accuracy bar for FP32 runs: frozen fraction within 0.5 % and aspect
     ratio within 1 % of the FP64 oracle (128 x 64 case, 2000 steps)."""
     w = W.plain_fp64_small()
     p = dict(w["params"], precision=W.FP32)

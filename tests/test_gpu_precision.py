@@ -1,7 +1,7 @@
 """Precision variants against the FP64 run to full freezing (GPU required).
 
 The FP64 library reproduces the oracle's bits (test_gpu_parity.py), so it
-stands in for the oracle on runs too long for the CPU.  Spec bar for
+stands in for the oracle on runs too long for the CPU.  Accuracy bar for
 FP32 and FP16 weight-shifted storage: frozen fraction and freezing time
 within 0.5 %, droplet aspect ratio within 1 %.
 """
