@@ -35,13 +35,20 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_LU = {"f64": 2 * (32 + 7) * 8, "f32": 2 * (32 + 7) * 4, "f16s": 2 * (9 * 4 + 23 * 2) + 2 * 7 * 4}
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_MD = os.path.join(ROOT, "profiles", "k_step_f32_production_512x256.md")
-KERNEL_SOURCES = ["lbm_kernels.cuh", "lbm_launch.cuh", "step_f32.cu", "lbm_internal.h", "philox.h"]
+NOMINAL_FP64_TFLOPS = 1.25     # FP64 rate of the part (nominal; no measured figure exists)
 
 
-def kernel_source_hash() -> str:
+def profile_md(precision: str) -> str:
+    return os.path.join(ROOT, "profiles", f"k_step_{precision}_production_512x256.md")
+
+
+def kernel_sources(precision: str):
+    return ["lbm_kernels.cuh", "lbm_launch.cuh", f"step_{precision}.cu", "lbm_internal.h", "philox.h"]
+
+
+def kernel_source_hash(precision: str = "f32") -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in kernel_sources(precision):
         with open(os.path.join(ROOT, "paper_2410_06657_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -57,16 +64,17 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(precision: str, workload: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, if it was taken on the current kernel source (the summary
-    covers the FP32 production lattice only)."""
-    if precision != "f32" or workload != "production" or not os.path.exists(PROFILE_MD):
+def profiled(precision: str, workload: str, key: str):
+    """A figure of the committed ncu summary of the step kernel (DRAM bytes
+    per launch, FP64 flops per lattice update), if the summary was taken on
+    the current kernel source; summaries cover the production lattice."""
+    path = profile_md(precision)
+    if workload != "production" or not os.path.exists(path):
         return None
-    text = open(PROFILE_MD).read()
-    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    text = open(path).read()
+    m_b = re.search(key + r":\s*([0-9.eE+]+)", text)
     m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    if not m_b or not m_h or m_h.group(1) != kernel_source_hash():
+    if not m_b or not m_h or m_h.group(1) != kernel_source_hash(precision):
         return None
     return float(m_b.group(1))
 
@@ -293,7 +301,7 @@ def run_gpu(args, world, rank, local):
     alg_bytes = bpl * cells
     achieved = alg_bytes / (launch_us * 1e-6) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = profiled_traffic(args.precision, args.workload)
+    traffic = profiled(args.precision, args.workload, "traffic_bytes_per_launch")
 
     # context for the fraction: a plain device copy moving the same bytes
     # (half read, half written), timed the same way (L2 flushed, events);
@@ -355,16 +363,15 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": label, "cells": cells, "precision": args.precision, "k_e": p["k_e"],
                    "obs_every": obs_every, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": roofline_f64(args, cells, launch_us, traffic) if args.precision == "f64" else {
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": f"k_step<{args.precision}>", "launch_us": launch_us,
                      "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_lu": bpl,
                      "copy_same_bytes": {"launch_us": copy_us, "gbs": alg_bytes / (copy_us * 1e-6) / 1e9,
                                          "frac": alg_bytes / (copy_us * 1e-6) / 1e9 / peak,
                                          "note": "device-to-device copy of the same byte count, same timing"},
-                     **({"note": "FP64 arithmetic runs at a small fraction of the FP32 rate on this part: "
-                                 "the FP64 step is arithmetic-bound, far from the HBM roofline"}
-                        if args.precision == "f64" else {})},
+                     },
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": ctypes.sizeof(lbm.Obs), "steps": k_e2e},
@@ -378,6 +385,22 @@ def run_gpu(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def roofline_f64(args, cells, launch_us, traffic):
+    """The FP64 step is bound by FP64 arithmetic, not HBM: FP64 operations
+    per launch (DADD, DMUL one each, DFMA two, counted by ncu on this kernel
+    source) over the launch time, against the part's nominal FP64 rate."""
+    flops_lu = profiled("f64", args.workload, "fp64_flops_per_lu")
+    if flops_lu is None:
+        return {"bound": "alu", "achieved": None, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": traffic, "peak_kind": "nominal",
+                "kernel": "k_step<f64>", "launch_us": launch_us,
+                "note": "FP64 operation count not profiled for this source"}
+    tflops = flops_lu * cells / (launch_us * 1e-6) / 1e12
+    return {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+            "frac": tflops / NOMINAL_FP64_TFLOPS, "traffic": traffic, "peak_kind": "nominal",
+            "kernel": "k_step<f64>", "launch_us": launch_us, "fp64_flops_per_lu": flops_lu}
 
 
 # ---------------------------------------------------------------------------
