@@ -102,6 +102,22 @@ def droplet_front(Fo, Ste=0.2, rho_sl=0.9, theta=120.0, alpha_lg=0.2, R=16.0, nx
     return dict(Fo=ob["Fo"], front_over_R0=ob["front"] / R)
 
 
+def freezing_time(R_sigma, S_eps, CaE, Ste=0.2, rho_sl=0.9, theta=120.0, alpha_lg=0.2, R=16.0, nx=96, ny=48,
+                  every=20):
+    """Steps until the frozen fraction reaches 0.99, observed every `every` steps."""
+    W = _W()
+    p = W.params(nx=nx, ny=ny, Ste=Ste, rho_sl=rho_sl, theta_deg=theta, alpha_lg=alpha_lg, CaE=CaE,
+                 R_sigma=R_sigma, S_eps=S_eps, R0=R)
+    o = _oracle().Oracle(p)
+    xc, yc = W.sessile_center(nx, R, theta)
+    o.init_droplet(R, xc, yc, 2000)
+    ob = o.observables()
+    while ob["t_fre"] < 0 and o.t < 100000:
+        o.step(every)
+        ob = o.observables()
+    return dict(t_fre=ob["t_fre"], height=ob["height"], R_tr=ob["R_tr"])
+
+
 def mass_conservation(steps=1000):
     """Sessile drop with the field on and no freezing (T_w = T_m)."""
     W = _W()
@@ -148,6 +164,9 @@ JOBS = {
     "deform_2_5": (deformation, (2.0, 5.0)),
     "front_paper": (droplet_front, (0.62,)),
     "mass": (mass_conservation, ()),
+    "freeze_off": (freezing_time, (5.0, 2.0, 0.0)),
+    "freeze_OB-": (freezing_time, (2.0, 5.0, 1.0)),
+    "freeze_PR-": (freezing_time, (5.0, 9.5, 1.0)),
 }
 
 
@@ -162,7 +181,7 @@ def run_all(processes=None):
     ctx = mp.get_context("spawn")
     procs = processes or min(len(JOBS), max(1, os.cpu_count() or 1))
     # longest jobs first so the pool drains evenly
-    order = ["deform_5_2", "deform_2_5", "sensitivity", "laplace_10", "laplace_14", "laplace_18",
+    order = ["freeze_off", "freeze_OB-", "freeze_PR-", "deform_5_2", "deform_2_5", "sensitivity", "laplace_10", "laplace_14", "laplace_18",
              "laplace_14_W5", "angle_60", "angle_90", "angle_120", "front_paper",
              "mass", "stefan", "stefan_solid_diffusivity", "volume_0.9", "volume_1.1"]
     with ctx.Pool(procs) as pool:

@@ -305,6 +305,23 @@ def test_droplet_front_matches_paper(runs):
     assert abs(g["h_numerical"] / g["h_analytical"] - 1) < 0.10
 
 
+def test_field_effect_on_freezing_time(runs):
+    """Sec. 5.4, Fig. 14(b): with Ste = 0.2 and theta = 120 the field
+    shortens the freezing of the oblate OB- droplet (it is pressed down,
+    its contact line lengthens) and prolongs that of the prolate PR-
+    droplet; t* = (t_CaE - t_0) / t_0 has the printed signs.  The heights
+    move the way the paper explains it (OB- lower, contact line longer)."""
+    g = GOLDEN["freezing_time_with_field"]
+    t0 = runs["freeze_off"]["t_fre"]
+    assert t0 > 0
+    t_ob = (runs["freeze_OB-"]["t_fre"] - t0) / t0
+    t_pr = (runs["freeze_PR-"]["t_fre"] - t0) / t0
+    assert math.copysign(1, t_ob) == g["sign_OB-"] and t_ob != 0, t_ob
+    assert math.copysign(1, t_pr) == g["sign_PR-"] and t_pr != 0, t_pr
+    assert runs["freeze_OB-"]["height"] < runs["freeze_off"]["height"]
+    assert runs["freeze_OB-"]["R_tr"] > runs["freeze_off"]["R_tr"]
+
+
 @pytest.mark.parametrize("theta", [60.0, 90.0, 120.0])
 def test_observables_geometry_of_initial_cap(theta):
     """The observable definitions on the initial circular cap: height
