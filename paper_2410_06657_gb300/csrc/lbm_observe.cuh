@@ -13,7 +13,8 @@ namespace lbm {
 // Observables (row a10): FP64 reductions over the tile grid.  Each block
 // handles a 32 x 8 tile plus a one-cell halo (for q_v's stencils and the
 // interface crossings) and leaves block partial sums and order-independent
-// max/min candidates in the workspace; the last block to finish reduces them.
+// max/min candidates in the workspace; the last block of each group of
+// OBS_GROUP blocks sums its group and the last group finishes the reduction.
 // ---------------------------------------------------------------------------
 constexpr int OBS_BY = 8;
 
