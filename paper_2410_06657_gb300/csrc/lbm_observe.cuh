@@ -351,36 +351,39 @@ static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratc
     }
     if ((t & 31) == 0) s_wb[t >> 5] = wb;
     __syncthreads();
+    // everything from registers and shared memory; the FP64 divisions are
+    // long on this part, so four warps take one group of results each
+    lbm_obs *o = ws.obs;
     if (t == 0) {
-        // everything from registers and shared memory; the stores below do
-        // not wait for one another
-        const double mass = s_fin[0][0], enth = s_fin[1][0], solid = s_fin[2][0], charge = s_fin[3][0];
-        const double liq = s_fin[4][0], liqu = s_fin[5][0], qdot = s_fin[6][0];
-        unsigned long long wmax = s_wb[0];
-        for (int w = 1; w < 8; w++) wmax = s_wb[w] > wmax ? s_wb[w] : wmax;
-        const double width = __longlong_as_double((long long)wmax), height = s_height;
+        const double mass = s_fin[0][0], solid = s_fin[2][0];
         const double ff = (mass != 0.0) ? solid / mass : 0.0;
         long long t_fre = s_tfre;
         if (t_fre < 0 && ff >= 0.99) t_fre = sc.step;
-        lbm_obs *o = ws.obs;
         o->step = sc.step;
-        o->Fo = sc.alpha_l * (double)sc.step / (sc.R0 * sc.R0);
         o->mass = mass;
-        o->enthalpy = enth;
+        o->enthalpy = s_fin[1][0];
         o->solid = solid;
-        o->charge = charge;
+        o->charge = s_fin[3][0];
         o->frozen_fraction = ff;
-        o->height = height;
-        o->width = width;
-        o->aspect = (width > 0.0) ? height / width : 0.0;
         o->R_tr = s_rtr;
         o->front = s_front;
         o->t_fre = t_fre;
         o->Fo_fre = (t_fre >= 0) ? sc.alpha_l * (double)t_fre / (sc.R0 * sc.R0) : -1.0;
         o->status = s_bad ? LBM_ERR_DIVERGED : LBM_OK;
         o->reserved = 0;
+        o->Qdot = s_fin[6][0];                                                  // R24
+    } else if (t == 32) {
+        o->Fo = sc.alpha_l * (double)sc.step / (sc.R0 * sc.R0);
+    } else if (t == 64) {
+        unsigned long long wmax = s_wb[0];
+        for (int w = 1; w < 8; w++) wmax = s_wb[w] > wmax ? s_wb[w] : wmax;
+        const double width = __longlong_as_double((long long)wmax), height = s_height;
+        o->height = height;
+        o->width = width;
+        o->aspect = (width > 0.0) ? height / width : 0.0;
+    } else if (t == 96) {
+        const double liq = s_fin[4][0], liqu = s_fin[5][0];
         o->Pe = (liq > 0.0) ? 2.0 * sc.R0 * (liqu / liq) / sc.alpha_l : 0.0;     // R25
-        o->Qdot = qdot;                                                         // R24
     }
     // leave the workspace at the identities of its reductions for the next
     // call (0 for maxima and flags, all ones for minima)
