@@ -2,7 +2,8 @@
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                 [--precision f32|f64|f16s]
-                [--workload production|precision|batched|serving]
+                [--workload production|precision|batched|serving|regimes]
+                [--requests N --max-ny NY --budget-gb G] [--with-oracle]
 
 A step is one pass of the whole hot path over the lattice: the fused
 collide-and-stream launch (local macros, stencils, forces, four collisions,
@@ -13,6 +14,15 @@ Ste = 0.5, rho_s/rho_l = 0.9, FP32.  The lattice state (about 45 MB) fits in
 L2, so L2 is flushed (a 256 MB write) before every timed step, outside the
 timed events.  Under torchrun each rank advances its own instance (replicas,
 no collective on the data path) and the slowest rank's time counts.
+
+Other workloads: `precision` (1024 x 512, R = 160, theta = 60, PR+);
+`batched` (64 uneven instances in one launch per step, against the same
+instances stepped one after another); `serving` (Poisson arrivals run to
+frozen fraction 0.99 under an HBM budget: p50/p99 time to result);
+`regimes` (the production droplet to freezing with the field off, prolate
+and oblate; --with-oracle adds the oracle on the 4x-coarsened lattice).
+The roofline object is the HBM one for FP32 and FP16S and the FP64
+arithmetic one for FP64, whose step is bound by the FP64 pipe.
 
 --impl reference times the FP64 CPU oracle on the same workload and metric.
 """
