@@ -40,9 +40,9 @@ enum {
     LBM_FP64 = 0,  /* populations and arithmetic in double                      */
     LBM_FP32 = 1,  /* populations and arithmetic in float                       */
     LBM_FP16S = 2  /* h, g, l stored as half after subtracting a reference      */
-                   /* state (weight-shifted) and rounded stochastically; the    */
-                   /* phase-field populations f stay in float; arithmetic in    */
-                   /* float                                                     */
+                   /* state (weight-shifted); g and l rounded stochastically,   */
+                   /* h to nearest; the phase-field populations f stay in       */
+                   /* float; arithmetic in float                                */
 };
 
 /* Return codes. */

@@ -98,7 +98,9 @@ struct Pol<__half, float> {
 };
 
 // Random bits of the stochastic rounding: one Philox block per cell, step
-// and population system (counter), under a fixed key.
+// and population system (counter), under a fixed key.  The enthalpy and
+// potential populations are rounded stochastically; the flow populations
+// change by more than half a spacing per step and are rounded to nearest.
 constexpr uint32_t SR_KEY0 = 0x24100665u, SR_KEY1 = 0x0F16A5EDu;
 __device__ __forceinline__ void sr_block(uint32_t w[4], long long k, uint32_t step, uint32_t sys) {
     w[0] = (uint32_t)k;
@@ -586,8 +588,6 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         const T A3 = T(3) * p;                      // p / c_s^2
         const T S3 = Sn - T(3) * uF;                // S - u.F~ / c_s^2
         const T Gx = Fx + rfx, Gy = Fy + rfy;
-        uint32_t rb[4] = {0u, 0u, 0u, 0u};
-        if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 1u);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             T post;
@@ -610,10 +610,9 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             }
             const int yt = y + CY[i];
             if (EDGE && (yt < 0 || yt >= ny))
-                Pol<S, T>::st_sr(io.h_out + (OPP9[i] * P + k), post, T(0), sh.h_scale, bits13(rb, i));
+                Pol<S, T>::st(io.h_out + (OPP9[i] * P + k), post, T(0), sh.h_scale);
             else
-                Pol<S, T>::st_sr(io.h_out + (i * P + dest(i, CX[i], CY[i])), post, T(0), sh.h_scale,
-                                 bits13(rb, i));
+                Pol<S, T>::st(io.h_out + (i * P + dest(i, CX[i], CY[i])), post, T(0), sh.h_scale);
         }
     }
     // a5: phase field

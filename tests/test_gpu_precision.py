@@ -42,9 +42,10 @@ def reference():
 
 @pytest.mark.parametrize("prec", [W.FP32, W.FP16S], ids=["fp32", "fp16s"])
 def test_observables_to_freezing_match_fp64(reference, prec):
-    """Half storage rounds the post-collision populations stochastically:
-    with round-to-nearest the per-step change from heat conduction (about
-    1e-5 of an enthalpy population) is below half a half-precision spacing,
+    """Half storage rounds the enthalpy and potential populations
+    stochastically: with round-to-nearest the per-step change from heat
+    conduction (about 1e-5 of an enthalpy population) is below half a
+    half-precision spacing,
     the stored values never move and freezing stops near 57 % frozen.  The
     phase-field populations stay in single precision: in half, the rounding
     noise on psi in the cold gas counts as solid (f_s = psi (1 - f_l)) and
