@@ -439,6 +439,35 @@ __device__ __forceinline__ void cp_async_elem(V *dst_smem, const V *src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Warp-cooperative 16-byte copies of one full tile row (32 cells starting at
+// offset k0, a multiple of 32 elements, so every chunk is 16-byte aligned)
+// of the 32 population planes into the stash: each warp instruction moves
+// 32 / CR planes, lane tx copies chunk tx % CR of plane j * (32 / CR) +
+// tx / CR.  Planes 0-26 (f, h, g) lie contiguously from pin, planes 27-31
+// (l) from lin.  A quarter (FP32) or half (FP64) of the instructions of
+// one copy per element.
+template <typename T, int BY>
+__device__ __forceinline__ void stash_row_async(T (*stash)[BY][32], int ty, int tx, const T *pin,
+                                                const T *lin, uint32_t P, uint32_t k0) {
+    constexpr int CR = 32 * int(sizeof(T)) / 16;    // 16-byte chunks per row
+    constexpr int PPJ = 32 / CR;                    // planes per instruction
+    constexpr int EPC = 16 / int(sizeof(T));        // elements per chunk
+    const int part = tx % CR, sub = tx / CR;
+#pragma unroll
+    for (int j = 0; j < CR; j++) {
+        const int q = j * PPJ + sub;
+        const T *src;
+        if (j * PPJ + PPJ <= 27)
+            src = pin + ((uint32_t)q * P + k0);
+        else if (j * PPJ >= 27)
+            src = lin + ((uint32_t)(q - 27) * P + k0);
+        else
+            src = q < 27 ? pin + ((uint32_t)q * P + k0) : lin + ((uint32_t)(q - 27) * P + k0);
+        const unsigned d = (unsigned)__cvta_generic_to_shared(&stash[q][ty][part * EPC]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + part * EPC) : "memory");
+    }
+}
+
 // Population sources for step_cell.
 template <typename T, int BY>
 struct StashPops {            // own cell's populations stashed in shared memory
@@ -766,19 +795,25 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     constexpr int NRING = 2 * 34 + 2 * BY;
     static_assert(NRING <= 32 * BY, "one ring cell per thread at most");
     if constexpr (ASYNC && std::is_same<S, T>::value && std::is_same<typename FStore<S>::type, S>::value) {
-        // ---- phase 1, FP32/FP64: the own cell's populations go straight
-        // from global to the stash (cp.async, no registers), the ring cell's
-        // loads are issued meanwhile, so both wait for memory once
+        // ---- phase 1, FP32/FP64: the own cells' populations go straight
+        // from global to the stash (cp.async, no registers; each warp copies
+        // its row in 16-byte chunks), the ring cell's loads are issued
+        // meanwhile, so both wait for memory once
         T pv = T(0), Sv = T(0);
         if (y < ny) {
+            if (x0 + 32 <= nx) {
+                stash_row_async<T, BY>(stash, ty, tx, io.f_in, io.l_in, P,
+                                       (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x0);
+            } else {          // ragged last tile: wrapped slots, one element each
 #pragma unroll
-            for (int i = 0; i < 9; i++) {
-                cp_async_elem(&stash[i][ty][tx], io.f_in + (i * P + k));
-                cp_async_elem(&stash[9 + i][ty][tx], io.h_in + (i * P + k));
-                cp_async_elem(&stash[18 + i][ty][tx], io.g_in + (i * P + k));
+                for (int i = 0; i < 9; i++) {
+                    cp_async_elem(&stash[i][ty][tx], io.f_in + (i * P + k));
+                    cp_async_elem(&stash[9 + i][ty][tx], io.h_in + (i * P + k));
+                    cp_async_elem(&stash[18 + i][ty][tx], io.g_in + (i * P + k));
+                }
+#pragma unroll
+                for (int i = 0; i < 5; i++) cp_async_elem(&stash[27 + i][ty][tx], io.l_in + (i * P + k));
             }
-#pragma unroll
-            for (int i = 0; i < 5; i++) cp_async_elem(&stash[27 + i][ty][tx], io.l_in + (i * P + k));
             pux_prev = T(io.aux_in[AUX_PUX * P + k]);
             puy_prev = T(io.aux_in[AUX_PUY * P + k]);
             fs_prev = T(io.aux_in[AUX_FS * P + k]);
@@ -804,6 +839,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         }
         if (y < ny) {
             cp_async_wait_all();
+            __syncwarp();     // the row's planes were copied by the whole warp
             T f[9], g[9];
 #pragma unroll
             for (int i = 0; i < 9; i++) {
