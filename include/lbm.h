@@ -226,6 +226,26 @@ int lbm_observables_async(struct lbm_handle *h);
 int lbm_observables_fetch(struct lbm_handle *h, lbm_obs *out);
 
 /*
+ * Streaming observables: enqueue the reduction and the copy of its result
+ * into the caller's host memory *out on the handle's stream, and return
+ * without waiting.  With *out in page-locked memory the copy is
+ * asynchronous, so a loop of steps and observations runs without a host
+ * round trip per step; *out holds the values once lbm_sync has returned and
+ * must stay valid until then (pageable memory works too, the copy then
+ * waits).  Divergence is reported in out->status (LBM_ERR_DIVERGED), not by
+ * the return value, and does not stop later steps.  Errors: BADPARAM (NULL),
+ * STATE, CUDA.
+ */
+int lbm_observables_to_host(struct lbm_handle *h, lbm_obs *out);
+
+/*
+ * Wait for everything enqueued on the handle's stream.  Returns CUDA if a
+ * bounded wait inside a step kernel ran out (the status lbm_observables
+ * reports).  Errors: BADPARAM (NULL), CUDA.
+ */
+int lbm_sync(struct lbm_handle *h);
+
+/*
  * Copy one field to the host as doubles (layout: see the field ids).
  * Synchronises the stream.  Errors: BADPARAM (unknown id, NULL), STATE, CUDA.
  */

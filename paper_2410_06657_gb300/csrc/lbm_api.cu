@@ -610,6 +610,23 @@ int lbm_observables(lbm_handle *h, lbm_obs *out) {
     return lbm_observables_fetch(h, out);
 }
 
+int lbm_observables_to_host(lbm_handle *h, lbm_obs *out) {
+    if (!h || !out) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    const int rc = lbm_observables_async(h);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle *h) {
+    if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    unsigned int err = 0;
+    CK(cudaMemcpyAsync(&err, h->err, sizeof err, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (err) return fail(LBM_ERR_CUDA, "a bounded wait in the step kernel timed out (tensor loads did not complete)");
+    return LBM_OK;
+}
+
 int lbm_substrate_heat_flux(lbm_handle *h, double *host_out) {
     if (!h || !host_out) return fail(LBM_ERR_BADPARAM, "NULL argument");
     if (h->P.ny < 3) return fail(LBM_ERR_BADPARAM, "the substrate heat flux needs ny >= 3");

@@ -31,7 +31,7 @@ EXPORTS = [
     "lbm_set_field", "lbm_state_bytes", "lbm_export_state", "lbm_import_state",
     "lbm_step_count", "lbm_configure", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tile_rows", "lbm_batch_destroy", "lbm_observables_noalloc",
-    "lbm_substrate_heat_flux",
+    "lbm_substrate_heat_flux", "lbm_observables_to_host", "lbm_sync",
 ]
 
 
@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True):
     L.lbm_observables.argtypes = [vp, P(Obs)]
     L.lbm_observables_async.argtypes = [vp]
     L.lbm_observables_fetch.argtypes = [vp, P(Obs)]
+    L.lbm_observables_to_host.argtypes = [vp, vp]
+    L.lbm_sync.argtypes = [vp]
     L.lbm_get_field.argtypes = [vp, C.c_int32, P(C.c_double)]
     L.lbm_set_field.argtypes = [vp, C.c_int32, P(C.c_double)]
     L.lbm_state_bytes.restype = C.c_size_t
@@ -221,6 +223,15 @@ class Simulation:
         if rc not in (OK, ERR_DIVERGED):
             _check(rc)
         return o.as_dict()
+
+    def observables_to_host(self, addr: int):
+        """Enqueue the observables and their copy to the host address `addr`
+        (an lbm_obs, page-locked for an asynchronous copy); read it with
+        `Obs.from_address(addr)` after `sync()`."""
+        _check(load().lbm_observables_to_host(self._h, C.c_void_p(addr)))
+
+    def sync(self):
+        _check(load().lbm_sync(self._h))
 
     def get(self, name: str) -> np.ndarray:
         planes = FIELD_PLANES.get(name, 1)

@@ -290,6 +290,31 @@ def test_graph_replay_and_single_launches_agree_bitwise(lbm):
     assert a.t == b.t == 64
 
 
+def test_streamed_observables_equal_synchronous_ones(lbm):
+    """lbm_observables_to_host enqueues the reduction and its copy into
+    page-locked host memory without waiting; after lbm_sync every record
+    equals what lbm_observables returns at the same step."""
+    import ctypes
+    import torch
+    p = W.params(nx=128, ny=64, R0=20.0, precision=W.FP32)
+    xc, yc = W.sessile_center(128, 20.0, 90.0)
+    a, b = lbm.Simulation(p), lbm.Simulation(p)
+    a.init_droplet(20.0, xc, yc, 0)
+    b.init_droplet(20.0, xc, yc, 0)
+    n, sz = 6, ctypes.sizeof(lbm.Obs)
+    buf = torch.zeros(n * sz, dtype=torch.uint8, pin_memory=True)
+    want = []
+    for i in range(n):
+        a.step(10)
+        a.observables_to_host(buf.data_ptr() + i * sz)
+        b.step(10)
+        want.append(b.observables())
+    a.sync()
+    got = [lbm.Obs.from_address(buf.data_ptr() + i * sz).as_dict() for i in range(n)]
+    assert got == want
+    assert [g["step"] for g in got] == [10 * (i + 1) for i in range(n)]
+
+
 # --------------------------------------------------------------------------
 # Batched form: same bits as stepping alone
 # --------------------------------------------------------------------------
