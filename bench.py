@@ -285,21 +285,25 @@ def run_gpu(args, world, rank, local):
     time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
+    # events a and c bracket each step; b separates the step launch from the
+    # observables only on the steps that observe, so the other steps carry
+    # no third event
     n_obs = 0
+    observe = [(i + 1) % obs_every == 0 for i in range(args.steps)]
     for i in range(args.steps):
         flush_l2()
         a, b, c = ev[i]
         a.record(stream)
         sim.step(1)
-        b.record(stream)
-        if (i + 1) % obs_every == 0:
+        if observe[i]:
+            b.record(stream)
             sim.observables_async()
             n_obs += 1
         c.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
-    step_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    step_ms = [ev[i][0].elapsed_time(ev[i][1] if observe[i] else ev[i][2]) for i in range(args.steps)]
     tot_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
     total_s = reduce_max(sum(tot_ms) / 1e3, world)
     obs = sim.observables_fetch()
@@ -342,21 +346,28 @@ def run_gpu(args, world, rank, local):
     ss_mlups = cells * n_ss / (s0.elapsed_time(s1) / 1e3) / 1e6
 
     # end to end through the C ABI with host buffers: every step uploads the
-    # whole state from pinned host memory, steps, and reads the observables
+    # whole state from pinned host memory, steps, and copies its observables
+    # into pinned host memory (streamed: the host enqueues the steps without
+    # a round trip each and waits once, then checks every record)
     nbytes = sim.state_bytes()
     host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     sim.export_state(host.numpy())
     k_e2e = max(10, min(args.steps, 200))
+    osz = ctypes.sizeof(lbm.Obs)
+    obs_host = torch.zeros(k_e2e * osz, dtype=torch.uint8, pin_memory=True)
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    for _ in range(k_e2e):
+    for i in range(k_e2e):
         sim.import_state(host.data_ptr())
         sim.step(1)
-        sim.observables()
-    torch.cuda.synchronize()
+        sim.observables_to_host(obs_host.data_ptr() + i * osz)
+    sim.sync()
     e2e_s = reduce_max(time.perf_counter() - t0, world)
     e2e_value = world * cells * k_e2e / e2e_s / 1e6
+    e2e_obs = [lbm.Obs.from_address(obs_host.data_ptr() + i * osz).as_dict() for i in range(k_e2e)]
+    if any(o["status"] != 0 or o["step"] != e2e_obs[0]["step"] for o in e2e_obs):
+        raise RuntimeError("end-to-end observables: a step diverged or read a wrong state")
 
     if rank != 0:
         return
@@ -384,7 +395,9 @@ def run_gpu(args, world, rank, local):
                      },
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": ctypes.sizeof(lbm.Obs), "steps": k_e2e},
+                "d2h_bytes_per_step": ctypes.sizeof(lbm.Obs), "steps": k_e2e,
+                "note": "per step: lbm_import_state from pinned host memory, lbm_step(1), "
+                        "lbm_observables_to_host into pinned host memory; one lbm_sync at the end"},
         "gpu_launches": args.steps + n_obs,
         "clocks": clocks,
         "steady_state": {"value": ss_mlups, "unit": "MLUPS",

@@ -263,11 +263,16 @@ int lbm_set_field(struct lbm_handle *h, int32_t field, const double *host_in);
  * counter, the stochastic-rounding counter, t_fre and every stored array in
  * the handle's storage precision.
  * lbm_state_bytes gives the size; export copies device -> host (synchronous),
- * import copies host -> device (enqueued on the stream; from pinned host
- * memory it is asynchronous, and the caller must keep the buffer alive and
- * unchanged until the stream reaches that point).  A snapshot only imports
- * into a handle created with identical lbm_params.
- * Errors: BADPARAM (NULL, size mismatch), STATE, CUDA.
+ * import copies host -> device and is ordered on the handle's stream: the
+ * whole snapshot goes into one of two device buffers on a private copy
+ * stream, which does not wait for the work already enqueued on the handle's
+ * stream, and the handle's stream then unpacks it (device to device).  From
+ * pinned host memory the call is asynchronous: the caller keeps the buffer
+ * alive and unchanged until the handle's stream has passed the import (for
+ * instance lbm_sync).  The first import allocates the two buffers
+ * (2 x lbm_state_bytes of device memory, kept until lbm_destroy).  A
+ * snapshot only imports into a handle created with identical lbm_params.
+ * Errors: BADPARAM (NULL, size mismatch), OOM, STATE, CUDA.
  */
 size_t lbm_state_bytes(const struct lbm_handle *h);
 int lbm_export_state(struct lbm_handle *h, void *host, size_t bytes);

@@ -200,6 +200,13 @@ struct lbm_handle {
     unsigned long long *ws_max_base = nullptr, *ws_min_base = nullptr;
     unsigned int *ws_u32_base = nullptr;
     double *staging = nullptr;
+    // two device copies of imported snapshots: the host-to-device copy of an
+    // import runs on its own stream while the handle's stream still works
+    // on the state before it (allocated by the first import)
+    void *imp_buf[2] = {nullptr, nullptr};
+    cudaStream_t imp_st = nullptr;
+    cudaEvent_t imp_filled[2] = {nullptr, nullptr}, imp_free[2] = {nullptr, nullptr};
+    int imp_next = 0;
     int cur = 0, lcur = 0;
     int64_t step = 0;
     bool inited = false, diverged = false;
@@ -503,6 +510,15 @@ void lbm_destroy(lbm_handle *h) {
     drop_graphs(h);
     if (h->cap) cudaStreamDestroy(h->cap);
     cudaFree(h->staging);
+    if (h->imp_st) {
+        cudaStreamSynchronize(h->imp_st);
+        cudaStreamDestroy(h->imp_st);
+    }
+    for (int j = 0; j < 2; j++) {
+        if (h->imp_filled[j]) cudaEventDestroy(h->imp_filled[j]);
+        if (h->imp_free[j]) cudaEventDestroy(h->imp_free[j]);
+        cudaFree(h->imp_buf[j]);
+    }
     cudaFree(h->ws_mem);
     cudaFree(h->mem);
     delete h;
@@ -756,17 +772,41 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
     if (std::memcmp(hd.magic, "LBMGB300", 8) != 0 || hd.nx != h->P.nx || hd.ny != h->P.ny ||
         hd.precision != h->P.precision || hd.k_e != h->P.k_e)
         return fail(LBM_ERR_BADPARAM, "snapshot does not match this handle");
+    if (!h->imp_st) {
+        if (cudaMalloc(&h->imp_buf[0], bytes) != cudaSuccess || cudaMalloc(&h->imp_buf[1], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->imp_buf[0]);
+            h->imp_buf[0] = h->imp_buf[1] = nullptr;
+            return fail(LBM_ERR_OOM, "device allocation of the import buffers failed");
+        }
+        for (int j = 0; j < 2; j++) {
+            CK(cudaEventCreateWithFlags(&h->imp_filled[j], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->imp_free[j], cudaEventDisableTiming));
+        }
+        CK(cudaStreamCreateWithFlags(&h->imp_st, cudaStreamNonBlocking));
+    }
+    // the whole snapshot to device buffer j on the import stream, once the
+    // handle's stream has unpacked what buffer j held before (an event never
+    // recorded is no wait); then the handle's stream unpacks it
+    const int j = h->imp_next;
+    h->imp_next ^= 1;
+    const char *dev = static_cast<const char *>(h->imp_buf[j]);
+    CK(cudaStreamWaitEvent(h->imp_st, h->imp_free[j], 0));
+    CK(cudaMemcpyAsync(h->imp_buf[j], host, bytes, cudaMemcpyHostToDevice, h->imp_st));
+    CK(cudaEventRecord(h->imp_filled[j], h->imp_st));
+    CK(cudaStreamWaitEvent(h->st, h->imp_filled[j], 0));
     size_t a, b, c, d;
     snap_sizes(h, a, b, c, d);
-    const char *o = static_cast<const char *>(host) + sizeof hd;
-    CK(cudaMemcpyAsync(h->s.pop[h->cur], o, a, cudaMemcpyHostToDevice, h->st));
+    const char *o = dev + sizeof hd;
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(h->s.pop[h->cur], o, a, dd, h->st));
     CK(cudaMemcpyAsync(static_cast<char *>(h->s.pop[h->lcur]) + l_offset_bytes(h->P.precision, h->s.plane), o + a, b,
-                       cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(h->s.aux[h->cur], o + a + b, c, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(h->s.sigma, o + a + b + c, d, cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(h->ws.obs, o + a + b + c + d, sizeof(lbm_obs), cudaMemcpyHostToDevice, h->st));
-    CK(cudaMemcpyAsync(h->s.rng + h->cur, static_cast<const char *>(host) + offsetof(SnapHeader, sr_step),
-                       sizeof(uint32_t), cudaMemcpyHostToDevice, h->st));
+                       dd, h->st));
+    CK(cudaMemcpyAsync(h->s.aux[h->cur], o + a + b, c, dd, h->st));
+    CK(cudaMemcpyAsync(h->s.sigma, o + a + b + c, d, dd, h->st));
+    CK(cudaMemcpyAsync(h->ws.obs, o + a + b + c + d, sizeof(lbm_obs), dd, h->st));
+    CK(cudaMemcpyAsync(h->s.rng + h->cur, dev + offsetof(SnapHeader, sr_step), sizeof(uint32_t), dd, h->st));
+    CK(cudaEventRecord(h->imp_free[j], h->st));
     h->step = hd.step;
     h->inited = true;
     h->diverged = false;
