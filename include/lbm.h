@@ -239,9 +239,26 @@ int lbm_observables_fetch(struct lbm_handle *h, lbm_obs *out);
 int lbm_observables_to_host(struct lbm_handle *h, lbm_obs *out);
 
 /*
- * Wait for everything enqueued on the handle's stream.  Returns CUDA if a
- * bounded wait inside a step kernel ran out (the status lbm_observables
- * reports).  Errors: BADPARAM (NULL), CUDA.
+ * Observation fused into the next step: request the observables of the
+ * current state without a pass of their own over the lattice.  The next
+ * lbm_step reduces them inside its first step's kernel, which reads exactly
+ * this state (rows a1-a3 already evaluate every macro and stencil they
+ * need); any other call on the handle first runs them on their own, as
+ * lbm_observables_async would.  out: NULL to fetch the result later with
+ * lbm_observables_fetch, or host memory (page-locked for an asynchronous
+ * copy) that receives it behind that kernel, as lbm_observables_to_host.
+ * Same values as lbm_observables at this step, up to the grouping of the
+ * FP64 sums (the step's tiles are 32 x tile_rows, the observables kernel's
+ * 32 x 8).  With the TMA step form the reduction runs at once.
+ * Errors: BADPARAM (NULL handle), STATE, CUDA.
+ */
+int lbm_observables_deferred(struct lbm_handle *h, lbm_obs *out);
+
+/*
+ * Wait for everything enqueued on the handle's stream (running a deferred
+ * observation first).  Returns CUDA if a bounded wait inside a step kernel
+ * ran out (the status lbm_observables reports).  Errors: BADPARAM (NULL),
+ * CUDA.
  */
 int lbm_sync(struct lbm_handle *h);
 

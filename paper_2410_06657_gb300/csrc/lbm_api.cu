@@ -207,6 +207,12 @@ struct lbm_handle {
     cudaStream_t imp_st = nullptr;
     cudaEvent_t imp_filled[2] = {nullptr, nullptr}, imp_free[2] = {nullptr, nullptr};
     int imp_next = 0;
+    // an observation requested and not yet run: the next lbm_step runs it
+    // inside its first step's kernel (the state it reads is the one
+    // observed); any other call runs it first on its own
+    bool obs_pending = false;
+    Scalars obs_sc;
+    lbm_obs *obs_out = nullptr;      // host copy requested with it, if any
     int cur = 0, lcur = 0;
     int64_t step = 0;
     bool inited = false, diverged = false;
@@ -308,11 +314,17 @@ const void *consts_for(const lbm_handle *h) {
     return h->P.precision == LBM_FP64 ? static_cast<const void *>(&h->cd) : static_cast<const void *>(&h->cf);
 }
 
-cudaError_t do_step(lbm_handle *h, cudaStream_t st) {
+cudaError_t do_step(lbm_handle *h, cudaStream_t st, const Scalars *observe = nullptr) {
     const int ws = h->P.k_e > 1 ? 1 : 0;
     const void *c = consts_for(h);
     cudaError_t e;
-    if (h->use_tma) {
+    if (observe) {           // the step also reduces the observables of the state it reads
+        switch (h->P.precision) {
+        case LBM_FP64: e = launch_step_obs_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->ws, *observe, st); break;
+        case LBM_FP32: e = launch_step_obs_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->ws, *observe, st); break;
+        default: e = launch_step_obs_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->ws, *observe, st); break;
+        }
+    } else if (h->use_tma) {
         switch (h->P.precision) {
         case LBM_FP64: e = launch_step_tma_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->maps, st); break;
         case LBM_FP32: e = launch_step_tma_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->maps, st); break;
@@ -352,6 +364,27 @@ cudaError_t do_sweep(lbm_handle *h, cudaStream_t st) {
     return e;
 }
 
+// Run a pending observation on its own (the observables kernel) and the
+// host copy requested with it; every entry point that reads or changes the
+// state, other than lbm_step, calls this first.
+int run_pending_obs(lbm_handle *h) {
+    if (!h->obs_pending) return LBM_OK;
+    h->obs_pending = false;
+    cudaError_t e;
+    switch (h->P.precision) {
+    case LBM_FP64: e = launch_obs_f64(h->s, h->cur, h->lcur, &h->cd, h->sh, h->ws, h->obs_sc, h->st); break;
+    case LBM_FP32: e = launch_obs_f32(h->s, h->cur, h->lcur, &h->cf, h->sh, h->ws, h->obs_sc, h->st); break;
+    default: e = launch_obs_f16s(h->s, h->cur, h->lcur, &h->cf, h->sh, h->ws, h->obs_sc, h->st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "observables kernels");
+    if (h->obs_out) {
+        lbm_obs *out = h->obs_out;
+        h->obs_out = nullptr;
+        CK(cudaMemcpyAsync(out, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
+    }
+    return LBM_OK;
+}
+
 void drop_graphs(lbm_handle *h) {
     for (int a = 0; a < 2; a++)
         for (int b = 0; b < 2; b++)
@@ -373,6 +406,7 @@ int ensure_staging(lbm_handle *h) {
 }
 
 int finish_init(lbm_handle *h, const double *psi_dev, double R, double xc, double yc, int presolve) {
+    if (int rc_ = run_pending_obs(h)) return rc_;
     h->cur = 0;
     h->lcur = 0;
     const void *c = consts_for(h);
@@ -449,7 +483,9 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->s.pitch = pitch;
     h->s.plane = plane;
     // observables workspace
-    const int nb = obs_grid_blocks(nx, ny);
+    // sized for the larger grid: the observables kernel's or, for the
+    // observation fused into a step, the step's with 4-row tiles
+    const int nb = std::max(obs_grid_blocks(nx, ny), ((nx + 31) / 32) * ((ny + 3) / 4));
     const int ng = (nb + OBS_GROUP - 1) / OBS_GROUP;
     const size_t part_b = round_up((size_t)(nb + ng) * OBS_NSUM * sizeof(double), 256);
     const size_t qdot_b = round_up((size_t)nx * sizeof(double), 256);
@@ -476,14 +512,14 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->ws.bad = h->ws_u32_base + ny;
     h->ws.gcount = h->ws_u32_base + ny + 3;
     h->ws.gpartials = h->ws.partials + (size_t)nb * OBS_NSUM;
-    h->ws.ngroups = ng;
+    h->ws.nblocks = obs_grid_blocks(nx, ny);
+    h->ws.ngroups = (h->ws.nblocks + OBS_GROUP - 1) / OBS_GROUP;
     h->ws.obs = reinterpret_cast<lbm_obs *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes);
     h->err = reinterpret_cast<unsigned int *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b);
     h->s.err = h->err;
     h->s.rng = h->err + 4;     // two counters in the same 256-byte block
     h->qdot = reinterpret_cast<double *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b +
                                          err_b);
-    h->ws.nblocks = nb;
     if (cudaMemset(h->err, 0, err_b) != cudaSuccess || cudaMemset(h->ws_max_base, 0x00, h->ws_max_bytes) != cudaSuccess ||
         cudaMemset(h->ws_min_base, 0xFF, h->ws_min_bytes) != cudaSuccess ||
         cudaMemset(h->ws_u32_base, 0x00, h->ws_u32_bytes) != cudaSuccess) {
@@ -506,6 +542,7 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
 
 void lbm_destroy(lbm_handle *h) {
     if (!h) return;
+    h->obs_pending = false;      // a requested observation nobody can fetch any more
     cudaStreamSynchronize(h->st);
     drop_graphs(h);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -549,6 +586,19 @@ int lbm_step(lbm_handle *h, int64_t n) {
         int rc = ensure_maps(h);
         if (rc) return rc;
     }
+    if (n >= 1 && h->obs_pending) {
+        // the first step reads the observed state: it reduces the observables too
+        h->obs_pending = false;
+        cudaError_t e = do_step(h, h->st, &h->obs_sc);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel with observables");
+        if (h->obs_out) {
+            lbm_obs *out = h->obs_out;
+            h->obs_out = nullptr;
+            CK(cudaMemcpyAsync(out, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
+        }
+        h->step += 1;
+        n -= 1;
+    }
     // Long runs replay a captured graph of G steps (G even, so both parities
     // return to their starting values and the graph can be reused).
     const int G = 32;
@@ -588,6 +638,8 @@ int lbm_step(lbm_handle *h, int64_t n) {
 int lbm_observables_async(lbm_handle *h) {
     if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
     if (!h->inited) return fail(LBM_ERR_STATE, "observables before init");
+    int rc = run_pending_obs(h);       // an earlier request that no step has taken
+    if (rc) return rc;
     // the workspace starts at the identities of its reductions (set at
     // creation) and the reduction's last block restores them
     Scalars sc;
@@ -607,6 +659,8 @@ int lbm_observables_async(lbm_handle *h) {
 int lbm_observables_fetch(lbm_handle *h, lbm_obs *out) {
     if (!h || !out) return fail(LBM_ERR_BADPARAM, "NULL argument");
     if (!h->inited) return fail(LBM_ERR_STATE, "observables before init");
+    int rc = run_pending_obs(h);
+    if (rc) return rc;
     unsigned int err = 0;
     CK(cudaMemcpyAsync(out, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(&err, h->err, sizeof err, cudaMemcpyDeviceToHost, h->st));
@@ -634,8 +688,24 @@ int lbm_observables_to_host(lbm_handle *h, lbm_obs *out) {
     return LBM_OK;
 }
 
+int lbm_observables_deferred(lbm_handle *h, lbm_obs *out) {
+    if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    if (!h->inited) return fail(LBM_ERR_STATE, "observables before init");
+    if (h->use_tma) return out ? lbm_observables_to_host(h, out) : lbm_observables_async(h);
+    int rc = run_pending_obs(h);       // an earlier request that no step has taken
+    if (rc) return rc;
+    h->obs_pending = true;
+    h->obs_sc.step = h->step;
+    h->obs_sc.alpha_l = h->P.alpha_l;
+    h->obs_sc.R0 = h->P.R0;
+    h->obs_out = out;
+    return LBM_OK;
+}
+
 int lbm_sync(lbm_handle *h) {
     if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    int rc = run_pending_obs(h);
+    if (rc) return rc;
     unsigned int err = 0;
     CK(cudaMemcpyAsync(&err, h->err, sizeof err, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
@@ -647,6 +717,7 @@ int lbm_substrate_heat_flux(lbm_handle *h, double *host_out) {
     if (!h || !host_out) return fail(LBM_ERR_BADPARAM, "NULL argument");
     if (h->P.ny < 3) return fail(LBM_ERR_BADPARAM, "the substrate heat flux needs ny >= 3");
     if (!h->inited) return fail(LBM_ERR_STATE, "heat flux before init");
+    if (int rc_ = run_pending_obs(h)) return rc_;
     cudaError_t e;
     switch (h->P.precision) {
     case LBM_FP64: e = launch_heat_flux_f64(h->s, h->cur, h->lcur, &h->cd, h->sh, h->qdot, h->st); break;
@@ -668,6 +739,7 @@ static int field_planes(int field) {
 
 int lbm_get_field(lbm_handle *h, int32_t field, double *host_out) {
     if (!h || !host_out) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (int rc_ = run_pending_obs(h)) return rc_;
     const int planes = field_planes(field);
     if (!planes) return fail(LBM_ERR_BADPARAM, "unknown field id");
     if (!h->inited) return fail(LBM_ERR_STATE, "field access before init");
@@ -688,6 +760,7 @@ int lbm_get_field(lbm_handle *h, int32_t field, double *host_out) {
 
 int lbm_set_field(lbm_handle *h, int32_t field, const double *host_in) {
     if (!h || !host_in) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (int rc_ = run_pending_obs(h)) return rc_;
     const int planes = field_planes(field);
     if (!planes || (field >= LBM_FIELD_PSI && field <= LBM_FIELD_HTOT))
         return fail(LBM_ERR_BADPARAM, "field id is not writable");
@@ -736,6 +809,7 @@ size_t lbm_state_bytes(const lbm_handle *h) {
 
 int lbm_export_state(lbm_handle *h, void *host, size_t bytes) {
     if (!h || !host) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (int rc_ = run_pending_obs(h)) return rc_;
     if (bytes != lbm_state_bytes(h)) return fail(LBM_ERR_BADPARAM, "snapshot size mismatch");
     if (!h->inited) return fail(LBM_ERR_STATE, "export before init");
     size_t a, b, c, d;
@@ -766,6 +840,7 @@ int lbm_export_state(lbm_handle *h, void *host, size_t bytes) {
 
 int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
     if (!h || !host) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (int rc_ = run_pending_obs(h)) return rc_;
     if (bytes != lbm_state_bytes(h)) return fail(LBM_ERR_BADPARAM, "snapshot size mismatch");
     SnapHeader hd;
     std::memcpy(&hd, host, sizeof hd);
@@ -817,6 +892,7 @@ int64_t lbm_step_count(const lbm_handle *h) { return h ? h->step : -1; }
 
 int lbm_configure(lbm_handle *h, int32_t variant, int32_t tile_rows) {
     if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    if (int rc_ = run_pending_obs(h)) return rc_;
     if (variant != LBM_STEP_TMA && variant != LBM_STEP_DIRECT) return fail(LBM_ERR_BADPARAM, "unknown variant");
     if (variant == LBM_STEP_TMA && h->P.precision == LBM_FP16S)
         return fail(LBM_ERR_BADPARAM, "the TMA form needs one storage type for f, h and g (FP64 or FP32)");
@@ -1092,6 +1168,13 @@ int lbm_batch_step(lbm_batch *b, int64_t n) {
     if (n < 0) return fail(LBM_ERR_BADPARAM, "n must be >= 0");
     for (lbm_handle *h : b->m)
         if (h->diverged) return fail(LBM_ERR_DIVERGED, "a member diverged earlier");
+    // a member's deferred observation runs alone, before the batch overwrites
+    // its state (on the member's stream: wait for it if that is another one)
+    for (lbm_handle *h : b->m) {
+        if (!h->obs_pending) continue;
+        if (int rc = run_pending_obs(h)) return rc;
+        if (h->st != b->st) CK(cudaStreamSynchronize(h->st));
+    }
     // A member stepped alone since the list was built has other parities:
     // rebuild the list from the members' current state.
     for (size_t i = 0; i < b->m.size(); i++) {

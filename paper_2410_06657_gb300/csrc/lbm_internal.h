@@ -102,6 +102,10 @@ struct Scalars {           // per-call scalars of the observables reduction
                                     const void *consts /* Consts of the step's type */,       \
                                     const Shift &sh, const ObsScratch &ws, const Scalars &sc,  \
                                     cudaStream_t st);                                          \
+    cudaError_t launch_step_obs_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma, \
+                                         const void *consts, const Shift &sh, int tile_rows,   \
+                                         const ObsScratch &ws, const Scalars &sc,              \
+                                         cudaStream_t st);                                      \
     cudaError_t launch_heat_flux_##SUFFIX(const DevState &s, int cur, int lcur,                \
                                           const void *consts /* Consts of the step's type */, \
                                           const Shift &sh, double *out, cudaStream_t st);      \

@@ -373,11 +373,17 @@ __device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, i
     return io;
 }
 
+// Observation hooks of a step: a plain step observes nothing.  A step that
+// also reduces the observables of the state it starts from passes an
+// observer (lbm_observe.cuh) that keeps the macros it needs from phase 1 and
+// adds every own cell's terms after the cell's push.
+struct NoObs {};
+
 // Halo/own macro evaluation of one cell into shared memory.
-template <typename S, typename T, typename A, int BY>
+template <typename S, typename T, typename A, int BY, typename OB = NoObs>
 __device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Consts<T> &c,
                                              const Shift &sh, TileSmem<T, BY> &sm, int ex, int ey,
-                                             int x, int y) {
+                                             int x, int y, OB *ob = nullptr) {
     const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
     const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
     Refs<T> rf;
@@ -397,6 +403,7 @@ __device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Co
                  T(io.aux_in[AUX_Q * P + k]), c, m);
     sm.q[ey][ex] = {m.psi, m.rho, m.eps, m.phi};
     sm.ps[ey][ex] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
+    if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ey, ex, m);
 }
 
 // The stored values one cell's macros need, in the arithmetic type T.
@@ -516,10 +523,11 @@ __device__ __forceinline__ void fill_ghosts(TileSmem<T, BY> &sm, const Consts<T>
 // supplies the cell's time-n populations (registers or shared memory).
 // EDGE: the tile touches a wall row, so destinations may leave the lattice;
 // interior tiles skip the per-direction wall tests.
-template <typename S, typename T, typename A, int BY, bool EDGE, typename PopSrc>
+template <typename S, typename T, typename A, int BY, bool EDGE, typename PopSrc, typename OB = NoObs>
 __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
                                           const TileSmem<T, BY> &sm, const PopSrc &PS, int tx, int ty, int x,
-                                          int y, const Macro<T> &m, T fs_prev, T pux_prev, T puy_prev) {
+                                          int y, const Macro<T> &m, T fs_prev, T pux_prev, T puy_prev,
+                                          OB *ob = nullptr) {
     const int nx = io.nx, ny = io.ny;
     const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
     const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
@@ -771,16 +779,17 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     io.aux_out[AUX_P * P + k] = A(p);
     io.aux_out[AUX_S * P + k] = A(Sn);
     if (io.write_sigma) io.sigma[k] = A(sig);
+    if constexpr (!std::is_same<OB, NoObs>::value) ob->cell(io, c, sm, tx, ty, x, y, k, m, qv);
 }
 
 
 // ASYNC: the own cell's populations reach the stash by cp.async while the
 // ring cell's loads are in flight (single-instance kernels; the batched
 // kernel's extra live state would spill with it).
-template <typename S, typename T, typename A, int BY, bool ASYNC = false>
+template <typename S, typename T, typename A, int BY, bool ASYNC = false, typename OB = NoObs>
 __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Consts<T> &c,
                                           const Shift &sh, TileSmem<T, BY> &sm, T (*stash)[BY][32], int x0,
-                                          int y0) {
+                                          int y0, OB *ob = nullptr) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
     const int nx = io.nx, ny = io.ny;
@@ -853,12 +862,14 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
             sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
             sm.ps[ty + 1][tx + 1] = {pv, Sv};
+            if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ty + 1, tx + 1, m);
         }
         if (ring) {
             Macro<T> mr;
             local_macros<T>(rl.f, rl.g, rl.l1234, rl.fs_prev, rl.mdot_prev, rl.Q_prev, c, mr);
             sm.q[rey][rex] = {mr.psi, mr.rho, mr.eps, mr.phi};
             sm.ps[rey][rex] = {rp, rS};
+            if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(rey, rex, mr);
         }
         __syncthreads();
     } else {
@@ -898,6 +909,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             for (int i = 0; i < 5; i++) stash[27 + i][ty][tx] = l[i];
             sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
             sm.ps[ty + 1][tx + 1] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
+            if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ty + 1, tx + 1, m);
         }
 
         // ---- phase 1: halo ring, recomputed from the neighbours' populations
@@ -909,7 +921,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             // x0 - 1 + ex lies in [-1, nx + 32]: beyond nx only on a ragged last tile
             int hx = x0 - 1 + ex;
             hx = hx < 0 ? hx + nx : (hx >= nx ? (hx - nx < nx ? hx - nx : (hx - nx) % nx) : hx);
-            cell_to_smem<S, T, A, BY>(io, c, sh, sm, ex, ey, hx, hy);
+            cell_to_smem<S, T, A, BY>(io, c, sh, sm, ex, ey, hx, hy, ob);
         }
         __syncthreads();
     }
@@ -919,9 +931,9 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     if (!own) return;
     const StashPops<T, BY> PS{stash, ty, tx};
     if (y0 == 0 || y0 + BY >= ny)
-        step_cell<S, T, A, BY, true>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev);
+        step_cell<S, T, A, BY, true>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
     else
-        step_cell<S, T, A, BY, false>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev);
+        step_cell<S, T, A, BY, false>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
 }
 
 // Blocks per SM the single-precision step asks the register allocator for:

@@ -174,6 +174,40 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
         k_obs<S, T, A><<<grid, dim3(32, OBS_BY), 0, st>>>(s, cur, lcur, c, sh, ws, sc);                     \
         return cudaGetLastError();                                                                          \
     }                                                                                                       \
+    cudaError_t launch_step_obs_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,             \
+                                         const void *consts, const Shift &sh, int tile_rows,                \
+                                         const ObsScratch &ws, const Scalars &sc, cudaStream_t st) {        \
+        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
+        dim3 grid((s.nx + 31) / 32, (s.ny + tile_rows - 1) / tile_rows);                                   \
+        ObsScratch w = ws;                                                                                  \
+        w.nblocks = (int)(grid.x * grid.y);                                                                 \
+        w.ngroups = (w.nblocks + OBS_GROUP - 1) / OBS_GROUP;                                                \
+        static bool r4 = false, r8 = false, r16 = false;                                                    \
+        cudaError_t e = cudaSuccess;                                                                        \
+        switch (tile_rows) {                                                                                \
+        case 4:                                                                                             \
+            e = allow_dynamic_smem(k_step_obs<S, T, A, 4>, stash_bytes<T, 4>(), r4);                        \
+            if (e == cudaSuccess)                                                                           \
+                k_step_obs<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(s, cur, lcur,        \
+                                                                                    write_sigma, c, sh, w, sc); \
+            break;                                                                                          \
+        case 8:                                                                                             \
+            e = allow_dynamic_smem(k_step_obs<S, T, A, 8>, stash_bytes<T, 8>(), r8);                        \
+            if (e == cudaSuccess)                                                                           \
+                k_step_obs<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(s, cur, lcur,        \
+                                                                                    write_sigma, c, sh, w, sc); \
+            break;                                                                                          \
+        case 16:                                                                                            \
+            e = allow_dynamic_smem(k_step_obs<S, T, A, 16>, stash_bytes<T, 16>(), r16);                     \
+            if (e == cudaSuccess)                                                                           \
+                k_step_obs<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(s, cur, lcur,     \
+                                                                                      write_sigma, c, sh, w, sc); \
+            break;                                                                                          \
+        default: return cudaErrorInvalidValue;                                                              \
+        }                                                                                                   \
+        if (e != cudaSuccess) return e;                                                                     \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
     cudaError_t launch_heat_flux_##SUFFIX(const DevState &s, int cur, int lcur, const void *consts,        \
                                           const Shift &sh, double *out, cudaStream_t st) {                  \
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \

@@ -84,6 +84,7 @@ __device__ __forceinline__ void cell_macros_t(const Planes<S> &pc, const S *lb, 
     local_macros<T>(f, g, l1234, T(aux[AUX_FS * P + k]), T(aux[AUX_MDOT * P + k]), T(aux[AUX_Q * P + k]), c, m);
 }
 
+template <int NT>
 static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc);
 
 // Sum of n values of quantity j at src[i * OBS_NSUM + j] (i < n), by one warp
@@ -104,15 +105,67 @@ static __device__ __forceinline__ double warp_sum_fixed(const double *src, int n
 }
 
 // First level: the last block of group g sums the group's block partials
-// (warp j sums quantity j) and restores the group's counter.
+// (warp w sums quantities w, w + NT/32, ...) and restores the group's counter.
+template <int NT>
 static __device__ __forceinline__ void obs_group(const ObsScratch &ws, int g, int gsize) {
     __shared__ double s_g[OBS_NSUM][32];
     const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp < OBS_NSUM) {
-        const double v = warp_sum_fixed(ws.partials + (long long)g * OBS_GROUP * OBS_NSUM, gsize, warp, s_g[warp]);
-        if (lane == 0) ws.gpartials[(long long)g * OBS_NSUM + warp] = v;
+    for (int j = warp; j < OBS_NSUM; j += NT / 32) {
+        const double v = warp_sum_fixed(ws.partials + (long long)g * OBS_GROUP * OBS_NSUM, gsize, j, s_g[j]);
+        if (lane == 0) ws.gpartials[(long long)g * OBS_NSUM + j] = v;
     }
     if (threadIdx.x == 0 && threadIdx.y == 0) ws.gcount[g] = 0u;
+}
+
+// The end of one block's part of the reduction (NT threads, one warp per
+// lattice row y): row flags, block sums (warp sums in R, warps combined in
+// FP64 in a fixed order) and the two-level finish.  FP64 adds run at a small
+// fraction of the FP32 rate on this part, so they are spread over many SMs:
+// the last block of each group of OBS_GROUP blocks sums its group, the last
+// group to finish sums the groups.  Every sum runs in a fixed order.
+template <int NT, typename R>
+static __device__ __forceinline__ void obs_block_finish(const ObsScratch &ws, const Scalars &sc, const R (&v)[OBS_NSUM],
+                                                        unsigned int rowbits, int y, int nx, int ny) {
+    __shared__ double s_red[OBS_NSUM][NT / 32];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    // row flags: OR across the warp (all lanes share the row), one atomic
+    {
+        unsigned int b = rowbits;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
+        if (tx == 0 && b && y < ny) atomicOr(&ws.rowany[y], b);
+    }
+#pragma unroll
+    for (int j = 0; j < OBS_NSUM; j++) {
+        R t = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (tx == 0) s_red[j][ty] = double(t);
+    }
+    __syncthreads();
+    if (tid < OBS_NSUM) {
+        double t = s_red[tid][0];
+        for (int w = 1; w < NT / 32; w++) t += s_red[tid][w];
+        ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * OBS_NSUM + tid] = t;
+    }
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
+    const int grp = blk / OBS_GROUP, gsize = min(OBS_GROUP, nblk - grp * OBS_GROUP);
+    __shared__ bool s_glast, s_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_glast = atomicAdd(ws.gcount + grp, 1u) == (unsigned int)gsize - 1u;
+    __syncthreads();
+    if (!s_glast) return;
+    __threadfence();
+    obs_group<NT>(ws, grp, gsize);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ws.bad + 2, 1u) == (unsigned int)ws.ngroups - 1u;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        obs_final<NT>(nx, ny, ws, sc);
+    }
 }
 
 template <typename S, typename T, typename A>
@@ -125,7 +178,6 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
     using R = typename std::conditional<sizeof(T) == 8, double, float>::type;
     __shared__ T s_psi[OBS_BY + 2][34], s_fs[OBS_BY + 2][34], s_eps[OBS_BY + 2][34], s_phi[OBS_BY + 2][34];
     __shared__ T s_H[OBS_BY + 2][34], s_Tm[OBS_BY + 2][34];
-    __shared__ double s_red[OBS_NSUM][32 * OBS_BY / 32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int nx = s.nx, ny = s.ny;
     const long long P = s.plane;
@@ -255,50 +307,8 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
             }
         }
     }
-    // row flags: OR across the warp (all lanes share the row), one atomic
-    {
-        unsigned int b = rowbits;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
-        if (tx == 0 && b && y < ny) atomicOr(&ws.rowany[y], b);
-    }
-    // block sums (fixed shuffle order; warps combined in FP64)
-    R v[OBS_NSUM] = {v_psi, v_H, v_fs, v_q, v_liq, v_liqu, v_qdot};
-#pragma unroll
-    for (int j = 0; j < OBS_NSUM; j++) {
-        R t = v[j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (tx == 0) s_red[j][ty] = double(t);
-    }
-    __syncthreads();
-    if (tid < OBS_NSUM) {
-        double t = s_red[tid][0];
-        for (int w = 1; w < OBS_BY; w++) t += s_red[tid][w];
-        ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * OBS_NSUM + tid] = t;
-    }
-    // Two-level finish.  FP64 adds run at a small fraction of the FP32 rate
-    // on this part, so they are spread over many SMs: the last block of each
-    // group of OBS_GROUP blocks sums its group, the last group to finish
-    // sums the groups.  Every sum runs in a fixed order.
-    const int blk = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
-    const int grp = blk / OBS_GROUP, gsize = min(OBS_GROUP, nblk - grp * OBS_GROUP);
-    __shared__ bool s_glast, s_last;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_glast = atomicAdd(ws.gcount + grp, 1u) == (unsigned int)gsize - 1u;
-    __syncthreads();
-    if (!s_glast) return;
-    __threadfence();
-    obs_group(ws, grp, gsize);
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(ws.bad + 2, 1u) == (unsigned int)ws.ngroups - 1u;
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        obs_final(nx, ny, ws, sc);
-    }
+    const R v[OBS_NSUM] = {v_psi, v_H, v_fs, v_q, v_liq, v_liqu, v_qdot};
+    obs_block_finish<32 * OBS_BY, R>(ws, sc, v, rowbits, y, nx, ny);
 }
 
 // psi = 1/2 extent of row y: 0 without liquid, nx without a left or right
@@ -313,34 +323,33 @@ static __device__ __forceinline__ double row_extent_of(const ObsScratch &ws, int
            __longlong_as_double((long long)__ldcg(ws.minv + 1 + y));
 }
 
-// Final reduction, run by the last group to finish (256 threads): the group
-// sums in a fixed order, the widest row, the single values and the result,
-// so nothing depends on which block finishes last.
+// Final reduction, run by the last group to finish (NT >= 128 threads): the
+// group sums in a fixed order, the widest row, the single values and the
+// result, so nothing depends on which block finishes last.
+template <int NT>
 static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc) {
+    static_assert(NT >= 128 && NT % 32 == 0, "four warps at least");
     __shared__ double s_height, s_rtr, s_front;
     __shared__ unsigned int s_bad;
     __shared__ long long s_tfre;
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
-    // the single values, one warp each, while the sums are gathered
-    if (t == 32) s_height = __longlong_as_double((long long)__ldcg(ws.maxv));
-    if (t == 64) s_rtr = 0.5 * row_extent_of(ws, 0, nx);
-    if (t == 96) {
+    // the single values, by the last warp, while the sums are gathered
+    if (t == NT - 32) {
+        s_height = __longlong_as_double((long long)__ldcg(ws.maxv));
         const unsigned long long fmin = __ldcg(ws.minv);
         s_front = __ldcg(ws.bad + 1) ? ((fmin == ~0ull) ? (double)ny : __longlong_as_double((long long)fmin)) : 0.0;
+        s_bad = __ldcg(ws.bad);
+        s_tfre = (long long)__ldcg(&ws.obs->t_fre);
+        s_rtr = 0.5 * row_extent_of(ws, 0, nx);
     }
-    if (t == 128) s_bad = __ldcg(ws.bad);
-    if (t == 160) s_tfre = (long long)__ldcg(&ws.obs->t_fre);
-    // the group sums (warp j sums quantity j over the groups)
+    // the group sums (warp w sums quantities w, w + NT/32, ... over the groups)
     __shared__ double s_fin[OBS_NSUM][32];
-    {
-        const int warp = t >> 5;
-        if (warp < OBS_NSUM) warp_sum_fixed(ws.gpartials, ws.ngroups, warp, s_fin[warp]);
-    }
+    for (int j = t >> 5; j < OBS_NSUM; j += NT / 32) warp_sum_fixed(ws.gpartials, ws.ngroups, j, s_fin[j]);
     // widest row: extents are non-negative doubles, so their bit patterns
     // order like the values and the maximum is an integer one
-    __shared__ unsigned long long s_wb[8];
+    __shared__ unsigned long long s_wb[NT / 32];
     unsigned long long wb = 0ull;
-    for (int y = t; y < ny; y += 256) {
+    for (int y = t; y < ny; y += NT) {
         const unsigned long long e = (unsigned long long)__double_as_longlong(row_extent_of(ws, y, nx));
         wb = e > wb ? e : wb;
     }
@@ -376,7 +385,7 @@ static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratc
         o->Fo = sc.alpha_l * (double)sc.step / (sc.R0 * sc.R0);
     } else if (t == 64) {
         unsigned long long wmax = s_wb[0];
-        for (int w = 1; w < 8; w++) wmax = s_wb[w] > wmax ? s_wb[w] : wmax;
+        for (int w = 1; w < NT / 32; w++) wmax = s_wb[w] > wmax ? s_wb[w] : wmax;
         const double width = __longlong_as_double((long long)wmax), height = s_height;
         o->height = height;
         o->width = width;
@@ -388,9 +397,124 @@ static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratc
     // leave the workspace at the identities of its reductions for the next
     // call (0 for maxima and flags, all ones for minima)
     __syncthreads();
-    for (int i = t; i < ny + 2; i += 256) ws.maxv[i] = 0ull;
-    for (int i = t; i < ny + 1; i += 256) ws.minv[i] = ~0ull;
-    for (int i = t; i < ny + 3; i += 256) ws.rowany[i] = 0u;     // rowany[ny], then bad[0..2]
+    for (int i = t; i < ny + 2; i += NT) ws.maxv[i] = 0ull;
+    for (int i = t; i < ny + 1; i += NT) ws.minv[i] = ~0ull;
+    for (int i = t; i < ny + 3; i += NT) ws.rowany[i] = 0u;     // rowany[ny], then bad[0..2]
+}
+
+// ---------------------------------------------------------------------------
+// Observables fused into a step.  The step from time n to n + 1 reads the
+// state at time n and already evaluates, for its tile and the ring around
+// it, every macro the observables need (and q_v with the same stencils), so
+// an observation of the state at time n can ride on that step instead of
+// reading the lattice once more.  The terms and crossings are k_obs's; the
+// step's 32 x BY tile (one warp per row) replaces k_obs's 32 x 8 one, so the
+// FP64 sums group the same terms differently (rounding only).
+// ---------------------------------------------------------------------------
+template <typename T, int BY>
+struct StepObs {
+    using R = typename std::conditional<sizeof(T) == 8, double, float>::type;
+    T (*fs)[34];                  // f_s of the extended tile (shared memory)
+    T (*Tm)[34];                  // temperature of the extended tile (shared memory)
+    unsigned long long *maxv, *minv;
+    unsigned int *bad;
+    R v[OBS_NSUM];                // psi, H, f_s, q_v, liquid, liquid speed, Qdot of the own cell
+    unsigned int rowbits;         // bit0 liquid, bit1 left crossing, bit2 right crossing
+
+    __device__ __forceinline__ void macro(int ey, int ex, const Macro<T> &m) {
+        fs[ey][ex] = m.fs;
+        Tm[ey][ex] = m.T_;
+    }
+
+    template <typename S, typename A>
+    __device__ __forceinline__ void cell(const StepIO<S, T, A> &io, const Consts<T> &c, const TileSmem<T, BY> &sm,
+                                         int tx, int ty, int x, int y, uint32_t k, const Macro<T> &m, T qv) {
+        const int ex = tx + 1, ey = ty + 1, nx = io.nx, ny = io.ny;
+        const uint32_t P = (uint32_t)io.plane;
+        // substrate heat flux (R24): -k (4 T_1 - T_2 - 3 T_0) / 2 on row 0
+        if (y == 0 && ny >= 3) {
+            const T kth0 = chi(m.fs, m.psi, c.kth);
+            v[6] = R(-kth0 * (T(4) * Tm[2][ex] - Tm[3][ex] - T(3) * Tm[1][ex]) / T(2));
+        }
+        // Peclet number (R25): liquid content psi - f_s weights |psi u| / psi
+        {
+            const T w = m.psi - m.fs;
+            if (w > T(0)) {
+                const T ux = T(io.aux_in[AUX_PUX * P + k]), uy = T(io.aux_in[AUX_PUY * P + k]);
+                const T sp = sqrt(ux * ux + uy * uy);
+                v[4] = R(w);
+                v[5] = R(w * sp / m.psi);
+            }
+        }
+        v[3] = R(qv);
+        v[0] = R(m.psi);
+        v[1] = R(m.H);
+        v[2] = R(m.fs);
+        if (!isfinite(v[0]) || !isfinite(v[1])) atomicOr(bad, 1u);
+        const double a = double(m.psi);
+        // column crossing (height): psi(y) >= 1/2 > psi(y+1)
+        if (a >= 0.5) {
+            rowbits |= 1u;
+            if (y == ny - 1) {
+                atomic_max_pos(&maxv[0], (double)ny);
+            } else {
+                const double b = double(sm.q[ey + 1][ex].psi);
+                if (b < 0.5) atomic_max_pos(&maxv[0], y + (a - 0.5) / (a - b) + 0.5);
+            }
+            // row crossings (width): left edge needs x >= 1, right edge x <= nx - 2
+            if (x >= 1) {
+                const double bl = double(sm.q[ey][ex - 1].psi);
+                if (bl < 0.5) {
+                    atomic_min_pos(&minv[1 + y], (x - 1) + (0.5 - bl) / (a - bl));
+                    rowbits |= 2u;
+                }
+            }
+            if (x + 1 < nx) {
+                const double br = double(sm.q[ey][ex + 1].psi);
+                if (br < 0.5) {
+                    atomic_max_pos(&maxv[2 + y], x + (a - 0.5) / (a - br));
+                    rowbits |= 4u;
+                }
+            }
+        }
+        // freezing front on the centre column (lowest f_s = 1/2 crossing)
+        if (x == nx / 2) {
+            const double fa = double(m.fs);
+            if (y == 0 && fa >= 0.5) atomicOr(bad + 1, 1u);
+            if (fa >= 0.5) {
+                if (y == ny - 1) {
+                    atomic_min_pos(&minv[0], (double)ny);
+                } else {
+                    const double fb = double(fs[ey + 1][ex]);
+                    if (fb < 0.5) atomic_min_pos(&minv[0], y + (fa - 0.5) / (fa - fb) + 0.5);
+                }
+            }
+        }
+    }
+};
+
+// One step (rows a1-a9) that also reduces the observables (row a10) of the
+// state it starts from.  `ws` carries this grid's block and group counts.
+template <typename S, typename T, typename A, int BY>
+__global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
+    k_step_obs(DevState s, int cur, int lcur, int write_sigma, Consts<T> c, Shift sh, ObsScratch ws, Scalars sc) {
+    __shared__ TileSmem<T, BY> sm;
+    __shared__ T s_fs[BY + 2][34], s_Tm[BY + 2][34];
+    extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
+    T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
+    const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
+    sr_advance(s, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
+    StepObs<T, BY> ob;
+    ob.fs = s_fs;
+    ob.Tm = s_Tm;
+    ob.maxv = ws.maxv;
+    ob.minv = ws.minv;
+    ob.bad = ws.bad;
+#pragma unroll
+    for (int j = 0; j < OBS_NSUM; j++) ob.v[j] = typename StepObs<T, BY>::R(0);
+    ob.rowbits = 0u;
+    step_tile<S, T, A, BY, true, StepObs<T, BY>>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY, &ob);
+    obs_block_finish<32 * BY>(ws, sc, ob.v, ob.rowbits, (int)(blockIdx.y * BY + threadIdx.y), s.nx, s.ny);
 }
 
 // Local substrate heat flux (R24), one thread per column, in the step's

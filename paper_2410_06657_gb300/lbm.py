@@ -31,7 +31,7 @@ EXPORTS = [
     "lbm_set_field", "lbm_state_bytes", "lbm_export_state", "lbm_import_state",
     "lbm_step_count", "lbm_configure", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tile_rows", "lbm_batch_destroy", "lbm_observables_noalloc",
-    "lbm_substrate_heat_flux", "lbm_observables_to_host", "lbm_sync",
+    "lbm_substrate_heat_flux", "lbm_observables_to_host", "lbm_sync", "lbm_observables_deferred",
 ]
 
 
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
     L.lbm_observables_fetch.argtypes = [vp, P(Obs)]
     L.lbm_observables_to_host.argtypes = [vp, vp]
     L.lbm_sync.argtypes = [vp]
+    L.lbm_observables_deferred.argtypes = [vp, vp]
     L.lbm_get_field.argtypes = [vp, C.c_int32, P(C.c_double)]
     L.lbm_set_field.argtypes = [vp, C.c_int32, P(C.c_double)]
     L.lbm_state_bytes.restype = C.c_size_t
@@ -229,6 +230,12 @@ class Simulation:
         (an lbm_obs, page-locked for an asynchronous copy); read it with
         `Obs.from_address(addr)` after `sync()`."""
         _check(load().lbm_observables_to_host(self._h, C.c_void_p(addr)))
+
+    def observables_deferred(self, addr: int = 0):
+        """Request the observables of the current state, reduced inside the
+        next step's kernel; fetch with `observables_fetch()`, or pass a host
+        address (an lbm_obs) to receive them there after `sync()`."""
+        _check(load().lbm_observables_deferred(self._h, C.c_void_p(addr) if addr else None))
 
     def sync(self):
         _check(load().lbm_sync(self._h))

@@ -410,6 +410,90 @@ def test_snapshot_resume_is_bitwise(lbm, prec):
         assert np.array_equal(b.get(n), ref[n]), n
 
 
+def _obs_close(got, want, rel):
+    """Observables equal up to the grouping of the FP64 sums: counters,
+    status and the crossing-based lengths exactly, sums to `rel`."""
+    for k, v in want.items():
+        g = got[k]
+        if k in ("mass", "enthalpy", "solid", "charge", "frozen_fraction", "Pe", "Qdot", "Fo_fre", "Fo"):
+            assert abs(g - v) <= rel * max(abs(v), 1e-300) or g == v, (k, g, v)
+        else:
+            assert g == v, (k, g, v)
+
+
+@pytest.mark.parametrize("prec,nx,ny,tile,k_e", [(W.FP64, 37, 19, 8, 1), (W.FP64, 64, 32, 4, 2),
+                                                 (W.FP64, 40, 3, 8, 1), (W.FP32, 128, 64, 4, 1),
+                                                 (W.FP16S, 96, 48, 4, 1), (W.FP32, 100, 45, 16, 1)])
+def test_observation_fused_into_the_next_step(lbm, prec, nx, ny, tile, k_e):
+    """lbm_observables_deferred + lbm_step: the first step's kernel also
+    reduces the observables of the state it reads.  They equal what
+    lbm_observables returns for that state (FP64 sums to 1e-13: the step's
+    tiles group them differently), and the state after the steps equals a
+    plain run's bit for bit, over several observations, across graph
+    replays and with extra potential sweeps."""
+    p = W.params(nx=nx, ny=ny, R0=ny / 3.0 + 1.0, precision=prec, k_e=k_e)
+    xc, yc = W.sessile_center(nx, ny / 3.0 + 1.0, 90.0)
+    a, b = lbm.Simulation(p), lbm.Simulation(p)
+    for s in (a, b):
+        s.configure(lbm.STEP_DIRECT, tile)
+        s.init_droplet(ny / 3.0 + 1.0, xc, yc, 2)
+        s.step(5)
+    rel = 1e-13 if prec == W.FP64 else 1e-6
+    for n in (1, 40, 3):
+        want = b.observables()
+        b.step(n)
+        a.observables_deferred()
+        a.step(n)
+        _obs_close(a.observables_fetch(), want, rel)
+    for name in STORED:
+        assert np.array_equal(a.get(name), b.get(name)), name
+
+
+def test_deferred_observation_runs_before_other_calls(lbm):
+    """A deferred observation that no step takes runs on its own before the
+    next call's work: a field read, a state import, a synchronisation, or
+    the next request; with a host address it lands there."""
+    import ctypes
+    import torch
+    p = W.params(nx=48, ny=24, R0=8.0, precision=W.FP64)
+    xc, yc = W.sessile_center(48, 8.0, 90.0)
+    a = lbm.Simulation(p)
+    a.init_droplet(8.0, xc, yc, 0)
+    a.step(6)
+    want = a.observables()
+    snap = a.export_state()
+    a.observables_deferred()
+    psi = a.get("psi")                       # runs the observation first
+    _obs_close(a.observables_fetch(), want, 1e-15)
+    a.observables_deferred()
+    a.import_state(snap)                     # same state: same observables
+    _obs_close(a.observables_fetch(), want, 1e-15)
+    buf = torch.zeros(2 * ctypes.sizeof(lbm.Obs), dtype=torch.uint8, pin_memory=True)
+    a.observables_deferred(buf.data_ptr())
+    a.observables_deferred(buf.data_ptr() + ctypes.sizeof(lbm.Obs))   # runs the first one
+    a.sync()                                                           # runs the second one
+    for i in range(2):
+        _obs_close(lbm.Obs.from_address(buf.data_ptr() + i * ctypes.sizeof(lbm.Obs)).as_dict(), want, 1e-15)
+    assert np.array_equal(psi, a.get("psi"))
+
+
+def test_deferred_observation_of_a_batch_member(lbm):
+    """A batch step first runs a member's deferred observation on its own:
+    the batch overwrites the state it refers to."""
+    p = W.params(nx=64, ny=32, R0=10.0, precision=W.FP64)
+    xc, yc = W.sessile_center(64, 10.0, 90.0)
+    sims = [lbm.Simulation(p) for _ in range(2)]
+    for s in sims:
+        s.init_droplet(10.0, xc, yc, 0)
+        s.step(3)
+    want = sims[0].observables()
+    sims[0].observables_deferred()
+    b = lbm.Batch(sims, tile_rows=8)
+    b.step(2)
+    _obs_close(sims[0].observables_fetch(), want, 1e-15)
+    assert sims[0].t == 5
+
+
 def test_back_to_back_imports_from_pinned_memory(lbm):
     """Imports are copied on a private stream into two alternating device
     buffers while the handle's stream still steps the previous state: three
