@@ -7,8 +7,8 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
 A step is one pass of the whole hot path over the lattice: the fused
 collide-and-stream launch (local macros, stencils, forces, four collisions,
-streaming with walls) and, every `--obs-every` steps, the FP64 observables
-reduction.  The default workload is the production sessile droplet:
+streaming with walls); every `--obs-every`-th step also reduces the FP64
+observables of the state it starts from inside the same kernel.  The default workload is the production sessile droplet:
 512 x 256 lattice, R = 80, theta = 90, CaE = 0.2, S = 2, R_sigma = 5,
 Ste = 0.5, rho_s/rho_l = 0.9, FP32.  The lattice state (about 45 MB) fits in
 L2, so L2 is flushed (a 256 MB write) before every timed step, outside the
