@@ -16,7 +16,9 @@
  * y = ny - 1/2 (adiabatic, top electrode phi = E0 * ny, neutral wetting).
  *
  * Conventions for every call:
- *   - Returns LBM_OK (0) or a negative LBM_ERR_* code; nothing throws.
+ *   - Returns LBM_OK (0) or a negative LBM_ERR_* code (lbm_presolve may
+ *     also return the positive warning LBM_WARN_NOT_CONVERGED); nothing
+ *     throws.
  *   - The library owns all device memory of a handle; callers own every
  *     host buffer they pass (it is only read or written during the call).
  *   - A handle is bound to one CUDA stream and is not thread-safe.  Calls
@@ -53,7 +55,9 @@ enum {
     LBM_ERR_DIVERGED = -3,   /* a non-finite psi or H was seen; the handle     */
                              /* refuses further steps                          */
     LBM_ERR_CUDA = -4,       /* a CUDA call failed (message: lbm_last_error)   */
-    LBM_ERR_STATE = -5       /* call out of order (e.g. step before init)      */
+    LBM_ERR_STATE = -5,      /* call out of order (e.g. step before init)      */
+    LBM_WARN_NOT_CONVERGED = 1  /* warning, lbm_presolve only: the tolerance  */
+                                /* was not met within max_sweeps              */
 };
 
 /*
@@ -197,6 +201,21 @@ int lbm_init_droplet(struct lbm_handle *h, double R, double xc, double yc, int32
  * call.  Errors: BADPARAM (NULL psi, presolve < 0), CUDA.
  */
 int lbm_init_psi(struct lbm_handle *h, const double *psi, int32_t presolve);
+
+/*
+ * Pre-solve of the potential to a tolerance (Algorithm 1's convergence of
+ * the electric field before the coupled run; reading R15): potential sweeps
+ * with sigma and every other field frozen, until the largest change of phi
+ * over one sweep, relative to |phi_top - phi_bot|, is below tol; measured
+ * every 64 sweeps, at most max_sweeps in all.  *sweeps and *residual (each
+ * may be NULL) receive the sweeps run and the last measured change.  The
+ * same sweeps as lbm_init_*'s `presolve` count: an init with presolve =
+ * *sweeps reaches the same state.  Synchronises the stream.  Returns LBM_OK,
+ * LBM_WARN_NOT_CONVERGED (> 0) when max_sweeps ran out first, or BADPARAM
+ * (NULL handle, tol <= 0, max_sweeps < 1), STATE (before init), DIVERGED
+ * (non-finite potential), CUDA.
+ */
+int lbm_presolve(struct lbm_handle *h, double tol, int32_t max_sweeps, int32_t *sweeps, double *residual);
 
 /*
  * Advance n >= 0 time steps (Algorithm 1 under a Jacobi reading: every

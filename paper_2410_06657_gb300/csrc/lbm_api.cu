@@ -888,6 +888,54 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
     return LBM_OK;
 }
 
+int lbm_presolve(lbm_handle *h, double tol, int32_t max_sweeps, int32_t *sweeps, double *residual) {
+    if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
+    if (!(tol > 0.0) || max_sweeps < 1) return fail(LBM_ERR_BADPARAM, "tol must be > 0 and max_sweeps >= 1");
+    if (!h->inited) return fail(LBM_ERR_STATE, "pre-solve before init");
+    if (int rc_ = run_pending_obs(h)) return rc_;
+    const double dphi = std::fabs(h->cd.phi_top - h->cd.phi_bot);
+    const double scale = dphi > 0.0 ? dphi : 1.0;
+    // the observables workspace's spare maximum slot holds the change
+    unsigned long long *d = h->ws.maxv + 1;
+    const int chunk = 64;        // sweeps between two measurements
+    int done = 0;
+    double res = HUGE_VAL;
+    while (done < max_sweeps) {
+        const int n = std::min(chunk, max_sweeps - done);
+        for (int j = 0; j < n; j++) {
+            cudaError_t e = do_sweep(h, h->st);
+            if (e != cudaSuccess) return cuda_fail(e, "pre-solve sweep");
+        }
+        done += n;
+        // change of phi over the last sweep: copy lcur against copy lcur ^ 1
+        CK(cudaMemsetAsync(d, 0, sizeof *d, h->st));
+        cudaError_t e;
+        switch (h->P.precision) {
+        case LBM_FP64: e = launch_phi_change_f64(h->s, h->lcur, h->lcur ^ 1, &h->cd, h->sh, d, h->st); break;
+        case LBM_FP32: e = launch_phi_change_f32(h->s, h->lcur, h->lcur ^ 1, &h->cd, h->sh, d, h->st); break;
+        default: e = launch_phi_change_f16s(h->s, h->lcur, h->lcur ^ 1, &h->cd, h->sh, d, h->st); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "pre-solve residual");
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, d, sizeof bits, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemsetAsync(d, 0, sizeof *d, h->st));      // the slot's identity again
+        CK(cudaStreamSynchronize(h->st));
+        double change;
+        std::memcpy(&change, &bits, sizeof change);
+        res = change / scale;
+        if (res < tol) break;
+        if (!std::isfinite(res)) {
+            if (sweeps) *sweeps = done;
+            if (residual) *residual = res;
+            return fail(LBM_ERR_DIVERGED, "non-finite potential in the pre-solve");
+        }
+    }
+    if (sweeps) *sweeps = done;
+    if (residual) *residual = res;
+    if (res < tol) return LBM_OK;
+    return fail(LBM_WARN_NOT_CONVERGED, "pre-solve stopped at max_sweeps above the tolerance");
+}
+
 int64_t lbm_step_count(const lbm_handle *h) { return h ? h->step : -1; }
 
 int lbm_configure(lbm_handle *h, int32_t variant, int32_t tile_rows) {

@@ -112,6 +112,10 @@ struct Scalars {           // per-call scalars of the observables reduction
     cudaError_t launch_get_##SUFFIX(const DevState &s, int cur, int lcur, int field,           \
                                     const void *consts, const Shift &sh, double *out,          \
                                     cudaStream_t st);                                          \
+    cudaError_t launch_phi_change_##SUFFIX(const DevState &s, int la, int lb,                  \
+                                           const void *consts /* Consts<double> */,           \
+                                           const Shift &sh, unsigned long long *out,           \
+                                           cudaStream_t st);                                   \
     cudaError_t launch_set_##SUFFIX(const DevState &s, int cur, int lcur, int field,           \
                                     const void *consts, const Shift &sh, const double *in,     \
                                     cudaStream_t st);

@@ -221,6 +221,13 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
         k_get<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, field, c, sh, out);                      \
         return cudaGetLastError();                                                                          \
     }                                                                                                       \
+    cudaError_t launch_phi_change_##SUFFIX(const DevState &s, int la, int lb, const void *consts,         \
+                                           const Shift &sh, unsigned long long *out, cudaStream_t st) {     \
+        const Consts<double> &c = *reinterpret_cast<const Consts<double> *>(consts);                      \
+        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
+        k_phi_change<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, la, lb, c, sh, out);                         \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
     cudaError_t launch_set_##SUFFIX(const DevState &s, int cur, int lcur, int field, const void *consts,   \
                                     const Shift &sh, const double *in, cudaStream_t st) {                   \
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \

@@ -316,11 +316,12 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
 // (Other blocks wrote the workspace with atomics during this launch: read
 // it from L2.)
 static __device__ __forceinline__ double row_extent_of(const ObsScratch &ws, int y, int nx) {
+    // the three loads are independent: one round trip
     const unsigned int bits = __ldcg(ws.rowany + y);
+    const unsigned long long r = __ldcg(ws.maxv + 2 + y), l = __ldcg(ws.minv + 1 + y);
     if (!(bits & 1u)) return 0.0;
     if ((bits & 6u) != 6u) return (double)nx;
-    return __longlong_as_double((long long)__ldcg(ws.maxv + 2 + y)) -
-           __longlong_as_double((long long)__ldcg(ws.minv + 1 + y));
+    return __longlong_as_double((long long)r) - __longlong_as_double((long long)l);
 }
 
 // Final reduction, run by the last group to finish (NT >= 128 threads): the
@@ -575,6 +576,41 @@ __global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c
                : field == LBM_FIELD_PHI ? m.phi
                : m.H;
     }
+}
+
+// Largest change of phi between the potential populations of copy la and
+// copy lb (the two ends of the last sweep), as the bit pattern of a
+// non-negative double: one atomic maximum per warp.
+template <typename S, typename T, typename A>
+__global__ void k_phi_change(DevState s, int la, int lb, Consts<double> c, Shift sh, unsigned long long *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    double d = 0.0;
+    if (x < s.nx && y < s.ny) {
+        const long long P = s.plane, k = (long long)y * s.pitch + x;
+        const S *l0 = Planes<S>::at(la ? s.pop[1] : s.pop[0], P).l;
+        const S *l1 = Planes<S>::at(lb ? s.pop[1] : s.pop[0], P).l;
+        Refs<T> rf;
+        Consts<T> ct;
+        ct.phi_bot = T(c.phi_bot);
+        ct.phi_top = T(c.phi_top);
+        make_refs<S, T>(rf, sh, ct, y, s.ny);
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int i = 1; i < 5; i++) {
+            a += double(Pol<S, T>::ld(l0 + i * P + k, rf.l[i], 1.0f / sh.l_scale));
+            b += double(Pol<S, T>::ld(l1 + i * P + k, rf.l[i], 1.0f / sh.l_scale));
+        }
+        d = fabs(a - b) / (1.0 - w5<double>(0));
+        if (!(d == d)) d = __longlong_as_double(0x7ff0000000000000ll);    // NaN counts as infinite
+    }
+    unsigned long long v = (unsigned long long)__double_as_longlong(d);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
 }
 
 template <typename S, typename T, typename A>

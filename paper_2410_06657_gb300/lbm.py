@@ -16,6 +16,7 @@ from . import build as _build
 FP64, FP32, FP16S = 0, 1, 2
 STEP_TMA, STEP_DIRECT = 0, 1
 OK, ERR_BADPARAM, ERR_OOM, ERR_DIVERGED, ERR_CUDA, ERR_STATE = 0, -1, -2, -3, -4, -5
+WARN_NOT_CONVERGED = 1
 
 FIELD_IDS = {
     "f": 0, "h": 1, "g": 2, "l": 3, "fs_prev": 4, "mdot_prev": 5, "Q_prev": 6,
@@ -32,6 +33,7 @@ EXPORTS = [
     "lbm_step_count", "lbm_configure", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tile_rows", "lbm_batch_destroy", "lbm_observables_noalloc",
     "lbm_substrate_heat_flux", "lbm_observables_to_host", "lbm_sync", "lbm_observables_deferred",
+    "lbm_presolve",
 ]
 
 
@@ -101,6 +103,7 @@ def load(build_if_missing: bool = True):
     L.lbm_observables_to_host.argtypes = [vp, vp]
     L.lbm_sync.argtypes = [vp]
     L.lbm_observables_deferred.argtypes = [vp, vp]
+    L.lbm_presolve.argtypes = [vp, C.c_double, C.c_int32, P(C.c_int32), P(C.c_double)]
     L.lbm_get_field.argtypes = [vp, C.c_int32, P(C.c_double)]
     L.lbm_set_field.argtypes = [vp, C.c_int32, P(C.c_double)]
     L.lbm_state_bytes.restype = C.c_size_t
@@ -230,6 +233,15 @@ class Simulation:
         (an lbm_obs, page-locked for an asynchronous copy); read it with
         `Obs.from_address(addr)` after `sync()`."""
         _check(load().lbm_observables_to_host(self._h, C.c_void_p(addr)))
+
+    def presolve(self, tol: float, max_sweeps: int) -> dict:
+        """Potential sweeps until phi changes by less than tol (relative to
+        the electrode difference) over one sweep; see lbm_presolve."""
+        n, r = C.c_int32(0), C.c_double(0.0)
+        rc = load().lbm_presolve(self._h, float(tol), int(max_sweeps), C.byref(n), C.byref(r))
+        if rc < 0:
+            _check(rc)
+        return {"converged": rc == OK, "sweeps": int(n.value), "residual": float(r.value)}
 
     def observables_deferred(self, addr: int = 0):
         """Request the observables of the current state, reduced inside the

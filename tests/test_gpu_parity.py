@@ -133,6 +133,41 @@ def test_droplet_initialisers_agree(lbm):
     assert_fp64(worst(g, o))
 
 
+def test_presolve_to_a_tolerance(lbm):
+    """lbm_presolve sweeps the potential until phi changes by less than
+    tol x |phi_top - phi_bot| over one sweep (checked every 64 sweeps).  The
+    linear potential of the initial state is already the fixed point of a
+    drop-free lattice; with a droplet, the sweep count it reports reproduces
+    the oracle's fixed-count pre-solve, and a cap below it gives the
+    NOT_CONVERGED warning with the count and residual reached."""
+    p = W.params(nx=32, ny=16, R0=5.0, precision=W.FP64)
+    s = lbm.Simulation(p)
+    s.init_psi(np.zeros((16, 32)), 0)
+    r = s.presolve(1e-12, 10000)
+    assert r["converged"] and r["sweeps"] == 64 and r["residual"] < 1e-12, r
+
+    p = W.params(nx=40, ny=20, R0=7.0, theta_deg=100.0, precision=W.FP64)
+    xc, yc = W.sessile_center(40, 7.0, 100.0)
+    psi0 = W.droplet_psi(40, 20, 7.0, xc, yc, p["W"])
+    g = lbm.Simulation(p)
+    g.init_psi(psi0, 0)
+    r = g.presolve(1e-9, 200000)
+    assert r["converged"] and r["residual"] < 1e-9 and r["sweeps"] % 64 == 0, r
+    ref = oracle.Oracle(p)
+    ref.init_psi(psi0, r["sweeps"])
+    for name in ("l", "phi"):
+        a, b = g.get(name), ref.get(name)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), name
+    h = lbm.Simulation(p)
+    h.init_psi(psi0, 0)
+    w = h.presolve(1e-9, 128)
+    assert not w["converged"] and w["sweeps"] == 128 and w["residual"] >= 1e-9, w
+    f32 = lbm.Simulation(W.params(nx=40, ny=20, R0=7.0, theta_deg=100.0, precision=W.FP32))
+    f32.init_psi(psi0, 0)
+    r32 = f32.presolve(1e-5, 200000)
+    assert r32["converged"] and r32["sweeps"] <= r["sweeps"], r32
+
+
 def test_fp64_matches_oracle_on_the_128x64_case(lbm):
     """The 128 x 64 sessile case (R = 20, theta = 90, CaE = 0.2, S = 2,
     R = 5, Ste = 0.5), 1000 steps; observables agree too."""

@@ -68,6 +68,7 @@ def test_calls_on_null_handles_fail_cleanly():
     assert L.lbm_observables_to_host(None, None) == lbm.ERR_BADPARAM
     assert L.lbm_sync(None) == lbm.ERR_BADPARAM
     assert L.lbm_observables_deferred(None, None) == lbm.ERR_BADPARAM
+    assert L.lbm_presolve(None, 1e-10, 10, None, None) == lbm.ERR_BADPARAM
     assert L.lbm_batch_create(None, 0, None, 0, None) == lbm.ERR_BADPARAM
     L.lbm_destroy(None)
 
