@@ -48,8 +48,11 @@ FALLBACK_HBM_GBS = 6800.0
 NOMINAL_FP64_TFLOPS = 1.25     # FP64 rate of the part (nominal; no measured figure exists)
 
 
-def profile_md(precision: str) -> str:
-    return os.path.join(ROOT, "profiles", f"k_step_{precision}_production_512x256.md")
+PROFILED_LATTICE = {"production": "512x256", "precision": "1024x512"}
+
+
+def profile_md(precision: str, workload: str = "production") -> str:
+    return os.path.join(ROOT, "profiles", f"k_step_{precision}_{workload}_{PROFILED_LATTICE[workload]}.md")
 
 
 def kernel_sources(precision: str):
@@ -77,9 +80,12 @@ def measured_peak():
 def profiled(precision: str, workload: str, key: str):
     """A figure of the committed ncu summary of the step kernel (DRAM bytes
     per launch, FP64 flops per lattice update), if the summary was taken on
-    the current kernel source; summaries cover the production lattice."""
-    path = profile_md(precision)
-    if workload != "production" or not os.path.exists(path):
+    the current kernel source; summaries cover the production and precision
+    lattices."""
+    if workload not in PROFILED_LATTICE:
+        return None
+    path = profile_md(precision, workload)
+    if not os.path.exists(path):
         return None
     text = open(path).read()
     m_b = re.search(key + r":\s*([0-9.eE+]+)", text)
