@@ -18,6 +18,18 @@ namespace lbm {
 // ---------------------------------------------------------------------------
 constexpr int OBS_BY = 8;
 
+// Counter increment with acquire-release semantics at GPU scope.  One
+// thread increments after a block barrier: the release covers every write
+// the block made before the barrier (its partials, its atomics), and the
+// block that draws the last count acquires all of them, then shares them
+// with its other threads through the next barrier; no thread needs a fence
+// of its own.
+static __device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 static __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) {
     atomicMax(a, (unsigned long long)__double_as_longlong(v));   // v >= 0: bits order like values
 }
@@ -151,21 +163,15 @@ static __device__ __forceinline__ void obs_block_finish(const ObsScratch &ws, co
     const int blk = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
     const int grp = blk / OBS_GROUP, gsize = min(OBS_GROUP, nblk - grp * OBS_GROUP);
     __shared__ bool s_glast, s_last;
-    __threadfence();
     __syncthreads();
-    if (tid == 0) s_glast = atomicAdd(ws.gcount + grp, 1u) == (unsigned int)gsize - 1u;
+    if (tid == 0) s_glast = atom_add_acq_rel(ws.gcount + grp, 1u) == (unsigned int)gsize - 1u;
     __syncthreads();
     if (!s_glast) return;
-    __threadfence();
     obs_group<NT>(ws, grp, gsize);
-    __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(ws.bad + 2, 1u) == (unsigned int)ws.ngroups - 1u;
+    if (tid == 0) s_last = atom_add_acq_rel(ws.bad + 2, 1u) == (unsigned int)ws.ngroups - 1u;
     __syncthreads();
-    if (s_last) {
-        __threadfence();
-        obs_final<NT>(nx, ny, ws, sc);
-    }
+    if (s_last) obs_final<NT>(nx, ny, ws, sc);
 }
 
 template <typename S, typename T, typename A>
