@@ -343,8 +343,11 @@ struct StepIO {
     uint32_t sr_step;       // stochastic-rounding step counter (half storage)
 };
 
+// The step's pointers and sizes for the parities (cur, lcur); the host
+// resolves them for the single-instance kernels, so those kernels receive
+// the pointers instead of selecting them per launch.
 template <typename S, typename T, typename A>
-__device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, int lcur, int write_sigma) {
+__host__ __device__ __forceinline__ StepIO<S, T, A> step_io(const DevState &s, int cur, int lcur, int write_sigma) {
     StepIO<S, T, A> io;
     // select rather than index the parameter arrays (a dynamic index would
     // copy them to local memory)
@@ -362,14 +365,27 @@ __device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, i
     io.aux_out = reinterpret_cast<A *>(cur ? s.aux[0] : s.aux[1]);
     io.sigma = reinterpret_cast<A *>(s.sigma);
     io.sr_step = 0u;
-    if constexpr (Pol<S, T>::shifted) {
-        if (s.rng) io.sr_step = s.rng[cur];
-    }
     io.nx = s.nx;
     io.ny = s.ny;
     io.pitch = s.pitch;
     io.write_sigma = write_sigma;
     io.plane = s.plane;
+    return io;
+}
+
+// Half storage: the stochastic-rounding counter of this step lives in device
+// memory (graph replays advance it), so the kernel reads it.
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void load_sr_step(StepIO<S, T, A> &io, const unsigned int *rng, int cur) {
+    if constexpr (Pol<S, T>::shifted) {
+        if (rng) io.sr_step = rng[cur];
+    }
+}
+
+template <typename S, typename T, typename A>
+__device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, int lcur, int write_sigma) {
+    StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);
+    load_sr_step(io, s.rng, cur);
     return io;
 }
 
@@ -959,20 +975,26 @@ inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes, bool &done) {
 // next step (parities flipped) reads rng[cur ^ 1], which no thread of this
 // step reads, so one thread per instance can write it.
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void sr_advance(const DevState &s, int cur, const StepIO<S, T, A> &io, bool leader) {
+__device__ __forceinline__ void sr_advance(unsigned int *rng, int cur, const StepIO<S, T, A> &io, bool leader) {
     if constexpr (Pol<S, T>::shifted) {
-        if (leader && s.rng) s.rng[cur ^ 1] = io.sr_step + 1u;
+        if (leader && rng) rng[cur ^ 1] = io.sr_step + 1u;
     }
 }
+template <typename S, typename T, typename A>
+__device__ __forceinline__ void sr_advance(const DevState &s, int cur, const StepIO<S, T, A> &io, bool leader) {
+    sr_advance(s.rng, cur, io, leader);
+}
 
+// io: step_io() of this launch's parities, resolved on the host; rng, cur:
+// the stochastic-rounding counters and the population parity (half storage).
 template <typename S, typename T, typename A, int BY>
-__global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_step(DevState s, int cur, int lcur,
-                                                                             int write_sigma, Consts<T> c, Shift sh) {
+__global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
+    k_step(StepIO<S, T, A> io, unsigned int *rng, int cur, Consts<T> c, Shift sh) {
     __shared__ TileSmem<T, BY> sm;
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
-    const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
-    sr_advance(s, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
+    load_sr_step(io, rng, cur);
+    sr_advance(rng, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
     step_tile<S, T, A, BY, true>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
 }
 

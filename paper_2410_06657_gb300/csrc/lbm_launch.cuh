@@ -89,23 +89,24 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
                                      const void *consts, const Shift &sh, int tile_rows, cudaStream_t st) { \
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
         dim3 grid((s.nx + 31) / 32, (s.ny + tile_rows - 1) / tile_rows);                                   \
+        const StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);                             \
         static bool r4 = false, r8 = false, r16 = false;                                                    \
         cudaError_t e = cudaSuccess;                                                                        \
         switch (tile_rows) {                                                                                \
         case 4:                                                                                             \
             e = allow_dynamic_smem(k_step<S, T, A, 4>, stash_bytes<T, 4>(), r4);                            \
             if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
+                k_step<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(io, s.rng, cur, c, sh); \
             break;                                                                                          \
         case 8:                                                                                             \
             e = allow_dynamic_smem(k_step<S, T, A, 8>, stash_bytes<T, 8>(), r8);                            \
             if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
+                k_step<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(io, s.rng, cur, c, sh); \
             break;                                                                                          \
         case 16:                                                                                            \
             e = allow_dynamic_smem(k_step<S, T, A, 16>, stash_bytes<T, 16>(), r16);                         \
             if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(s, cur, lcur, write_sigma, c, sh); \
+                k_step<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(io, s.rng, cur, c, sh); \
             break;                                                                                          \
         default: return cudaErrorInvalidValue;                                                              \
         }                                                                                                   \
@@ -179,6 +180,7 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
                                          const ObsScratch &ws, const Scalars &sc, cudaStream_t st) {        \
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
         dim3 grid((s.nx + 31) / 32, (s.ny + tile_rows - 1) / tile_rows);                                   \
+        const StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);                             \
         ObsScratch w = ws;                                                                                  \
         w.nblocks = (int)(grid.x * grid.y);                                                                 \
         w.ngroups = (w.nblocks + OBS_GROUP - 1) / OBS_GROUP;                                                \
@@ -188,20 +190,20 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
         case 4:                                                                                             \
             e = allow_dynamic_smem(k_step_obs<S, T, A, 4>, stash_bytes<T, 4>(), r4);                        \
             if (e == cudaSuccess)                                                                           \
-                k_step_obs<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(s, cur, lcur,        \
-                                                                                    write_sigma, c, sh, w, sc); \
+                k_step_obs<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(                     \
+                    io, s.rng, cur, c, sh, w, sc);                                                          \
             break;                                                                                          \
         case 8:                                                                                             \
             e = allow_dynamic_smem(k_step_obs<S, T, A, 8>, stash_bytes<T, 8>(), r8);                        \
             if (e == cudaSuccess)                                                                           \
-                k_step_obs<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(s, cur, lcur,        \
-                                                                                    write_sigma, c, sh, w, sc); \
+                k_step_obs<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(                     \
+                    io, s.rng, cur, c, sh, w, sc);                                                          \
             break;                                                                                          \
         case 16:                                                                                            \
             e = allow_dynamic_smem(k_step_obs<S, T, A, 16>, stash_bytes<T, 16>(), r16);                     \
             if (e == cudaSuccess)                                                                           \
-                k_step_obs<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(s, cur, lcur,     \
-                                                                                      write_sigma, c, sh, w, sc); \
+                k_step_obs<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(                  \
+                    io, s.rng, cur, c, sh, w, sc);                                                          \
             break;                                                                                          \
         default: return cudaErrorInvalidValue;                                                              \
         }                                                                                                   \

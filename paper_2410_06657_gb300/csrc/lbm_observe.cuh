@@ -501,16 +501,17 @@ struct StepObs {
 };
 
 // One step (rows a1-a9) that also reduces the observables (row a10) of the
-// state it starts from.  `ws` carries this grid's block and group counts.
+// state it starts from.  io, rng, cur as for k_step; `ws` carries this
+// grid's block and group counts.
 template <typename S, typename T, typename A, int BY>
 __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
-    k_step_obs(DevState s, int cur, int lcur, int write_sigma, Consts<T> c, Shift sh, ObsScratch ws, Scalars sc) {
+    k_step_obs(StepIO<S, T, A> io, unsigned int *rng, int cur, Consts<T> c, Shift sh, ObsScratch ws, Scalars sc) {
     __shared__ TileSmem<T, BY> sm;
     __shared__ T s_fs[BY + 2][34], s_Tm[BY + 2][34];
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
-    const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
-    sr_advance(s, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
+    load_sr_step(io, rng, cur);
+    sr_advance(rng, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
     StepObs<T, BY> ob;
     ob.fs = s_fs;
     ob.Tm = s_Tm;
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
     for (int j = 0; j < OBS_NSUM; j++) ob.v[j] = typename StepObs<T, BY>::R(0);
     ob.rowbits = 0u;
     step_tile<S, T, A, BY, true, StepObs<T, BY>>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY, &ob);
-    obs_block_finish<32 * BY>(ws, sc, ob.v, ob.rowbits, (int)(blockIdx.y * BY + threadIdx.y), s.nx, s.ny);
+    obs_block_finish<32 * BY>(ws, sc, ob.v, ob.rowbits, (int)(blockIdx.y * BY + threadIdx.y), io.nx, io.ny);
 }
 
 // Local substrate heat flux (R24), one thread per column, in the step's
