@@ -245,9 +245,9 @@ int lbm_observables_async(struct lbm_handle *h);
 int lbm_observables_fetch(struct lbm_handle *h, lbm_obs *out);
 
 /*
- * Streaming observables: enqueue the reduction and the copy of its result
- * into the caller's host memory *out on the handle's stream, and return
- * without waiting.  With *out in page-locked memory the copy is
+ * Streaming observables: enqueue the reduction of lbm_observables (Secs.
+ * 4-5) and the copy of its result into the caller's host memory *out on the
+ * handle's stream, and return without waiting.  With *out in page-locked memory the copy is
  * asynchronous, so a loop of steps and observations runs without a host
  * round trip per step; *out holds the values once lbm_sync has returned and
  * must stay valid until then (pageable memory works too, the copy then
@@ -259,7 +259,8 @@ int lbm_observables_to_host(struct lbm_handle *h, lbm_obs *out);
 
 /*
  * Observation fused into the next step: request the observables of the
- * current state without a pass of their own over the lattice.  The next
+ * current state (those of lbm_observables, Secs. 4-5) without a pass of
+ * their own over the lattice.  The next
  * lbm_step reduces them inside its first step's kernel, which reads exactly
  * this state (rows a1-a3 already evaluate every macro and stencil they
  * need); any other call on the handle first runs them on their own, as
