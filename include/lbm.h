@@ -20,10 +20,15 @@
  *     also return the positive warning LBM_WARN_NOT_CONVERGED); nothing
  *     throws.
  *   - The library owns all device memory of a handle; callers own every
- *     host buffer they pass (it is only read or written during the call).
- *   - A handle is bound to one CUDA stream and is not thread-safe.  Calls
- *     that only enqueue work (lbm_step) return before the GPU finishes;
- *     calls that return data to the host synchronise that stream.
+ *     host buffer they pass.  It is only read or written during the call,
+ *     except by the asynchronous transfers of lbm_import_state,
+ *     lbm_observables_to_host and lbm_observables_deferred, which use it
+ *     until the handle's stream has passed them (lbm_sync).
+ *   - A handle is bound to one CUDA stream and to the device that was
+ *     current at lbm_create (make it current for every call on the handle),
+ *     and is not thread-safe.  Calls that only enqueue work (lbm_step)
+ *     return before the GPU finishes; calls that return data to the host
+ *     synchronise that stream.
  *   - All arithmetic runs in the library's CUDA kernels; there is no CPU
  *     path.  A call made without a usable GPU returns LBM_ERR_CUDA.
  */
