@@ -286,6 +286,34 @@ def test_fp64_full_size_production_lattice(lbm):
     assert_fp64(worst(g, o))
 
 
+def test_fp64_full_size_precision_lattice(lbm):
+    """1024 x 512, R = 160, theta = 60, PR+ field (the largest lattice the
+    benchmark times), in its launch configuration: every field of every cell
+    after 2 steps against the oracle."""
+    w = W.precision_case(W.FP64)
+    p = w["params"]
+    g, o = pair(lbm, p, w["R"])
+    g.step(2)
+    o.step(2)
+    assert_fp64(worst(g, o))
+
+
+def test_fp32_full_size_precision_lattice_observables(lbm):
+    """1024 x 512 FP32 in the benchmark's launch configuration against the
+    FP64 oracle after 5 steps: conserved sums to 1e-5 relative, interface
+    geometry to 1e-3 lattice units."""
+    w = W.precision_case(W.FP32)
+    p = w["params"]
+    g, o = pair(lbm, p, w["R"])
+    g.step(5)
+    o.step(5)
+    og, oo = g.observables(), o.observables()
+    for k in ("mass", "enthalpy"):
+        assert abs(og[k] / oo[k] - 1) < 1e-5, k
+    for k in ("height", "width", "R_tr"):
+        assert abs(og[k] - oo[k]) < 1e-3, k
+
+
 @pytest.mark.parametrize("nx,ny", [(4, 3), (37, 19), (64, 32), (100, 45)])
 def test_tma_and_direct_step_kernels_agree_bitwise(lbm, nx, ny):
     """The tensor-load step (halo'd tile brought into shared memory, wrap
