@@ -478,6 +478,7 @@ def run_batched(args, world, rank, local):
     t_batch = reduce_max(t_batch, world)
     v_batch = world * cells * K / t_batch / 1e6
     v_plain = cells * K / t_plain / 1e6
+    state_gb = sum(s.state_bytes() for s in sims) / 1e9
     if rank == 0:
         print(json.dumps({
             "metric": "MLUPS", "value": v_batch, "unit": "MLUPS", "n_gpus": world, "steps": K,
@@ -485,7 +486,8 @@ def run_batched(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": "batched: 64 instances, sizes uniform in {128x64 .. 512x256}, seeded "
                                    "CaE/R/S/theta/Ste draws", "cells": cells,
-                       "tile_rows": batch.tile_rows, "l2": "state (1.2 GB in FP32) larger than L2"},
+                       "tile_rows": batch.tile_rows,
+                       "l2": f"state ({state_gb:.2f} GB a copy, two copies resident) larger than L2"},
             "plain_one_after_another": {"value": v_plain, "unit": "MLUPS"},
             "batched_over_plain": v_batch / v_plain,
             "gpu_launches": K * (1 if items[0]["params"]["k_e"] == 1 else items[0]["params"]["k_e"]),
