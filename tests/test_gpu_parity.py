@@ -648,7 +648,7 @@ def test_fp32_fields_track_the_oracle_over_a_short_horizon(lbm):
     update give ~1e-6 per step; bar 1e-4 (normwise, natural-scale floors)
     on every stored field.  Over long horizons the scheme's sensitivity near
     the wall on the droplet axis grows last-bit differences, so long FP32
-    runs are judged on observables (next tests)."""
+    runs are assessed on observables (next tests)."""
     w = W.plain_fp64_small()
     p = dict(w["params"], precision=W.FP32)
     g, o = pair(lbm, p, w["R"])
