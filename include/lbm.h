@@ -215,7 +215,11 @@ int lbm_init_psi(struct lbm_handle *h, const double *psi, int32_t presolve);
  * every 64 sweeps, at most max_sweeps in all.  *sweeps and *residual (each
  * may be NULL) receive the sweeps run and the last measured change.  The
  * same sweeps as lbm_init_*'s `presolve` count: an init with presolve =
- * *sweeps reaches the same state.  Synchronises the stream.  Returns LBM_OK,
+ * *sweeps reaches the same state.  In half storage the sweeps round
+ * stochastically, which leaves a per-sweep change of a few 1e-4 of the
+ * electrode difference: tighter tolerances end at max_sweeps with the
+ * warning (the field itself settles to about 2e-4 of that difference).
+ * Synchronises the stream.  Returns LBM_OK,
  * LBM_WARN_NOT_CONVERGED (> 0) when max_sweeps ran out first, or BADPARAM
  * (NULL handle, tol <= 0, max_sweeps < 1), STATE (before init), DIVERGED
  * (non-finite potential), CUDA.

@@ -207,6 +207,7 @@ struct lbm_handle {
     cudaStream_t imp_st = nullptr;
     cudaEvent_t imp_filled[2] = {nullptr, nullptr}, imp_free[2] = {nullptr, nullptr};
     int imp_next = 0;
+    uint32_t presolve_sweeps = 0;    // pre-solve sweeps run so far (rounding streams)
     // an observation requested and not yet run: the next lbm_step runs it
     // inside its first step's kernel (the state it reads is the one
     // observed); any other call runs it first on its own
@@ -340,11 +341,14 @@ cudaError_t do_step(lbm_handle *h, cudaStream_t st, const Scalars *observe = nul
     if (e != cudaSuccess) return e;
     h->cur ^= 1;
     h->lcur ^= 1;
+    // the extra sweeps round with the next step's counter, on streams 4, 5, ...
+    // (the step itself uses 0-3)
     for (int j = 1; j < h->P.k_e; j++) {
+        const uint32_t sys = 3u + (uint32_t)j;
         switch (h->P.precision) {
-        case LBM_FP64: e = launch_sweep_f64(h->s, h->lcur, c, h->sh, st); break;
-        case LBM_FP32: e = launch_sweep_f32(h->s, h->lcur, c, h->sh, st); break;
-        default: e = launch_sweep_f16s(h->s, h->lcur, c, h->sh, st); break;
+        case LBM_FP64: e = launch_sweep_f64(h->s, h->lcur, h->cur, sys, c, h->sh, st); break;
+        case LBM_FP32: e = launch_sweep_f32(h->s, h->lcur, h->cur, sys, c, h->sh, st); break;
+        default: e = launch_sweep_f16s(h->s, h->lcur, h->cur, sys, c, h->sh, st); break;
         }
         if (e != cudaSuccess) return e;
         h->lcur ^= 1;
@@ -352,13 +356,17 @@ cudaError_t do_step(lbm_handle *h, cudaStream_t st, const Scalars *observe = nul
     return cudaSuccess;
 }
 
+// A pre-solve sweep: its rounding stream (half storage) is the handle's
+// running count of pre-solve sweeps with the top bit set, apart from the
+// streams of the steps.
 cudaError_t do_sweep(lbm_handle *h, cudaStream_t st) {
     const void *c = consts_for(h);
+    const uint32_t sys = 0x80000000u | (h->presolve_sweeps++ & 0x7fffffffu);
     cudaError_t e;
     switch (h->P.precision) {
-    case LBM_FP64: e = launch_sweep_f64(h->s, h->lcur, c, h->sh, st); break;
-    case LBM_FP32: e = launch_sweep_f32(h->s, h->lcur, c, h->sh, st); break;
-    default: e = launch_sweep_f16s(h->s, h->lcur, c, h->sh, st); break;
+    case LBM_FP64: e = launch_sweep_f64(h->s, h->lcur, h->cur, sys, c, h->sh, st); break;
+    case LBM_FP32: e = launch_sweep_f32(h->s, h->lcur, h->cur, sys, c, h->sh, st); break;
+    default: e = launch_sweep_f16s(h->s, h->lcur, h->cur, sys, c, h->sh, st); break;
     }
     if (e == cudaSuccess) h->lcur ^= 1;
     return e;
@@ -982,16 +990,20 @@ static cudaError_t list_steps(const lbm_batch *b, const WorkList &L, int64_t n, 
         flips++;
         lflips++;
         for (int sw = 1; sw < b->k_e; sw++) {
-            const int fl2 = lflips & 1;
+            const int fl2 = lflips & 1, fc2 = flips & 1;
+            const uint32_t sys = 3u + (uint32_t)sw;   // as the single-instance sweeps
             switch (b->precision) {
             case LBM_FP64:
-                e = launch_batch_sweep_f64(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2, st);
+                e = launch_batch_sweep_f64(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2, fc2,
+                                           sys, st);
                 break;
             case LBM_FP32:
-                e = launch_batch_sweep_f32(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2, st);
+                e = launch_batch_sweep_f32(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2, fc2,
+                                           sys, st);
                 break;
             default:
-                e = launch_batch_sweep_f16s(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2, st);
+                e = launch_batch_sweep_f16s(L.items_dev, L.consts_dev, L.n, L.total_sweep_tiles, L.sweep_grid, fl2,
+                                            fc2, sys, st);
                 break;
             }
             if (e != cudaSuccess) return e;

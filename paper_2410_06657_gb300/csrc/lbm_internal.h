@@ -93,8 +93,8 @@ struct Scalars {           // per-call scalars of the observables reduction
                                          const void *consts, const Shift &sh, const TmaMaps &m,\
                                          cudaStream_t st);                                     \
     size_t tma_smem_##SUFFIX(int tile_rows);                                                   \
-    cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, const void *consts,         \
-                                      const Shift &sh, cudaStream_t st);                       \
+    cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, int cur, uint32_t sr_sys,   \
+                                      const void *consts, const Shift &sh, cudaStream_t st);  \
     cudaError_t launch_init_##SUFFIX(const DevState &s, const double *psi_dev, double R,       \
                                      double xc, double yc, const void *consts,                 \
                                      const Shift &sh, cudaStream_t st);                        \
@@ -146,7 +146,7 @@ struct BatchItem {
                                            cudaStream_t st);                                       \
     cudaError_t launch_batch_sweep_##SUFFIX(const BatchItem *items_dev, const void *consts_dev,    \
                                             int n_items, int total_tiles, int grid, int flip_l,    \
-                                            cudaStream_t st);
+                                            int flip_cur, uint32_t sr_sys, cudaStream_t st);
 LBM_DECLARE_BATCH(f64)
 LBM_DECLARE_BATCH(f32)
 LBM_DECLARE_BATCH(f16s)

@@ -1261,8 +1261,13 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_batch_ste
 template <typename S, typename T, typename A>
 __device__ __forceinline__ void sweep_cell(const S *l_in, S *l_out, const A *sigma, int nx, int ny,
                                            int pitch, long long P, const Consts<T> &c, const Shift &sh,
-                                           int x, int y) {
+                                           int x, int y, uint32_t sr_step, uint32_t sr_sys) {
     const long long k = (long long)y * pitch + x;
+    // half storage rounds stochastically here too: rounding to nearest would
+    // stall the relaxation once a sweep changes phi by less than half a
+    // spacing (sr_sys keeps every sweep's bits apart from the step's)
+    uint32_t rb[4] = {0u, 0u, 0u, 0u};
+    if constexpr (Pol<S, T>::shifted) sr_block(rb, k, sr_step, sr_sys);
     Refs<T> rf, ro;
     make_refs<S, T>(rf, sh, c, y, ny);
     const float lsc = 1.0f / sh.l_scale;
@@ -1282,31 +1287,36 @@ __device__ __forceinline__ void sweep_cell(const S *l_in, S *l_out, const A *sig
         if (yt < 0 || yt >= ny) {
             const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
             if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-            Pol<S, T>::st(l_out + OPP5[i] * P + k, -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]], sh.l_scale);
+            Pol<S, T>::st_sr(l_out + OPP5[i] * P + k, -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]], sh.l_scale,
+                             bits13(rb, i));
         } else {
             if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-            Pol<S, T>::st(l_out + i * P + (long long)yt * pitch + wrapx<T>(x + CX5[i], nx), post, ro.l[i],
-                          sh.l_scale);
+            Pol<S, T>::st_sr(l_out + i * P + (long long)yt * pitch + wrapx<T>(x + CX5[i], nx), post, ro.l[i],
+                             sh.l_scale, bits13(rb, i));
         }
     }
 }
 
+// cur: the population parity, whose rounding counter (half storage) the
+// sweep reads; sr_sys: this sweep's rounding stream.
 template <typename S, typename T, typename A>
-__global__ void k_sweep(DevState s, int lcur, Consts<T> c, Shift sh) {
+__global__ void k_sweep(DevState s, int lcur, int cur, uint32_t sr_sys, Consts<T> c, Shift sh) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= s.nx || y >= s.ny) return;
     const S *l_in = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], s.plane).l;
     S *l_out = Planes<S>::at(lcur ? s.pop[0] : s.pop[1], s.plane).l;
+    const uint32_t sr_step = (Pol<S, T>::shifted && s.rng) ? s.rng[cur] : 0u;
     sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(s.sigma), s.nx, s.ny, s.pitch, s.plane, c,
-                        sh, x, y);
+                        sh, x, y, sr_step, sr_sys);
 }
 
 // Batched potential sweep over the same work list (32 x 8 cells per tile).
 template <typename S, typename T, typename A>
 __global__ void __launch_bounds__(256) k_batch_sweep(const BatchItem *__restrict__ items,
                                                      const Consts<T> *__restrict__ consts, int n_items,
-                                                     int total_tiles, int flip_l) {
+                                                     int total_tiles, int flip_l, int flip_cur,
+                                                     uint32_t sr_sys) {
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
         const int ii = find_item<true>(items, n_items, t);
         const BatchItem &it = items[ii];
@@ -1317,8 +1327,9 @@ __global__ void __launch_bounds__(256) k_batch_sweep(const BatchItem *__restrict
             const int lc = it.lcur ^ flip_l;
             const S *l_in = Planes<S>::at(lc ? it.s.pop[1] : it.s.pop[0], it.s.plane).l;
             S *l_out = Planes<S>::at(lc ? it.s.pop[0] : it.s.pop[1], it.s.plane).l;
+            const uint32_t sr_step = (Pol<S, T>::shifted && it.s.rng) ? it.s.rng[it.cur ^ flip_cur] : 0u;
             sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(it.s.sigma), it.s.nx, it.s.ny,
-                                it.s.pitch, it.s.plane, consts[ii], it.sh, x, y);
+                                it.s.pitch, it.s.plane, consts[ii], it.sh, x, y, sr_step, sr_sys);
         }
     }
 }

@@ -56,9 +56,9 @@ cudaError_t launch_batch_step_t(const BatchItem *items, const void *consts, cons
 
 template <typename S, typename T, typename A>
 cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int n_items, int total_tiles, int grid,
-                                 int flip_l, cudaStream_t st) {
+                                 int flip_l, int flip_cur, uint32_t sr_sys, cudaStream_t st) {
     const Consts<T> *c = reinterpret_cast<const Consts<T> *>(consts);
-    k_batch_sweep<S, T, A><<<grid, dim3(32, 8), 0, st>>>(items, c, n_items, total_tiles, flip_l);
+    k_batch_sweep<S, T, A><<<grid, dim3(32, 8), 0, st>>>(items, c, n_items, total_tiles, flip_l, flip_cur, sr_sys);
     return cudaGetLastError();
 }
 
@@ -75,8 +75,10 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
                                             grid, flip_cur, flip_l, st);                                   \
     }                                                                                                       \
     cudaError_t launch_batch_sweep_##SUFFIX(const BatchItem *items_dev, const void *consts_dev, int n_items,\
-                                            int total_tiles, int grid, int flip_l, cudaStream_t st) {       \
-        return launch_batch_sweep_t<S, T, A>(items_dev, consts_dev, n_items, total_tiles, grid, flip_l, st);\
+                                            int total_tiles, int grid, int flip_l, int flip_cur,            \
+                                            uint32_t sr_sys, cudaStream_t st) {                             \
+        return launch_batch_sweep_t<S, T, A>(items_dev, consts_dev, n_items, total_tiles, grid, flip_l,     \
+                                             flip_cur, sr_sys, st);                                         \
     }                                                                                                       \
     }
 
@@ -153,11 +155,11 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
         default: return cudaErrorInvalidValue;                                                              \
         }                                                                                                   \
     }                                                                                                       \
-    cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, const void *consts, const Shift &sh,    \
-                                      cudaStream_t st) {                                                    \
+    cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, int cur, uint32_t sr_sys,               \
+                                      const void *consts, const Shift &sh, cudaStream_t st) {               \
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
         dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
-        k_sweep<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, lcur, c, sh);                                     \
+        k_sweep<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, lcur, cur, sr_sys, c, sh);                        \
         return cudaGetLastError();                                                                          \
     }                                                                                                       \
     cudaError_t launch_init_##SUFFIX(const DevState &s, const double *psi_dev, double R, double xc,        \

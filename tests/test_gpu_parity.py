@@ -166,6 +166,15 @@ def test_presolve_to_a_tolerance(lbm):
     f32.init_psi(psi0, 0)
     r32 = f32.presolve(1e-5, 200000)
     assert r32["converged"] and r32["sweeps"] <= r["sweeps"], r32
+    # half storage: the sweeps round stochastically (to nearest they stalled
+    # 1.2e-2 of the range short of the solution), so phi reaches the FP64
+    # solution to 2e-4 of the range, while the rounding noise keeps the
+    # per-sweep change near 4e-4: a tighter tolerance ends with the warning
+    f16 = lbm.Simulation(W.params(nx=40, ny=20, R0=7.0, theta_deg=100.0, precision=W.FP16S))
+    f16.init_psi(psi0, 0)
+    r16 = f16.presolve(1e-7, 20000)
+    assert not r16["converged"] and r16["sweeps"] == 20000 and r16["residual"] > 1e-5, r16
+    assert np.abs(f16.get("phi") - g.get("phi")).max() <= 1e-3 * np.abs(g.get("phi")).max()
 
 
 def test_fp64_matches_oracle_on_the_128x64_case(lbm):
@@ -382,7 +391,7 @@ def test_streamed_observables_equal_synchronous_ones(lbm):
 # Batched form: same bits as stepping alone
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec,tile", [(W.FP64, 0), (W.FP32, 8), (W.FP32, 0)])
+@pytest.mark.parametrize("prec,tile", [(W.FP64, 0), (W.FP32, 8), (W.FP32, 0), (W.FP16S, 4)])
 def test_batch_equals_members_stepped_alone(lbm, prec, tile):
     """Uneven members, a member that starts at the other parity.  FP64
     results are bitwise those of stepping alone whatever the tile shape and
@@ -391,7 +400,10 @@ def test_batch_equals_members_stepped_alone(lbm, prec, tile):
     single-instance kernel may still round differently; the
     accuracy bar for single precision is on observables, so after 300
     steps the observables must agree to 1e-4 and the fields to 1e-3 (max
-    norm with natural-scale floors)."""
+    norm with natural-scale floors).  Half storage uses the same rounding
+    bits in both forms, but a last-bit difference before rounding moves a
+    stored value by a whole half spacing: its bar is the observables, to
+    1e-3."""
     cases = [(96, 48, 15.0, 80.0, 0.1, 2.0, 5.0), (64, 32, 10.0, 110.0, 0.4, 0.5, 2.0),
              (37, 21, 6.0, 95.0, 0.0, 5.0, 9.5)]
     sims, alone = [], []
@@ -419,12 +431,13 @@ def test_batch_equals_members_stepped_alone(lbm, prec, tile):
         for name in STORED:
             if prec == W.FP64:
                 assert np.array_equal(s.get(name), a.get(name)), name
-            else:
+            elif prec == W.FP32:
                 assert normwise(s.get(name), a.get(name), fl.get(name, 0.0)) <= 1e-3, name
         if prec != W.FP64:
+            tol = 1e-4 if prec == W.FP32 else 1e-3
             os_, oa = s.observables(), a.observables()
             for k in ("mass", "enthalpy", "frozen_fraction", "height", "width", "aspect"):
-                assert abs(os_[k] - oa[k]) <= 1e-4 * max(abs(oa[k]), 1.0), k
+                assert abs(os_[k] - oa[k]) <= tol * max(abs(oa[k]), 1.0), k
 
 
 def test_batch_in_l2_groups_equals_members_stepped_alone(lbm):
