@@ -856,17 +856,26 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
         hd.precision != h->P.precision || hd.k_e != h->P.k_e)
         return fail(LBM_ERR_BADPARAM, "snapshot does not match this handle");
     if (!h->imp_st) {
-        if (cudaMalloc(&h->imp_buf[0], bytes) != cudaSuccess || cudaMalloc(&h->imp_buf[1], bytes) != cudaSuccess) {
+        // buffers, events and the copy stream, all or none
+        bool ok = cudaMalloc(&h->imp_buf[0], bytes) == cudaSuccess && cudaMalloc(&h->imp_buf[1], bytes) == cudaSuccess;
+        const bool oom = !ok;
+        for (int j = 0; j < 2 && ok; j++)
+            ok = cudaEventCreateWithFlags(&h->imp_filled[j], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->imp_free[j], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&h->imp_st, cudaStreamNonBlocking) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
-            cudaFree(h->imp_buf[0]);
-            h->imp_buf[0] = h->imp_buf[1] = nullptr;
-            return fail(LBM_ERR_OOM, "device allocation of the import buffers failed");
+            for (int j = 0; j < 2; j++) {
+                if (h->imp_filled[j]) cudaEventDestroy(h->imp_filled[j]);
+                if (h->imp_free[j]) cudaEventDestroy(h->imp_free[j]);
+                cudaFree(h->imp_buf[j]);
+                h->imp_filled[j] = h->imp_free[j] = nullptr;
+                h->imp_buf[j] = nullptr;
+            }
+            h->imp_st = nullptr;
+            return oom ? fail(LBM_ERR_OOM, "device allocation of the import buffers failed")
+                       : fail(LBM_ERR_CUDA, "events or stream of the import path could not be created");
         }
-        for (int j = 0; j < 2; j++) {
-            CK(cudaEventCreateWithFlags(&h->imp_filled[j], cudaEventDisableTiming));
-            CK(cudaEventCreateWithFlags(&h->imp_free[j], cudaEventDisableTiming));
-        }
-        CK(cudaStreamCreateWithFlags(&h->imp_st, cudaStreamNonBlocking));
     }
     // the whole snapshot to device buffer j on the import stream, once the
     // handle's stream has unpacked what buffer j held before (an event never
