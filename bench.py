@@ -7,22 +7,29 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
 A step is one pass of the whole hot path over the lattice: the fused
 collide-and-stream launch (local macros, stencils, forces, four collisions,
-streaming with walls); every `--obs-every`-th step also reduces the FP64
-observables of the state it starts from inside the same kernel.  The default workload is the production sessile droplet:
-512 x 256 lattice, R = 80, theta = 90, CaE = 0.2, S = 2, R_sigma = 5,
-Ste = 0.5, rho_s/rho_l = 0.9, FP32.  The lattice state (about 45 MB) fits in
-L2, so L2 is flushed (a 256 MB write) before every timed step, outside the
-timed events.  Under torchrun each rank advances its own instance (replicas,
-no collective on the data path) and the slowest rank's time counts.
+in-place streaming with walls); every `--obs-every`-th step also reduces the
+observables of the state it starts from inside the same kernel.  The default
+workload is the precision case, the largest single-instance configuration:
+1024 x 512 lattice, R = 160, theta = 60, PR+ (R_sigma = 2, S = 0.5),
+CaE = 0.2, Ste = 0.5, rho_s/rho_l = 0.9, FP32.  L2 is flushed (a 256 MB
+write) before every timed step, outside the timed events.  Under torchrun
+each rank advances its own instance (replicas, no collective on the data
+path) and the slowest rank's time counts.
 
-Other workloads: `precision` (1024 x 512, R = 160, theta = 60, PR+);
-`batched` (64 uneven instances in one launch per step, against the same
-instances stepped one after another); `serving` (Poisson arrivals run to
-frozen fraction 0.99 under an HBM budget: p50/p99 time to result);
-`regimes` (the production droplet to freezing with the field off, prolate
-and oblate; --with-oracle adds the oracle on the 4x-coarsened lattice).
-The roofline object is the HBM one for FP32 and FP16S and the FP64
-arithmetic one for FP64, whose step is bound by the FP64 pipe.
+With N = 1 the line also carries, measured after the headline's timed
+region: `production_fp32` (512 x 256), `plain_fp64` (the 128 x 64 and
+512 x 256 cases in FP64), `fp16s` (the precision case in weight-shifted half
+storage), `batched` (64 uneven instances, one launch per step, against the
+same instances stepped one after another) and `serving` (a reduced Poisson
+stream run to frozen fraction 0.99 under an HBM budget: p50/p99 time to
+result); --no-extras leaves them out.
+
+Other workloads (--workload): `production`, `plain` (128 x 64 FP64),
+`batched`, `serving`, `regimes` (the production droplet to freezing with the
+field off, prolate and oblate; --with-oracle adds the oracle on the
+4x-coarsened lattice).  The roofline object is the HBM one for FP32 and
+FP16S and the FP64 arithmetic one for FP64, whose step is bound by the FP64
+pipe.
 
 --impl reference times the FP64 CPU oracle on the same workload and metric.
 """
@@ -48,7 +55,7 @@ FALLBACK_HBM_GBS = 6800.0
 NOMINAL_FP64_TFLOPS = 1.25     # FP64 rate of the part (nominal; no measured figure exists)
 
 
-PROFILED_LATTICE = {"production": "512x256", "precision": "1024x512"}
+PROFILED_LATTICE = {"production": "512x256", "precision": "1024x512", "plain": "128x64"}
 
 
 def profile_md(precision: str, workload: str = "production") -> str:
@@ -152,10 +159,23 @@ def workload(name: str, precision: str):
         label = "production sessile droplet 512x256, R=80, theta=90, CaE=0.2, S=2, R_sigma=5, Ste=0.5"
     elif name == "precision":
         w = W.precision_case(precision=prec)
-        label = "precision case 1024x512, R=160, theta=60, PR+ (R_sigma=2, S=0.5), CaE=0.2"
+        label = "precision case 1024x512, R=160, theta=60, PR+ (R_sigma=2, S=0.5), CaE=0.2, Ste=0.5"
+    elif name == "plain":
+        w = W.plain_fp64_small()
+        w["params"] = dict(w["params"], precision=prec)
+        label = "plain sessile droplet 128x64, R=20, theta=90, CaE=0.2, S=2, R_sigma=5, Ste=0.5"
     else:
         raise SystemExit(f"unknown workload {name}")
     return w, label
+
+
+def config_for(args, p: dict, label: str, world: int) -> dict:
+    """The workload description both arms print (identical keys and values)."""
+    return {"workload": label, "cells": p["nx"] * p["ny"], "precision": args.precision, "k_e": p["k_e"],
+            "obs_every": args.obs_every, "observation": "fused into the step that reads the observed state",
+            "streaming": "in place (AA pattern), one population copy",
+            "l2": "flushed (256 MB write) before every timed step",
+            "parallelism": f"replicas x{world}"}
 
 
 def dist_setup():
@@ -243,7 +263,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": label},
+        "data": "synthetic", "config": config_for(args, dict(w["params"]), label, world),
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} FP64 oracle steps on the {sample}, 1 thread"},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -387,11 +407,8 @@ def run_gpu(args, world, rank, local):
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": label, "cells": cells, "precision": args.precision, "k_e": p["k_e"],
-                   "obs_every": obs_every, "observation": "fused into the step that reads the observed state",
-                   "observing_step_us": 1e3 * statistics.mean(obs_step_ms) if obs_step_ms else None,
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{world}"},
+        "config": config_for(args, p, label, world),
+        "observing_step_us": 1e3 * statistics.mean(obs_step_ms) if obs_step_ms else None,
         "roofline": roofline_f64(args, cells, launch_us, traffic) if args.precision == "f64" else {
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -411,7 +428,12 @@ def run_gpu(args, world, rank, local):
         "steady_state": {"value": ss_mlups, "unit": "MLUPS",
                          "note": f"lbm_step({n_ss}) graph replay, state resident in L2 (informational)"},
         "observables": {k: obs[k] for k in ("step", "mass", "frozen_fraction", "height", "width", "status")},
+        "state_bytes_device": sim.device_bytes(),
     }
+    sim.close()
+    del flush
+    if world == 1 and not args.no_extras:
+        line.update(extras(args))
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -432,6 +454,143 @@ def roofline_f64(args, cells, launch_us, traffic):
     return {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
             "frac": tflops / NOMINAL_FP64_TFLOPS, "traffic": traffic, "peak_kind": "nominal",
             "kernel": "k_step<f64>", "launch_us": launch_us, "fp64_flops_per_lu": flops_lu}
+
+
+# ---------------------------------------------------------------------------
+# The other configurations, measured after the headline's timed region
+# ---------------------------------------------------------------------------
+
+def step_rate(name: str, precision: str, steps: int, warmup: int = 3):
+    """MLUPS and the step kernel's roofline on one workload: `steps` timed
+    steps, each bracketed by two events with L2 flushed before it."""
+    import torch
+    from paper_2410_06657_gb300 import lbm, workloads as W
+    w, label = workload(name, precision)
+    p = dict(w["params"])
+    cells = p["nx"] * p["ny"]
+    stream = torch.cuda.current_stream()
+    sim = lbm.Simulation(p, stream)
+    xc, yc = W.sessile_center(p["nx"], w["R"], p["theta_deg"])
+    sim.init_droplet(w["R"], xc, yc, 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        sim.step(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        flush.fill_(1.0)
+        a.record(stream)
+        sim.step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    launch_us = 1e3 * statistics.mean(ms)
+    o = sim.observables()
+    out = {"workload": label, "precision": precision, "cells": cells, "steps": steps,
+           "value": cells / (launch_us * 1e-6) / 1e6, "unit": "MLUPS", "launch_us": launch_us,
+           "state_bytes_device": sim.device_bytes(), "status": o["status"]}
+    if precision == "f64":
+        out["roofline"] = roofline_f64(argparse.Namespace(workload=name), cells, launch_us,
+                                       profiled("f64", name, "traffic_bytes_per_launch"))
+    else:
+        peak, kind = measured_peak()
+        gbs = BYTES_PER_LU[precision] * cells / (launch_us * 1e-6) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                           "peak_kind": kind, "bytes_per_lu": BYTES_PER_LU[precision],
+                           "traffic": profiled(precision, name, "traffic_bytes_per_launch")}
+    sim.close()
+    return out
+
+
+def extras(args):
+    out = {}
+    t0 = time.perf_counter()
+    out["production_fp32"] = step_rate("production", "f32", 50)
+    out["plain_fp64"] = {"128x64": step_rate("plain", "f64", 50), "512x256": step_rate("production", "f64", 20)}
+    out["fp16s"] = step_rate("precision", "f16s", 20)
+    out["batched"] = batched_rate("f32", steps=64, warmup=32)
+    out["serving"] = serving_rate("f32", requests=args.extra_requests, max_ny=128, budget_gb=80.0)
+    out["extras_wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def batched_rate(precision: str, steps: int, warmup: int, rank: int = 0):
+    """64 uneven instances (C4): one launch per step for all of them against
+    the same instances advanced one after another (each replaying its own
+    graph of 32 steps), both on the members' own data."""
+    import torch
+    from paper_2410_06657_gb300 import lbm, workloads as W
+    stream = torch.cuda.current_stream()
+    prec = W.PRECISIONS[precision]
+    items = W.batched(n=64, seed=2410066570 + rank, precision=prec)
+    sims = []
+    for it in items:
+        p = it["params"]
+        s = lbm.Simulation(p, stream)
+        xc, yc = W.sessile_center(p["nx"], it["R"], p["theta_deg"])
+        s.init_droplet(it["R"], xc, yc, 0)
+        sims.append(s)
+    cells = sum(it["params"]["nx"] * it["params"]["ny"] for it in items)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    for s in sims:
+        s.step(warmup)
+    t_plain = timed(lambda: [s.step(steps) for s in sims])
+    batch = lbm.Batch(sims, stream, tile_rows=0)
+    batch.step(warmup)
+    t_batch = timed(lambda: batch.step(steps))
+    v_batch, v_plain = cells * steps / t_batch / 1e6, cells * steps / t_plain / 1e6
+    state = sum(s.device_bytes() for s in sims)
+    tile_rows = batch.tile_rows
+    batch.close()
+    for s in sims:
+        s.close()
+    return {"workload": "64 instances, sizes uniform in {128x64 .. 512x256}, seeded CaE/R/S/theta/Ste draws",
+            "precision": precision, "cells": cells, "steps": steps, "value": v_batch, "unit": "MLUPS",
+            "plain_one_after_another": v_plain, "batched_over_plain": v_batch / v_plain, "tile_rows": tile_rows,
+            "hbm_gbs_algorithmic": BYTES_PER_LU[precision] * cells * steps / t_batch / 1e9,
+            "state_bytes_device": state}
+
+
+def serving_rate(precision: str, requests: int, max_ny: int, budget_gb: float, rank: int = 0):
+    """A Poisson stream (C5's arrival rate and parameter draws, a stated
+    number of requests and largest lattice) served to frozen fraction 0.99."""
+    import numpy as np
+    import torch
+    from paper_2410_06657_gb300 import workloads as W
+    from paper_2410_06657_gb300.serving import Request, Server
+    stream = torch.cuda.current_stream()
+    prec = W.PRECISIONS[precision]
+    items = W.serving_stream(n=requests, rate=20.0, seed=2410066571 + rank, max_ny=max_ny, precision=prec)
+    reqs = []
+    for it in items:
+        p = it["params"]
+        xc, yc = W.sessile_center(p["nx"], it["R"], p["theta_deg"])
+        reqs.append(Request(id=it["id"], arrival=it["arrival"], params=p, R=it["R"], xc=xc, yc=yc))
+    srv = Server(int(budget_gb * 1e9), stream, chunk=200)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    lat = np.array([r.latency for r in res])
+    lu = srv.lattice_updates
+    return {"workload": f"{requests} Poisson arrivals at 20/s (seed 2410066571), sizes up to {2 * max_ny}x{max_ny}, "
+                        f"C4 parameter draws, each run to frozen fraction 0.99", "precision": precision,
+            "budget_gb": budget_gb, "chunk": 200, "value": lu / wall / 1e6, "unit": "MLUPS",
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "hbm_gbs_algorithmic": lu * BYTES_PER_LU[precision] / wall / 1e9,
+            "gpu_busy_fraction": srv.gpu_busy_s / wall if wall > 0 else None,
+            "all_frozen": bool(all(r.frozen for r in res)), "wall_s": wall}
 
 
 # ---------------------------------------------------------------------------
@@ -617,8 +776,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16s"])
-    ap.add_argument("--workload", default="production",
-                    choices=["production", "precision", "batched", "serving", "regimes"])
+    ap.add_argument("--workload", default="precision",
+                    choices=["precision", "production", "plain", "batched", "serving", "regimes"])
+    ap.add_argument("--no-extras", action="store_true", help="headline line only")
+    ap.add_argument("--extra-requests", type=int, default=48, help="requests of the serving extra")
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--max-ny", type=int, default=128)
     ap.add_argument("--budget-gb", type=float, default=80.0)

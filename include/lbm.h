@@ -117,7 +117,10 @@ typedef struct lbm_params {
  * Observables of one instance (row a10).  The paper measures these from
  * its fields but gives no discrete definition; the library's are:
  *   mass = sum psi, enthalpy = sum H, solid = sum f_s, charge = sum q_v with
- *   q_v = div(eps E) by the product rule (all FP64 reductions);
+ *   q_v = div(eps E) by the product rule.  The per-cell terms are evaluated
+ *   in the handle's arithmetic precision; the 32 cells of one tile row are
+ *   summed in that precision (FP32 for LBM_FP32 and LBM_FP16S), and every
+ *   level above -- rows, tiles, groups of tiles, the lattice -- in FP64;
  *   frozen_fraction = solid / mass;
  *   height = highest interpolated psi = 1/2 crossing of any column,
  *            measured from the wall at y = -1/2;
@@ -175,11 +178,15 @@ const char *lbm_last_error(void);
 
 /*
  * Create an instance.  Validates `p` (see lbm_params), derives the lattice
- * constants of Secs. 2-3, and allocates the device state: two copies of the
+ * constants of Secs. 2-3, and allocates the device state: ONE copy of the
  * 32 populations per cell (f 9, h 9, g 9, l 5) in the precision's storage
- * type and two copies of 7 per-cell auxiliary fields (previous-step f_s,
- * mdot, rho C_p T mdot, psi u_x, psi u_y, p, S), plus sigma and a small
- * reduction workspace.  `stream` is a cudaStream_t (NULL: the legacy
+ * type, streamed in place (AA pattern: the layout alternates between steps),
+ * two copies of 7 per-cell auxiliary fields (previous-step f_s, mdot,
+ * rho C_p T mdot, psi u_x, psi u_y, p, S), sigma, a record of four macros
+ * and f_s per cell in the arithmetic type (published by the tile edges for
+ * their neighbours' halos), one flag per 32 x 4 tile and a small reduction
+ * workspace: about 208 bytes per cell in FP32, 162 in LBM_FP16S, 416 in
+ * FP64.  `stream` is a cudaStream_t (NULL: the legacy
  * default stream); all work of the handle is enqueued there.
  * On success *out owns the memory until lbm_destroy.
  * Errors: BADPARAM, OOM, CUDA.
@@ -229,8 +236,8 @@ int lbm_presolve(struct lbm_handle *h, double tol, int32_t max_sweeps, int32_t *
 /*
  * Advance n >= 0 time steps (Algorithm 1 under a Jacobi reading: every
  * system collides with time-n fields, then all stream, then the walls act).
- * Each step is one fused kernel launch over the lattice plus k_e - 1
- * potential-only sweeps (sigma frozen at time n).  Enqueues asynchronously
+ * Each step is one fused kernel launch over the lattice, streaming in place,
+ * plus k_e - 1 potential-only sweeps (sigma frozen at time n).  Enqueues asynchronously
  * on the handle's stream (long runs replay a captured CUDA graph).
  * Errors: STATE (not initialised), DIVERGED (an earlier observables call
  * saw non-finite values), BADPARAM (n < 0), CUDA.
@@ -238,8 +245,8 @@ int lbm_presolve(struct lbm_handle *h, double tol, int32_t max_sweeps, int32_t *
 int lbm_step(struct lbm_handle *h, int64_t n);
 
 /*
- * Observables at the current time (see lbm_obs), reduced on the GPU in
- * FP64 and copied to *out.  Synchronises the stream.  Updates t_fre.
+ * Observables at the current time (see lbm_obs), reduced on the GPU (FP64
+ * above the first, 32-cell level) and copied to *out.  Synchronises the stream.  Updates t_fre.
  * Returns LBM_ERR_DIVERGED (and sets out->status) if a non-finite psi or H
  * was found.  Errors: BADPARAM (NULL out), STATE, CUDA.
  */
@@ -278,7 +285,7 @@ int lbm_observables_to_host(struct lbm_handle *h, lbm_obs *out);
  * copy) that receives it behind that kernel, as lbm_observables_to_host.
  * Same values as lbm_observables at this step, up to the grouping of the
  * FP64 sums (the step's tiles are 32 x tile_rows, the observables kernel's
- * 32 x 8).  With the TMA step form the reduction runs at once.
+ * 32 x 8).
  * Errors: BADPARAM (NULL handle), STATE, CUDA.
  */
 int lbm_observables_deferred(struct lbm_handle *h, lbm_obs *out);
@@ -307,7 +314,9 @@ int lbm_set_field(struct lbm_handle *h, int32_t field, const double *host_in);
 /*
  * Whole-state snapshot for checkpoint/resume and host hand-over: the step
  * counter, the stochastic-rounding counter, t_fre and every stored array in
- * the handle's storage precision.
+ * the handle's storage precision, populations always in the natural layout
+ * (population i of cell (x, y) in plane i at (x, y), whatever the layout
+ * phase of the in-place streaming; export converts on the host).
  * lbm_state_bytes gives the size; export copies device -> host (synchronous),
  * import copies host -> device and is ordered on the handle's stream: the
  * whole snapshot goes into one of two device buffers on a private copy
@@ -327,16 +336,13 @@ int lbm_import_state(struct lbm_handle *h, const void *host, size_t bytes);
 /*
  * Step kernel selection (tuning and testing; results do not depend on it in
  * FP64, and differ only by rounding in FP32):
- *   variant LBM_STEP_DIRECT (default): every thread loads its cell from
- *     global memory and stashes it in shared memory for the collisions;
- *   variant LBM_STEP_TMA: tensor-memory-accelerator loads bring each tile
- *     with its halo into shared memory (FP64 and FP32 only: the boxes
- *     assume one storage type for f, h and g).
+ *   variant LBM_STEP_DIRECT (the one variant): every thread loads its cell
+ *     from global memory and stashes it in shared memory for the collisions;
  *   tile_rows: 4, 8 or 16 lattice rows per 32-column tile (default 4 in
  *     single precision, 8 in FP64).
- * Errors: BADPARAM (unknown variant or height, TMA with LBM_FP16S, NULL).
+ * Errors: BADPARAM (unknown variant or height, NULL).
  */
-enum { LBM_STEP_TMA = 0, LBM_STEP_DIRECT = 1 };
+enum { LBM_STEP_DIRECT = 1 };
 int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
 
 /*
@@ -349,7 +355,8 @@ int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
  * fixed-size array that the library keeps in device memory on every GPU
  * that loads it (about 1.3 MB, held until the process exits).
  *   p     parameters of the state (host struct, read during the call)
- *   pop   device array of 32 planes, f 0-8 then h 0-8, g 0-8, l 0-4, each
+ *   pop   device array of 32 planes, f 0-8 then h 0-8, g 0-8, l 0-4, in the
+ *         natural layout (population i of cell (x, y) in plane i), each
  *         ny rows of `pitch` elements, x fastest: all in double for
  *         LBM_FP64, all in float for LBM_FP32; for LBM_FP16S the 9 f planes
  *         in float followed by the 23 others in half -- for example the body
@@ -363,13 +370,17 @@ int lbm_configure(struct lbm_handle *h, int32_t variant, int32_t tile_rows);
  *   stream cudaStream_t on which the work is enqueued (the call returns
  *         without waiting; synchronise before reading out)
  * Limits: ny <= 4096 and at most 20480 tiles of 32 x 8 cells (about 5.2
- * million cells); larger lattices return LBM_ERR_BADPARAM.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call shares the one array and clears what must start at zero, so calls
- * whose work overlaps on the GPU (several streams at once) race; serialise
- * them.  Errors: BADPARAM (NULL pointers, invalid parameters, size limits),
- * CUDA (launch failure).
+ * million cells); larger lattices return LBM_ERR_BADPARAM.  pop and aux
+ * must be aligned to their element size (8 bytes for LBM_FP64, 4 otherwise)
+ * and out to 8 bytes, else LBM_ERR_BADPARAM.
+ * A call looks up the array's device address on the current device (a
+ * device reset moves it); a call made while `stream` is being captured uses
+ * the address of the last lookup on that device instead, so make one call
+ * before any stream capture (a capture before it returns LBM_ERR_CUDA).
+ * Every call shares the one array and clears what must start at zero, so
+ * calls whose work overlaps on the GPU (several streams at once) race;
+ * serialise them.  Errors: BADPARAM (NULL pointers, invalid parameters,
+ * size limits, misaligned pointers), CUDA (lookup or launch failure).
  */
 int lbm_observables_noalloc(const lbm_params *p, const void *pop, const void *aux, int32_t pitch,
                             int64_t step, lbm_obs *out, void *stream);
@@ -387,6 +398,12 @@ int lbm_substrate_heat_flux(struct lbm_handle *h, double *host_out);
 
 /* Steps taken since the last init.  */
 int64_t lbm_step_count(const struct lbm_handle *h);
+
+/* Device memory the handle holds, in bytes: the state allocated by
+ * lbm_create (see there) and the reduction workspace, plus the field
+ * staging buffer and the two import buffers once a call has allocated them.
+ * 0 for NULL. */
+size_t lbm_device_bytes(const struct lbm_handle *h);
 
 /* Free the device state.  NULL is ignored. */
 void lbm_destroy(struct lbm_handle *h);

@@ -89,31 +89,53 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = build()
-        L = C.CDLL(path)
-        P = C.POINTER
-        L.orc_create.restype = C.c_void_p
-        L.orc_create.argtypes = [P(OrcParams)]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        L.orc_derive.argtypes = [P(OrcParams), P(OrcDerived)]
-        L.orc_get_derived.argtypes = [C.c_void_p, P(OrcDerived)]
-        L.orc_step.argtypes = [C.c_void_p, C.c_int64]
-        L.orc_get_step.restype = C.c_int64
-        L.orc_get_step.argtypes = [C.c_void_p]
-        L.orc_init_droplet.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int32]
-        L.orc_init_psi.argtypes = [C.c_void_p, P(C.c_double), C.c_int32]
-        L.orc_get_field.argtypes = [C.c_void_p, C.c_int32, P(C.c_double)]
-        L.orc_set_field.argtypes = [C.c_void_p, C.c_int32, P(C.c_double)]
-        L.orc_observables.argtypes = [C.c_void_p, P(OrcObs)]
-        L.orc_heat_flux.argtypes = [C.c_void_p, P(C.c_double)]
-        L.orc_lattice.argtypes = [P(C.c_int32), P(C.c_int32), P(C.c_double)]
-        L.orc_enthalpy_inversion.argtypes = [C.c_double] * 5 + [P(C.c_double), P(C.c_double)]
-        L.orc_stencils.argtypes = [C.c_int32, C.c_int32, P(C.c_double), C.c_int32, C.c_double,
-                                   C.c_double, C.c_double, P(C.c_double), P(C.c_double),
-                                   P(C.c_double)]
-        L.orc_pointwise.argtypes = [C.c_double] * 23 + [P(C.c_double)] * 6
-        _lib = L
+        _lib = _load(build())
     return _lib
+
+
+def build_variant(source: str, out_dir: str, tag: str):
+    """Compile another oracle source text (a copy with one change, for the
+    mutation tests of the pins) the way build() compiles the oracle, and
+    load it.  Returns the library to pass as Oracle(..., lib=...)."""
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, f"lbm_oracle_{tag}.c")
+    with open(src, "w") as fh:
+        fh.write(source)
+    so = os.path.join(out_dir, f"liblbm_oracle_{tag}.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", so,
+                    src, "-lm"], check=True)
+    return _load(so)
+
+
+def source() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def _load(path):
+    L = C.CDLL(path)
+    P = C.POINTER
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [P(OrcParams)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_derive.argtypes = [P(OrcParams), P(OrcDerived)]
+    L.orc_get_derived.argtypes = [C.c_void_p, P(OrcDerived)]
+    L.orc_step.argtypes = [C.c_void_p, C.c_int64]
+    L.orc_get_step.restype = C.c_int64
+    L.orc_get_step.argtypes = [C.c_void_p]
+    L.orc_init_droplet.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int32]
+    L.orc_init_psi.argtypes = [C.c_void_p, P(C.c_double), C.c_int32]
+    L.orc_get_field.argtypes = [C.c_void_p, C.c_int32, P(C.c_double)]
+    L.orc_set_field.argtypes = [C.c_void_p, C.c_int32, P(C.c_double)]
+    L.orc_observables.argtypes = [C.c_void_p, P(OrcObs)]
+    L.orc_heat_flux.argtypes = [C.c_void_p, P(C.c_double)]
+    L.orc_lattice.argtypes = [P(C.c_int32), P(C.c_int32), P(C.c_double)]
+    L.orc_enthalpy_inversion.argtypes = [C.c_double] * 5 + [P(C.c_double), P(C.c_double)]
+    L.orc_stencils.argtypes = [C.c_int32, C.c_int32, P(C.c_double), C.c_int32, C.c_double,
+                               C.c_double, C.c_double, P(C.c_double), P(C.c_double),
+                               P(C.c_double)]
+    L.orc_pointwise.argtypes = [C.c_double] * 23 + [P(C.c_double)] * 6
+    return L
 
 
 def _dp(a: np.ndarray):
@@ -145,17 +167,18 @@ def derive(p: dict) -> dict:
 class Oracle:
     """One simulation instance on the CPU (FP64)."""
 
-    def __init__(self, params: dict):
+    def __init__(self, params: dict, lib=None):
         self.params = dict(params)
         self._p = make_params(params)
-        self._h = lib().orc_create(C.byref(self._p))
+        self._L = lib if lib is not None else globals()["lib"]()
+        self._h = self._L.orc_create(C.byref(self._p))
         if not self._h:
             raise ValueError("oracle: invalid parameters")
         self.nx, self.ny = int(params["nx"]), int(params["ny"])
 
     def close(self):
         if self._h:
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -165,23 +188,23 @@ class Oracle:
             pass
 
     def init_droplet(self, R, xc, yc, presolve=0):
-        lib().orc_init_droplet(self._h, float(R), float(xc), float(yc), int(presolve))
+        self._L.orc_init_droplet(self._h, float(R), float(xc), float(yc), int(presolve))
 
     def init_psi(self, psi, presolve=0):
         a = np.ascontiguousarray(psi, dtype=np.float64).reshape(self.ny, self.nx)
-        lib().orc_init_psi(self._h, _dp(a), int(presolve))
+        self._L.orc_init_psi(self._h, _dp(a), int(presolve))
 
     def step(self, n=1):
-        lib().orc_step(self._h, int(n))
+        self._L.orc_step(self._h, int(n))
 
     @property
     def t(self):
-        return int(lib().orc_get_step(self._h))
+        return int(self._L.orc_get_step(self._h))
 
     def get(self, name: str) -> np.ndarray:
         planes = FIELD_PLANES.get(name, 1)
         out = np.empty((planes, self.ny, self.nx), dtype=np.float64)
-        rc = lib().orc_get_field(self._h, FIELD_IDS[name], _dp(out))
+        rc = self._L.orc_get_field(self._h, FIELD_IDS[name], _dp(out))
         if rc != 0:
             raise KeyError(name)
         return out if planes > 1 else out[0]
@@ -189,25 +212,25 @@ class Oracle:
     def set(self, name: str, values: np.ndarray):
         planes = FIELD_PLANES.get(name, 1)
         a = np.ascontiguousarray(values, dtype=np.float64).reshape(planes, self.ny, self.nx)
-        rc = lib().orc_set_field(self._h, FIELD_IDS[name], _dp(a))
+        rc = self._L.orc_set_field(self._h, FIELD_IDS[name], _dp(a))
         if rc != 0:
             raise KeyError(name)
 
     def derived(self) -> dict:
         d = OrcDerived()
-        lib().orc_get_derived(self._h, C.byref(d))
+        self._L.orc_get_derived(self._h, C.byref(d))
         return {n: (list(getattr(d, n)) if not isinstance(getattr(d, n), float) else getattr(d, n))
                 for n, _ in OrcDerived._fields_}
 
     def observables(self) -> dict:
         o = OrcObs()
-        lib().orc_observables(self._h, C.byref(o))
+        self._L.orc_observables(self._h, C.byref(o))
         return o.as_dict()
 
     def heat_flux(self) -> np.ndarray:
         """Local substrate heat flux per column (Sec. 4.3, reading R24)."""
         out = np.zeros(self.nx)
-        if lib().orc_heat_flux(self._h, _dp(out)) != 0:
+        if self._L.orc_heat_flux(self._h, _dp(out)) != 0:
             raise ValueError("oracle: heat flux needs ny >= 3")
         return out
 

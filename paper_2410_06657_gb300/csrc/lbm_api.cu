@@ -1,8 +1,6 @@
 // Host side of the C ABI declared in include/lbm.h: parameter validation,
 // derived lattice constants, device memory, stepping (with CUDA-graph
 // replay of long runs), observables, field access, snapshots and batches.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,6 +48,40 @@ size_t f_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
 size_t pop_cell_bytes(int precision) { return 9 * f_bytes(precision) + (NPOP - 9) * storage_bytes(precision); }
 size_t l_offset_bytes(int precision, long long plane) {
     return (size_t)plane * (9 * f_bytes(precision) + 18 * storage_bytes(precision));
+}
+// Published edge macros per cell: a (psi, rho, eps, phi) record and f_s, in
+// the arithmetic type.
+size_t pub_rec_bytes(int precision) { return precision == LBM_FP64 ? 32 : 16; }
+size_t arith_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+// Step tiles of the tallest grid (4-row tiles): one publication flag each.
+size_t flag_count(int nx, int ny) { return (size_t)((nx + 31) / 32) * (size_t)((ny + 3) / 4); }
+
+// D2Q9 and D2Q5 velocity sets (Secs. 3.1, 3.4) for the host-side layout
+// conversion of snapshots.
+const int HCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, HCY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+const int HOPP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+const int HCX5[5] = {0, 1, 0, -1, 0}, HCY5[5] = {0, 0, 1, 0, -1}, HOPP5[5] = {0, 3, 4, 1, 2};
+
+// Rewrite nq planes of elements of `es` bytes, held in the swapped layout of
+// the in-place streaming (population i of cell x in plane opp(i) at x - c_i,
+// or in plane i at x where x - c_i lies beyond a wall), into the natural one
+// (population i of cell x in plane i at x).
+void unswap_planes(char *buf, size_t es, int nq, int nx, int ny, int pitch, long long plane) {
+    const int *cx = nq == 9 ? HCX : HCX5, *cy = nq == 9 ? HCY : HCY5, *op = nq == 9 ? HOPP9 : HOPP5;
+    std::vector<char> raw(buf, buf + (size_t)nq * plane * es);
+    for (int i = 0; i < nq; i++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                const int yu = y - cy[i];
+                int q = i, sy = y, sx = x;
+                if (yu >= 0 && yu < ny && (cx[i] != 0 || cy[i] != 0)) {
+                    q = op[i];
+                    sy = yu;
+                    sx = ((x - cx[i]) % nx + nx) % nx;
+                }
+                std::memcpy(buf + ((size_t)i * plane + (size_t)y * pitch + x) * es,
+                            raw.data() + ((size_t)q * plane + (size_t)sy * pitch + sx) * es, es);
+            }
 }
 
 // Lattice constants from the dimensionless parameters (Secs. 2-4).
@@ -195,6 +227,7 @@ struct lbm_handle {
     void *mem = nullptr;
     size_t mem_bytes = 0;
     void *ws_mem = nullptr;
+    size_t ws_mem_bytes = 0;
     ObsScratch ws;
     size_t ws_max_bytes = 0, ws_min_bytes = 0, ws_u32_bytes = 0;
     unsigned long long *ws_max_base = nullptr, *ws_min_base = nullptr;
@@ -218,9 +251,7 @@ struct lbm_handle {
     int64_t step = 0;
     bool inited = false, diverged = false;
     int tile_rows = 4;         // lattice rows per tile (set per precision in lbm_create)
-    bool use_tma = false;      // TMA form of the step (tensor-map loads of the halo'd tile)
-    TmaMaps maps;              // tensor maps for tile_rows (encoded on first use)
-    unsigned int *err = nullptr;   // device status word of bounded waits (sticky)
+    unsigned int *err = nullptr;   // device status word (sticky error bits)
     double *qdot = nullptr;        // nx doubles: substrate heat flux profile
     // graph cache: one per starting parity (cur, lcur)
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -254,63 +285,6 @@ struct lbm_batch {
 
 namespace {
 
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-        else
-            cudaGetLastError();
-    }
-    return fn;
-}
-
-// One 3-D map (x, y, plane) over `planes` planes starting at `base`, with a
-// box of (32 + 2 * 16/elem) x (by + 2) x planes elements.
-int encode_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, size_t elem, int nx, int ny, int pitch,
-               long long plane, int planes, int by) {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc) return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)pitch * elem, (cuuint64_t)plane * elem};
-    const cuuint32_t box[3] = {(cuuint32_t)(32 + 2 * (16 / elem)), (cuuint32_t)(by + 2), (cuuint32_t)planes};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    return LBM_OK;
-}
-
-const void *consts_for(const lbm_handle *h);
-
-int ensure_maps(lbm_handle *h) {
-    if (h->maps.by == h->tile_rows) return LBM_OK;
-    const int prec = h->P.precision;
-    const size_t sb = storage_bytes(prec), ab = aux_bytes(prec);
-    const CUtensorMapDataType dp = prec == LBM_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                                 : prec == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    const CUtensorMapDataType da = prec == LBM_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const DevState &s = h->s;
-    for (int b = 0; b < 2; b++) {
-        int rc = encode_map(&h->maps.fhg[b], s.pop[b], dp, sb, s.nx, s.ny, s.pitch, s.plane, NFHG, h->tile_rows);
-        if (!rc)
-            rc = encode_map(&h->maps.l[b], static_cast<char *>(s.pop[b]) + (size_t)NFHG * s.plane * sb, dp, sb, s.nx,
-                            s.ny, s.pitch, s.plane, NPOP - NFHG, h->tile_rows);
-        if (!rc) rc = encode_map(&h->maps.aux[b], s.aux[b], da, ab, s.nx, s.ny, s.pitch, s.plane, NAUX, h->tile_rows);
-        if (rc) return rc;
-    }
-    h->maps.by = h->tile_rows;
-    return LBM_OK;
-}
-
 const void *consts_for(const lbm_handle *h) {
     return h->P.precision == LBM_FP64 ? static_cast<const void *>(&h->cd) : static_cast<const void *>(&h->cf);
 }
@@ -324,12 +298,6 @@ cudaError_t do_step(lbm_handle *h, cudaStream_t st, const Scalars *observe = nul
         case LBM_FP64: e = launch_step_obs_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->ws, *observe, st); break;
         case LBM_FP32: e = launch_step_obs_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->ws, *observe, st); break;
         default: e = launch_step_obs_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->ws, *observe, st); break;
-        }
-    } else if (h->use_tma) {
-        switch (h->P.precision) {
-        case LBM_FP64: e = launch_step_tma_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->maps, st); break;
-        case LBM_FP32: e = launch_step_tma_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->maps, st); break;
-        default: e = launch_step_tma_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->maps, st); break;
         }
     } else {
         switch (h->P.precision) {
@@ -413,10 +381,18 @@ int ensure_staging(lbm_handle *h) {
     return LBM_OK;
 }
 
+// The parities were reset outside a step: the epoch of the next step may
+// repeat one used before, so no tile may still show it.
+int clear_flags(lbm_handle *h) {
+    CK(cudaMemsetAsync(h->s.tflag, 0, flag_count(h->P.nx, h->P.ny) * sizeof(unsigned int), h->st));
+    return LBM_OK;
+}
+
 int finish_init(lbm_handle *h, const double *psi_dev, double R, double xc, double yc, int presolve) {
     if (int rc_ = run_pending_obs(h)) return rc_;
     h->cur = 0;
     h->lcur = 0;
+    if (int rc_ = clear_flags(h)) return rc_;
     const void *c = consts_for(h);
     cudaError_t e;
     switch (h->P.precision) {
@@ -474,18 +450,24 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     (void)sb;
     const size_t aux_b = round_up((size_t)NAUX * plane * ab, 256);
     const size_t sig_b = round_up((size_t)plane * ab, 256);
-    h->mem_bytes = 2 * pop_b + 2 * aux_b + sig_b;
+    const size_t pub_b = round_up((size_t)plane * pub_rec_bytes(p->precision), 256);
+    const size_t pfs_b = round_up((size_t)plane * arith_bytes(p->precision), 256);
+    const size_t flag_b = round_up(flag_count(nx, ny) * sizeof(unsigned int), 256);
+    // one population copy: the step streams in place (AA pattern)
+    h->mem_bytes = pop_b + 2 * aux_b + sig_b + pub_b + pfs_b + flag_b;
     if (cudaMalloc(&h->mem, h->mem_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return fail(LBM_ERR_OOM, "device allocation of the state failed");
     }
     char *b = static_cast<char *>(h->mem);
-    h->s.pop[0] = b;
-    h->s.pop[1] = b + pop_b;
-    h->s.aux[0] = b + 2 * pop_b;
-    h->s.aux[1] = b + 2 * pop_b + aux_b;
-    h->s.sigma = b + 2 * pop_b + 2 * aux_b;
+    h->s.pop = b;
+    h->s.aux[0] = b + pop_b;
+    h->s.aux[1] = b + pop_b + aux_b;
+    h->s.sigma = b + pop_b + 2 * aux_b;
+    h->s.pub = b + pop_b + 2 * aux_b + sig_b;
+    h->s.pub_fs = b + pop_b + 2 * aux_b + sig_b + pub_b;
+    h->s.tflag = reinterpret_cast<unsigned int *>(b + pop_b + 2 * aux_b + sig_b + pub_b + pfs_b);
     h->s.nx = nx;
     h->s.ny = ny;
     h->s.pitch = pitch;
@@ -502,8 +484,8 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->ws_u32_bytes = round_up((size_t)(ny + 3 + ng) * 4, 256);
     const size_t obs_b = round_up(sizeof(lbm_obs), 256);
     const size_t err_b = 256;
-    if (cudaMalloc(&h->ws_mem, part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b + err_b +
-                                   qdot_b) != cudaSuccess) {
+    h->ws_mem_bytes = part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b + err_b + qdot_b;
+    if (cudaMalloc(&h->ws_mem, h->ws_mem_bytes) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->mem);
         delete h;
@@ -526,9 +508,14 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->err = reinterpret_cast<unsigned int *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b);
     h->s.err = h->err;
     h->s.rng = h->err + 4;     // two counters in the same 256-byte block
+    h->s.epoch = h->err + 8;   // two epochs there too
     h->qdot = reinterpret_cast<double *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b +
                                          err_b);
-    if (cudaMemset(h->err, 0, err_b) != cudaSuccess || cudaMemset(h->ws_max_base, 0x00, h->ws_max_bytes) != cudaSuccess ||
+    const unsigned int first_epochs[2] = {1u, 1u};
+    if (cudaMemset(h->err, 0, err_b) != cudaSuccess ||
+        cudaMemcpy(h->s.epoch, first_epochs, sizeof first_epochs, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->s.tflag, 0, flag_b) != cudaSuccess ||
+        cudaMemset(h->ws_max_base, 0x00, h->ws_max_bytes) != cudaSuccess ||
         cudaMemset(h->ws_min_base, 0xFF, h->ws_min_bytes) != cudaSuccess ||
         cudaMemset(h->ws_u32_base, 0x00, h->ws_u32_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -590,10 +577,6 @@ int lbm_step(lbm_handle *h, int64_t n) {
     if (n < 0) return fail(LBM_ERR_BADPARAM, "n must be >= 0");
     if (!h->inited) return fail(LBM_ERR_STATE, "step before init");
     if (h->diverged) return fail(LBM_ERR_DIVERGED, "instance diverged earlier");
-    if (h->use_tma) {
-        int rc = ensure_maps(h);
-        if (rc) return rc;
-    }
     if (n >= 1 && h->obs_pending) {
         // the first step reads the observed state: it reduces the observables too
         h->obs_pending = false;
@@ -673,7 +656,7 @@ int lbm_observables_fetch(lbm_handle *h, lbm_obs *out) {
     CK(cudaMemcpyAsync(out, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(&err, h->err, sizeof err, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    if (err) return fail(LBM_ERR_CUDA, "a bounded wait in the step kernel timed out (tensor loads did not complete)");
+    if (err) return fail(LBM_ERR_CUDA, "a kernel reported an error status");
     if (out->status == LBM_ERR_DIVERGED) {
         h->diverged = true;
         return fail(LBM_ERR_DIVERGED, "non-finite psi or H");
@@ -699,7 +682,6 @@ int lbm_observables_to_host(lbm_handle *h, lbm_obs *out) {
 int lbm_observables_deferred(lbm_handle *h, lbm_obs *out) {
     if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
     if (!h->inited) return fail(LBM_ERR_STATE, "observables before init");
-    if (h->use_tma) return out ? lbm_observables_to_host(h, out) : lbm_observables_async(h);
     int rc = run_pending_obs(h);       // an earlier request that no step has taken
     if (rc) return rc;
     h->obs_pending = true;
@@ -717,7 +699,7 @@ int lbm_sync(lbm_handle *h) {
     unsigned int err = 0;
     CK(cudaMemcpyAsync(&err, h->err, sizeof err, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    if (err) return fail(LBM_ERR_CUDA, "a bounded wait in the step kernel timed out (tensor loads did not complete)");
+    if (err) return fail(LBM_ERR_CUDA, "a kernel reported an error status");
     return LBM_OK;
 }
 
@@ -836,13 +818,21 @@ int lbm_export_state(lbm_handle *h, void *host, size_t bytes) {
     CK(cudaMemcpyAsync(o + offsetof(SnapHeader, sr_step), h->s.rng + h->cur, sizeof(uint32_t),
                        cudaMemcpyDeviceToHost, h->st));
     o += sizeof hd;
-    CK(cudaMemcpyAsync(o, h->s.pop[h->cur], a, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(o + a, static_cast<char *>(h->s.pop[h->lcur]) + l_offset_bytes(h->P.precision, h->s.plane), b,
-                       cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(o, h->s.pop, a + b, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(o + a + b, h->s.aux[h->cur], c, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(o + a + b + c, h->s.sigma, d, cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemcpyAsync(o + a + b + c + d, h->ws.obs, sizeof(lbm_obs), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    // snapshots hold the natural layout whatever the phase of the state
+    const int prec = h->P.precision;
+    const size_t fb = f_bytes(prec), sb = storage_bytes(prec);
+    const long long P = h->s.plane;
+    if (h->cur) {
+        unswap_planes(o, fb, 9, h->P.nx, h->P.ny, h->s.pitch, P);
+        unswap_planes(o + 9 * P * fb, sb, 9, h->P.nx, h->P.ny, h->s.pitch, P);
+        unswap_planes(o + 9 * P * fb + 9 * P * sb, sb, 9, h->P.nx, h->P.ny, h->s.pitch, P);
+    }
+    if (h->lcur) unswap_planes(o + a, sb, 5, h->P.nx, h->P.ny, h->s.pitch, P);
     return LBM_OK;
 }
 
@@ -891,14 +881,16 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
     snap_sizes(h, a, b, c, d);
     const char *o = dev + sizeof hd;
     const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
-    CK(cudaMemcpyAsync(h->s.pop[h->cur], o, a, dd, h->st));
-    CK(cudaMemcpyAsync(static_cast<char *>(h->s.pop[h->lcur]) + l_offset_bytes(h->P.precision, h->s.plane), o + a, b,
-                       dd, h->st));
-    CK(cudaMemcpyAsync(h->s.aux[h->cur], o + a + b, c, dd, h->st));
+    // the snapshot holds the natural layout: both phases restart at 0
+    h->cur = 0;
+    h->lcur = 0;
+    CK(cudaMemcpyAsync(h->s.pop, o, a + b, dd, h->st));
+    CK(cudaMemcpyAsync(h->s.aux[0], o + a + b, c, dd, h->st));
     CK(cudaMemcpyAsync(h->s.sigma, o + a + b + c, d, dd, h->st));
     CK(cudaMemcpyAsync(h->ws.obs, o + a + b + c + d, sizeof(lbm_obs), dd, h->st));
-    CK(cudaMemcpyAsync(h->s.rng + h->cur, dev + offsetof(SnapHeader, sr_step), sizeof(uint32_t), dd, h->st));
+    CK(cudaMemcpyAsync(h->s.rng, dev + offsetof(SnapHeader, sr_step), sizeof(uint32_t), dd, h->st));
     CK(cudaEventRecord(h->imp_free[j], h->st));
+    if (int rc_ = clear_flags(h)) return rc_;
     h->step = hd.step;
     h->inited = true;
     h->diverged = false;
@@ -917,20 +909,32 @@ int lbm_presolve(lbm_handle *h, double tol, int32_t max_sweeps, int32_t *sweeps,
     const int chunk = 64;        // sweeps between two measurements
     int done = 0;
     double res = HUGE_VAL;
+    // phi before the last sweep of each chunk goes to the spare auxiliary
+    // copy (the next step overwrites it without reading it)
+    void *snap = h->s.aux[h->cur ^ 1];
     while (done < max_sweeps) {
         const int n = std::min(chunk, max_sweeps - done);
         for (int j = 0; j < n; j++) {
-            cudaError_t e = do_sweep(h, h->st);
+            cudaError_t e = cudaSuccess;
+            if (j == n - 1) {
+                switch (h->P.precision) {
+                case LBM_FP64: e = launch_phi_snap_f64(h->s, h->lcur, &h->cd, h->sh, snap, h->st); break;
+                case LBM_FP32: e = launch_phi_snap_f32(h->s, h->lcur, &h->cd, h->sh, snap, h->st); break;
+                default: e = launch_phi_snap_f16s(h->s, h->lcur, &h->cd, h->sh, snap, h->st); break;
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "pre-solve snapshot");
+            }
+            e = do_sweep(h, h->st);
             if (e != cudaSuccess) return cuda_fail(e, "pre-solve sweep");
         }
         done += n;
-        // change of phi over the last sweep: copy lcur against copy lcur ^ 1
+        // change of phi over the last sweep
         CK(cudaMemsetAsync(d, 0, sizeof *d, h->st));
         cudaError_t e;
         switch (h->P.precision) {
-        case LBM_FP64: e = launch_phi_change_f64(h->s, h->lcur, h->lcur ^ 1, &h->cd, h->sh, d, h->st); break;
-        case LBM_FP32: e = launch_phi_change_f32(h->s, h->lcur, h->lcur ^ 1, &h->cd, h->sh, d, h->st); break;
-        default: e = launch_phi_change_f16s(h->s, h->lcur, h->lcur ^ 1, &h->cd, h->sh, d, h->st); break;
+        case LBM_FP64: e = launch_phi_change_f64(h->s, h->lcur, &h->cd, h->sh, snap, d, h->st); break;
+        case LBM_FP32: e = launch_phi_change_f32(h->s, h->lcur, &h->cd, h->sh, snap, d, h->st); break;
+        default: e = launch_phi_change_f16s(h->s, h->lcur, &h->cd, h->sh, snap, d, h->st); break;
         }
         if (e != cudaSuccess) return cuda_fail(e, "pre-solve residual");
         unsigned long long bits = 0;
@@ -955,19 +959,21 @@ int lbm_presolve(lbm_handle *h, double tol, int32_t max_sweeps, int32_t *sweeps,
 
 int64_t lbm_step_count(const lbm_handle *h) { return h ? h->step : -1; }
 
+size_t lbm_device_bytes(const lbm_handle *h) {
+    if (!h) return 0;
+    size_t n = h->mem_bytes + h->ws_mem_bytes;
+    if (h->staging) n += (size_t)9 * h->P.nx * h->P.ny * sizeof(double);
+    if (h->imp_buf[0]) n += 2 * lbm_state_bytes(h);
+    return n;
+}
+
 int lbm_configure(lbm_handle *h, int32_t variant, int32_t tile_rows) {
     if (!h) return fail(LBM_ERR_BADPARAM, "NULL handle");
     if (int rc_ = run_pending_obs(h)) return rc_;
-    if (variant != LBM_STEP_TMA && variant != LBM_STEP_DIRECT) return fail(LBM_ERR_BADPARAM, "unknown variant");
-    if (variant == LBM_STEP_TMA && h->P.precision == LBM_FP16S)
-        return fail(LBM_ERR_BADPARAM, "the TMA form needs one storage type for f, h and g (FP64 or FP32)");
+    if (variant != LBM_STEP_DIRECT) return fail(LBM_ERR_BADPARAM, "unknown variant");
     if (tile_rows != 4 && tile_rows != 8 && tile_rows != 16) return fail(LBM_ERR_BADPARAM, "tile_rows must be 4, 8 or 16");
     CK(cudaStreamSynchronize(h->st));
-    h->use_tma = (variant == LBM_STEP_TMA);
-    if (h->tile_rows != tile_rows) {
-        h->tile_rows = tile_rows;
-        h->maps.by = 0;
-    }
+    h->tile_rows = tile_rows;
     drop_graphs(h);
     return LBM_OK;
 }
@@ -1037,10 +1043,12 @@ static void free_list(WorkList &L) {
     L.tile_item_dev = nullptr;
 }
 
-// Device bytes a member's step touches (both copies of every plane).
+// Device bytes a member's step touches: the populations (one copy, in
+// place), both auxiliary copies, sigma and the published records.
 static size_t member_state_bytes(const lbm_handle *h) {
-    const size_t ab = aux_bytes(h->P.precision);
-    return (size_t)h->s.plane * (2 * pop_cell_bytes(h->P.precision) + 2 * NAUX * ab + ab);
+    const int prec = h->P.precision;
+    const size_t ab = aux_bytes(prec);
+    return (size_t)h->s.plane * (pop_cell_bytes(prec) + 2 * NAUX * ab + ab + pub_rec_bytes(prec));
 }
 
 static int build_list(lbm_batch *b, const std::vector<int> &idx, int tile_rows, int sms, WorkList &L) {
@@ -1191,26 +1199,69 @@ int lbm_batch_create(lbm_handle *const *members, int32_t n, void *stream, int32_
     }
     int rc = LBM_OK;
     if (tile_rows == 0) {
-        // Autotune: time each tile height on the members' own data.  The step
-        // reads one copy and writes the other, so re-running it without
-        // flipping parities leaves every member's state unchanged.
+        // Autotune: time each tile height on the members' own data.  The
+        // steps stream in place, so the trials advance the members' state
+        // (six steps per height, an even number: the layout phases return)
+        // and overwrite both auxiliary copies; the state they started from
+        // (populations, auxiliary copies, sigma, counters) is saved first
+        // and put back after, with every publication flag cleared (the
+        // epochs will repeat).
+        std::vector<size_t> pop_sz(n), sig_sz(n), aux_sz(n);
+        size_t total = 0;
+        for (int i = 0; i < n; i++) {
+            const lbm_handle *h = members[i];
+            pop_sz[i] = (size_t)h->s.plane * pop_cell_bytes(h->P.precision);
+            sig_sz[i] = (size_t)h->s.plane * aux_bytes(h->P.precision);
+            aux_sz[i] = (size_t)NAUX * h->s.plane * aux_bytes(h->P.precision);
+            total += round_up(pop_sz[i], 256) + round_up(sig_sz[i], 256) + 2 * round_up(aux_sz[i], 256) + 256;
+        }
+        char *saved = nullptr;
+        if (cudaMalloc(&saved, total) != cudaSuccess) {
+            cudaGetLastError();
+            lbm_batch_destroy(b);
+            return fail(LBM_ERR_OOM, "device allocation of the autotuner's saved state failed");
+        }
+        auto copy_members = [&](bool save) -> cudaError_t {
+            size_t off = 0;
+            for (int i = 0; i < n; i++) {
+                const lbm_handle *h = members[i];
+                char *a = saved + off, *bb = a + round_up(pop_sz[i], 256), *x0 = bb + round_up(sig_sz[i], 256);
+                char *x1 = x0 + round_up(aux_sz[i], 256), *cnt = x1 + round_up(aux_sz[i], 256);
+                off += round_up(pop_sz[i], 256) + round_up(sig_sz[i], 256) + 2 * round_up(aux_sz[i], 256) + 256;
+                const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+                cudaError_t e = cudaMemcpyAsync(save ? a : h->s.pop, save ? h->s.pop : a, pop_sz[i], dd, b->st);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(save ? bb : h->s.sigma, save ? h->s.sigma : bb, sig_sz[i], dd, b->st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(save ? x0 : h->s.aux[0], save ? h->s.aux[0] : x0, aux_sz[i], dd, b->st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(save ? x1 : h->s.aux[1], save ? h->s.aux[1] : x1, aux_sz[i], dd, b->st);
+                // the status word, rounding counters and epochs
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(save ? static_cast<void *>(cnt) : static_cast<void *>(h->err),
+                                        save ? static_cast<const void *>(h->err) : static_cast<const void *>(cnt), 64, dd,
+                                        b->st);
+                if (e == cudaSuccess && !save)
+                    e = cudaMemsetAsync(h->s.tflag, 0, flag_count(h->P.nx, h->P.ny) * sizeof(unsigned int), b->st);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        };
         float best = 1e30f;
         int best_rows = 8;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
+        cudaError_t es = copy_members(true);
+        if (es != cudaSuccess) rc = cuda_fail(es, "autotune save");
         for (int rows : {4, 8, 16}) {
+            if (rc) break;
             if ((rc = batch_build(b, rows))) break;
             const int k_e = b->k_e;
             b->k_e = 1;
             int f = 0, lf = 0;
             cudaError_t e = list_steps(b, b->all, 1, f, lf, b->st);       // warm-up
             cudaEventRecord(e0, b->st);
-            for (int r = 0; r < 5 && e == cudaSuccess; r++) {
-                f = 0;
-                lf = 0;
-                e = list_steps(b, b->all, 1, f, lf, b->st);
-            }
+            for (int r = 0; r < 5 && e == cudaSuccess; r++) e = list_steps(b, b->all, 1, f, lf, b->st);
             cudaEventRecord(e1, b->st);
             b->k_e = k_e;
             if (e != cudaSuccess) { rc = cuda_fail(e, "autotune launch"); break; }
@@ -1219,6 +1270,10 @@ int lbm_batch_create(lbm_handle *const *members, int32_t n, void *stream, int32_
             cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best) { best = ms; best_rows = rows; }
         }
+        es = copy_members(false);
+        if (es != cudaSuccess && !rc) rc = cuda_fail(es, "autotune restore");
+        if (cudaStreamSynchronize(b->st) != cudaSuccess && !rc) rc = fail(LBM_ERR_CUDA, "autotune restore sync");
+        cudaFree(saved);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         tile_rows = best_rows;

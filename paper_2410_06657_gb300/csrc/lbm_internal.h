@@ -46,20 +46,17 @@ struct Shift {
 
 // Views of one instance's device state (element pointers).
 struct DevState {
-    void *pop[2];          // two copies of NPOP planes
+    void *pop;             // one copy of NPOP planes, streamed in place (AA pattern)
     void *aux[2];          // two copies of NAUX planes
     void *sigma;           // one plane
-    unsigned int *err;     // device status word: bit 0 = a bounded wait timed out
+    void *pub;             // one record (psi, rho, eps, phi) per cell, arithmetic type
+    void *pub_fs;          // one plane of f_s, arithmetic type
+    unsigned int *tflag;   // per step tile (4-row tiles: the most): epoch of its last publication
+    unsigned int *err;     // device status word (sticky error bits)
     unsigned int *rng;     // [2] stochastic-rounding step counters of half storage (or null)
+    unsigned int *epoch;   // [2] step epochs (>= 1), alternating with the parity
     int nx, ny, pitch;     // pitch: elements per row (multiple of 32)
     long long plane;       // elements per plane (pitch * ny)
-};
-
-// Tensor maps of one buffer copy for the TMA step (tile height BY):
-// f, h, g planes, l planes, auxiliary planes.
-struct TmaMaps {
-    CUtensorMap fhg[2], l[2], aux[2];
-    int by;                // tile height the boxes were encoded for (0: none)
 };
 
 // Workspace of the observables reduction.
@@ -89,10 +86,6 @@ struct Scalars {           // per-call scalars of the observables reduction
     cudaError_t launch_step_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,    \
                                      const void *consts, const Shift &sh, int tile_rows,       \
                                      cudaStream_t st);                                         \
-    cudaError_t launch_step_tma_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,\
-                                         const void *consts, const Shift &sh, const TmaMaps &m,\
-                                         cudaStream_t st);                                     \
-    size_t tma_smem_##SUFFIX(int tile_rows);                                                   \
     cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, int cur, uint32_t sr_sys,   \
                                       const void *consts, const Shift &sh, cudaStream_t st);  \
     cudaError_t launch_init_##SUFFIX(const DevState &s, const double *psi_dev, double R,       \
@@ -112,10 +105,13 @@ struct Scalars {           // per-call scalars of the observables reduction
     cudaError_t launch_get_##SUFFIX(const DevState &s, int cur, int lcur, int field,           \
                                     const void *consts, const Shift &sh, double *out,          \
                                     cudaStream_t st);                                          \
-    cudaError_t launch_phi_change_##SUFFIX(const DevState &s, int la, int lb,                  \
+    cudaError_t launch_phi_snap_##SUFFIX(const DevState &s, int lcur,                          \
+                                         const void *consts /* Consts<double> */,             \
+                                         const Shift &sh, void *snap, cudaStream_t st);        \
+    cudaError_t launch_phi_change_##SUFFIX(const DevState &s, int lcur,                        \
                                            const void *consts /* Consts<double> */,           \
-                                           const Shift &sh, unsigned long long *out,           \
-                                           cudaStream_t st);                                   \
+                                           const Shift &sh, const void *snap,                  \
+                                           unsigned long long *out, cudaStream_t st);          \
     cudaError_t launch_set_##SUFFIX(const DevState &s, int cur, int lcur, int field,           \
                                     const void *consts, const Shift &sh, const double *in,     \
                                     cudaStream_t st);

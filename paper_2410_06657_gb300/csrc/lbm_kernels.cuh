@@ -6,22 +6,28 @@
 // Included once by each precision's translation unit.
 //
 // Memory layout (all structure-of-arrays, x fastest, rows padded to `pitch`):
-//   pop[b]  : 32 planes  f_0..8 | h_0..8 | g_0..8 | l_0..4 (half storage:
-//             the f planes in float, the others in half)
+//   pop     : ONE copy of 32 planes  f_0..8 | h_0..8 | g_0..8 | l_0..4 (half
+//             storage: the f planes in float, the others in half), streamed
+//             in place with the AA pattern (below); f, h, g share a layout
+//             phase that flips every step, l keeps its own because the extra
+//             potential sweeps flip it alone
 //   aux[b]  : 7 planes   f_s, mdot, rho C_p T mdot, psi u_x, psi u_y, p, S
 //             of the previous step (read by the next step's stencils, so the
 //             step reads copy b and writes copy 1-b)
-//   sigma   : conductivity at time n for the extra potential sweeps.
-// f, h, g swap copies every step; l swaps on every potential sweep, so it
-// keeps its own parity.
+//   sigma   : conductivity at time n for the extra potential sweeps
+//   pub     : (psi, rho, eps, phi) of each tile's edge cells at the current
+//             time level, and f_s for observing steps, published by the tile
+//             before it overwrites its slots; tflag: per tile, the epoch of
+//             the step that last published.
 //
 // One step is one launch.  A thread block owns a 32 x BY tile.  Phase 1
 // computes the local macroscopic fields (row a1) of the tile and of its
-// one-cell halo (recomputed from the halo's own populations, so no second
-// pass over HBM is needed) into shared memory; phase 2 applies the
-// radius-1 stencils (a2), forces (a3), flow macros (a4), the four
-// collisions (a5-a8) and pushes the post-collision populations to their
-// destinations in the other copy, applying the wall rules (a9).
+// one-cell halo into shared memory: the halo's from the halo cells' own
+// populations, or from their owner's published record once the owner has
+// started to overwrite them (no block waits for another).  Phase 2 applies
+// the radius-1 stencils (a2), forces (a3), flow macros (a4), the four
+// collisions (a5-a8) and writes the post-collision populations back into
+// the slots the cell read, with the wall rules (a9).
 #pragma once
 
 #include <cuda.h>
@@ -29,6 +35,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "lbm_internal.h"
@@ -315,6 +322,110 @@ __device__ __forceinline__ void ring_slot(int r, int &ex, int &ey) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// In-place streaming: the AA pattern (Bailey, Myre, Walsh, Lilja and Saar,
+// ICPP 2009).  One copy of the populations holds the state in one of two
+// layouts, which alternate from step to step:
+//   phase 0 (natural): population i of cell x sits in plane i at x;
+//   phase 1 (swapped): population i of cell x sits in plane opp(i) at the
+//     upstream cell x - c_i, or in plane i at x itself where x - c_i lies
+//     beyond a wall (the previous step left the bounced-back value there).
+// A step from phase 0 reads each cell's own slots and writes the
+// post-collision population i into plane opp(i) of the same cell (already
+// bounced back where x + c_i lies beyond a wall); a step from phase 1 reads
+// through the swapped layout and pushes population i into plane i at
+// x + c_i (into a wall: back into plane opp(i) at x).  Either way a cell
+// writes exactly the slots it read and no other cell writes them, so the
+// update is race-free in place.  x is periodic.  Half storage keeps the
+// reference of (direction, row of the cell that will read the value), as
+// the two-copy push did, so a slot's raw bits mean the same in both layouts.
+// ---------------------------------------------------------------------------
+
+// Offset (plane times P plus the cell offset) of the slot holding population
+// i of cell (x, y) at the start of a step from phase ph, relative to the
+// system's first plane; xm, xp are x - 1 and x + 1 wrapped.
+template <int NQ>
+__device__ __forceinline__ uint32_t aa_src(int ph, int i, uint32_t P, uint32_t pitch, int x, int y, int xm, int xp,
+                                           int ny) {
+    const int cx = NQ == 9 ? CX[i] : CX5[i], cy = NQ == 9 ? CY[i] : CY5[i];
+    const int io = NQ == 9 ? OPP9[i] : OPP5[i];
+    const uint32_t own = (uint32_t)i * P + (uint32_t)y * pitch + (uint32_t)x;
+    if (ph == 0 || (cx == 0 && cy == 0)) return own;
+    const int yu = y - cy;
+    if (yu < 0 || yu >= ny) return own;
+    const int xu = cx > 0 ? xm : (cx < 0 ? xp : x);
+    return (uint32_t)io * P + (uint32_t)yu * pitch + (uint32_t)xu;
+}
+
+// Destination of cell (x, y)'s post-collision population i in a step from
+// phase ph; `wall` tells whether it leaves through a wall, in which case the
+// slot receives the bounced value (population opp(i) of the cell itself).
+// EDGE false: the tile touches no wall row, so no direction leaves.
+template <int NQ, bool EDGE>
+__device__ __forceinline__ uint32_t aa_dst(int ph, int i, uint32_t P, uint32_t pitch, int x, int y, int xm, int xp,
+                                           int ny, bool &wall) {
+    const int cx = NQ == 9 ? CX[i] : CX5[i], cy = NQ == 9 ? CY[i] : CY5[i];
+    const int io = NQ == 9 ? OPP9[i] : OPP5[i];
+    const int yt = y + cy;
+    wall = EDGE && (yt < 0 || yt >= ny);
+    if (ph == 0 || wall) return (uint32_t)io * P + (uint32_t)y * pitch + (uint32_t)x;
+    const int xt = cx > 0 ? xp : (cx < 0 ? xm : x);
+    return (uint32_t)i * P + (uint32_t)yt * pitch + (uint32_t)xt;
+}
+
+// ---------------------------------------------------------------------------
+// Publication of tile-edge macros.  The fused step recomputes its halo's
+// macros from the halo cells' populations, which their owner tile (another
+// block) overwrites in place during the same step.  Before it overwrites any
+// slot, the owner stores the macros of its edge cells and then its tile's
+// flag = this step's epoch (publish_flag); a reader loads a halo cell's
+// populations, then -- after a fence -- its owner's flag: if the flag shows
+// this step's epoch, some loaded slot may already hold the new value and the
+// published record is used; otherwise the owner had not started writing when
+// the loads were performed, so they hold the time-n values.  The two routes
+// give the same macros bit for bit (the same code on the same inputs).  No
+// thread waits for another: a reader never depends on an owner's progress.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int ld_flag(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_flag(unsigned int *p, unsigned int v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+template <typename T>
+struct alignas(4 * sizeof(T)) PubRec { T psi, rho, eps, phi; };
+
+__device__ __forceinline__ PubRec<float> ld_pub(const PubRec<float> *p) {
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ PubRec<double> ld_pub(const PubRec<double> *p) {
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st_pub(PubRec<float> *p, float psi, float rho, float eps, float phi) {
+    *reinterpret_cast<float4 *>(p) = make_float4(psi, rho, eps, phi);
+}
+__device__ __forceinline__ void st_pub(PubRec<double> *p, double psi, double rho, double eps, double phi) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(psi, rho);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(eps, phi);
+}
+
+// The tile's records (stored by its threads before the block barrier that
+// precedes this call) become visible before the flag, and the flag before
+// any slot of the tile is overwritten (after the next block barrier).
+__device__ __forceinline__ void publish_flag(unsigned int *flag, unsigned int epoch) {
+    fence_gpu();
+    st_flag(flag, epoch);
+    fence_gpu();
+}
+
 // ---------------------------------------------------------------------------
 // The fused step (rows a1-a9) for one 32 x BY tile.
 // ---------------------------------------------------------------------------
@@ -331,62 +442,72 @@ struct TileSmem {
 template <typename S, typename T, typename A>
 struct StepIO {
     using F = typename FStore<S>::type;
-    const F *f_in;
-    F *f_out;
-    const S *h_in, *g_in, *l_in;
-    S *h_out, *g_out, *l_out;
+    F *f;                    // population planes (one copy, streamed in place)
+    S *h, *g, *l;
     const A *aux_in;
     A *aux_out;
     A *sigma;
-    int nx, ny, pitch, write_sigma;
+    PubRec<T> *pub;          // published edge macros of the current time level
+    T *pub_fs;               // published f_s (observing steps)
+    unsigned int *tflag;     // per tile: epoch of its last publication
+    unsigned int *rng;       // [2] stochastic-rounding counters (half storage) or null
+    unsigned int *ep;        // [2] step epochs
+    int nx, ny, pitch, write_sigma, lph, tiles_x;
     long long plane;
-    uint32_t sr_step;       // stochastic-rounding step counter (half storage)
+    uint32_t sr_step;        // this step's stochastic-rounding counter (half storage)
+    uint32_t epoch;          // this step's epoch
 };
 
-// The step's pointers and sizes for the parities (cur, lcur); the host
-// resolves them for the single-instance kernels, so those kernels receive
-// the pointers instead of selecting them per launch.
+// The step's pointers and sizes for the parities (cur, lcur): cur is the
+// layout phase of f, h, g and selects the auxiliary copy, lcur the phase of
+// l.  The host resolves them for the single-instance kernels.
 template <typename S, typename T, typename A>
 __host__ __device__ __forceinline__ StepIO<S, T, A> step_io(const DevState &s, int cur, int lcur, int write_sigma) {
     StepIO<S, T, A> io;
+    const Planes<S> pl = Planes<S>::at(s.pop, s.plane);
+    io.f = pl.f;
+    io.h = pl.h;
+    io.g = pl.g;
+    io.l = pl.l;
     // select rather than index the parameter arrays (a dynamic index would
     // copy them to local memory)
-    const Planes<S> pin = Planes<S>::at(cur ? s.pop[1] : s.pop[0], s.plane);
-    const Planes<S> pout = Planes<S>::at(cur ? s.pop[0] : s.pop[1], s.plane);
-    io.f_in = pin.f;
-    io.h_in = pin.h;
-    io.g_in = pin.g;
-    io.f_out = pout.f;
-    io.h_out = pout.h;
-    io.g_out = pout.g;
-    io.l_in = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], s.plane).l;
-    io.l_out = Planes<S>::at(lcur ? s.pop[0] : s.pop[1], s.plane).l;
     io.aux_in = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     io.aux_out = reinterpret_cast<A *>(cur ? s.aux[0] : s.aux[1]);
     io.sigma = reinterpret_cast<A *>(s.sigma);
+    io.pub = reinterpret_cast<PubRec<T> *>(s.pub);
+    io.pub_fs = reinterpret_cast<T *>(s.pub_fs);
+    io.tflag = s.tflag;
+    io.rng = s.rng;
+    io.ep = s.epoch;
     io.sr_step = 0u;
+    io.epoch = 0u;
     io.nx = s.nx;
     io.ny = s.ny;
     io.pitch = s.pitch;
     io.write_sigma = write_sigma;
+    io.lph = lcur;
+    io.tiles_x = (s.nx + 31) / 32;
     io.plane = s.plane;
     return io;
 }
 
-// Half storage: the stochastic-rounding counter of this step lives in device
-// memory (graph replays advance it), so the kernel reads it.
+// The step's counters live in device memory (graph replays advance them):
+// counter[cur] is this step's, and one thread writes counter[cur ^ 1] for
+// the next step (parities flipped), which no thread of this step reads.
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void load_sr_step(StepIO<S, T, A> &io, const unsigned int *rng, int cur) {
+__device__ __forceinline__ void load_counters(StepIO<S, T, A> &io, int cur) {
     if constexpr (Pol<S, T>::shifted) {
-        if (rng) io.sr_step = rng[cur];
+        if (io.rng) io.sr_step = io.rng[cur];
     }
+    io.epoch = io.ep[cur];
 }
-
 template <typename S, typename T, typename A>
-__device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, int lcur, int write_sigma) {
-    StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);
-    load_sr_step(io, s.rng, cur);
-    return io;
+__device__ __forceinline__ void advance_counters(const StepIO<S, T, A> &io, int cur, bool leader) {
+    if (!leader) return;
+    if constexpr (Pol<S, T>::shifted) {
+        if (io.rng) io.rng[cur ^ 1] = io.sr_step + 1u;
+    }
+    io.ep[cur ^ 1] = io.epoch + 1u;
 }
 
 // Observation hooks of a step: a plain step observes nothing.  A step that
@@ -395,59 +516,85 @@ __device__ __forceinline__ StepIO<S, T, A> make_io(const DevState &s, int cur, i
 // adds every own cell's terms after the cell's push.
 struct NoObs {};
 
-// Halo/own macro evaluation of one cell into shared memory.
-template <typename S, typename T, typename A, int BY, typename OB = NoObs>
-__device__ __forceinline__ void cell_to_smem(const StepIO<S, T, A> &io, const Consts<T> &c,
-                                             const Shift &sh, TileSmem<T, BY> &sm, int ex, int ey,
-                                             int x, int y, OB *ob = nullptr) {
-    const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
-    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
-    Refs<T> rf;
-    make_refs<S, T>(rf, sh, c, y, io.ny);
-    const float fi = 1.0f / sh.f_scale, gi = 1.0f / sh.g_scale, li = 1.0f / sh.l_scale;
-    T f[9], g[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        f[i] = Pol<typename FStore<S>::type, T>::ld(io.f_in + (i * P + k), rf.f[i], fi);
-        g[i] = Pol<S, T>::ld(io.g_in + (i * P + k), rf.g[i], gi);
-    }
-    T l1234 = T(0);
-#pragma unroll
-    for (int i = 1; i < 5; i++) l1234 += Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], li);
-    Macro<T> m;
-    local_macros(f, g, l1234, T(io.aux_in[AUX_FS * P + k]), T(io.aux_in[AUX_MDOT * P + k]),
-                 T(io.aux_in[AUX_Q * P + k]), c, m);
-    sm.q[ey][ex] = {m.psi, m.rho, m.eps, m.phi};
-    sm.ps[ey][ex] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
-    if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ey, ex, m);
-}
-
 // The stored values one cell's macros need, in the arithmetic type T.
 template <typename T>
 struct CellLoad {
     T f[9], g[9], l1234, fs_prev, mdot_prev, Q_prev;
 };
 
-// A ring cell's stored values and its (p, S), loaded into registers.
-template <typename S, typename T, typename A>
-__device__ __forceinline__ void load_ring_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
-                                               uint32_t P, uint32_t k, int y, CellLoad<T> &o, T &pv, T &Sv) {
+// Loads of cell (x, y)'s stored values for its macros, through the layout
+// of phases (PH, io.lph), and its previous-step (p, S).
+template <typename S, typename T, typename A, int PH>
+__device__ __forceinline__ void load_cell_aa(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, int x,
+                                             int y, CellLoad<T> &o, T &pv, T &Sv) {
+    const uint32_t P = (uint32_t)io.plane, pitch = (uint32_t)io.pitch;
+    const int xm = x == 0 ? io.nx - 1 : x - 1, xp = x == io.nx - 1 ? 0 : x + 1;
+    const uint32_t k = (uint32_t)y * pitch + (uint32_t)x;
     Refs<T> rf;
     make_refs<S, T>(rf, sh, c, y, io.ny);
     const float fi = 1.0f / sh.f_scale, gi = 1.0f / sh.g_scale, li = 1.0f / sh.l_scale;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        o.f[i] = Pol<typename FStore<S>::type, T>::ld(io.f_in + (i * P + k), rf.f[i], fi);
-        o.g[i] = Pol<S, T>::ld(io.g_in + (i * P + k), rf.g[i], gi);
+        const uint32_t o9 = aa_src<9>(PH, i, P, pitch, x, y, xm, xp, io.ny);
+        o.f[i] = Pol<typename FStore<S>::type, T>::ld(io.f + o9, rf.f[i], fi);
+        o.g[i] = Pol<S, T>::ld(io.g + o9, rf.g[i], gi);
     }
     o.l1234 = T(0);
 #pragma unroll
-    for (int i = 1; i < 5; i++) o.l1234 += Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], li);
+    for (int i = 1; i < 5; i++)
+        o.l1234 += Pol<S, T>::ld(io.l + aa_src<5>(io.lph, i, P, pitch, x, y, xm, xp, io.ny), rf.l[i], li);
     o.fs_prev = T(io.aux_in[AUX_FS * P + k]);
     o.mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
     o.Q_prev = T(io.aux_in[AUX_Q * P + k]);
     pv = T(io.aux_in[AUX_P * P + k]);
     Sv = T(io.aux_in[AUX_S * P + k]);
+}
+
+// Macros of a cell outside the tile whose loads (load_cell_aa) have been
+// issued: its owner's published record if the owner has published in this
+// step, else the macros of the loaded values (see publish_flag).  OBS: the
+// record's f_s is needed too.
+template <typename S, typename T, typename A, int BY, bool OBS>
+__device__ __forceinline__ void resolve_ext(const StepIO<S, T, A> &io, const Consts<T> &c, int x, int y,
+                                            const CellLoad<T> &ld, Macro<T> &m) {
+    fence_gpu();      // the loads above are performed before the flag is read
+    const unsigned int e = ld_flag(io.tflag + (uint32_t)(y / BY) * (uint32_t)io.tiles_x + (uint32_t)(x >> 5));
+    if (e == io.epoch) {
+        const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
+        const PubRec<T> r = ld_pub(io.pub + k);
+        m.psi = r.psi;
+        m.rho = r.rho;
+        m.eps = r.eps;
+        m.phi = r.phi;
+        m.fs = OBS ? __ldcg(io.pub_fs + k) : T(0);
+        m.H = T(0);
+        m.T_ = T(0);
+    } else {
+        local_macros<T>(ld.f, ld.g, ld.l1234, ld.fs_prev, ld.mdot_prev, ld.Q_prev, c, m);
+    }
+}
+
+// Macros of an outside cell into the extended tile slot (ex, ey).
+template <typename S, typename T, typename A, int BY, int PH, typename OB>
+__device__ __forceinline__ void ext_to_smem(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
+                                            TileSmem<T, BY> &sm, int ex, int ey, int x, int y, OB *ob) {
+    constexpr bool OBS = !std::is_same<OB, NoObs>::value;
+    CellLoad<T> ld;
+    T pv, Sv;
+    load_cell_aa<S, T, A, PH>(io, c, sh, x, y, ld, pv, Sv);
+    Macro<T> m;
+    resolve_ext<S, T, A, BY, OBS>(io, c, x, y, ld, m);
+    sm.q[ey][ex] = {m.psi, m.rho, m.eps, m.phi};
+    sm.ps[ey][ex] = {pv, Sv};
+    if constexpr (OBS) ob->macro(ey, ex, m);
+}
+
+// An own cell's record, for the halos of its neighbour tiles: cells on the
+// tile's edge only (no other tile reads the inner ones).
+template <typename S, typename T, typename A, bool OBS>
+__device__ __forceinline__ void publish_cell(const StepIO<S, T, A> &io, uint32_t k, const Macro<T> &m) {
+    st_pub(io.pub + k, m.psi, m.rho, m.eps, m.phi);
+    if constexpr (OBS) io.pub_fs[k] = m.fs;
 }
 
 // Asynchronous global -> shared copy of one 4- or 8-byte element.
@@ -464,20 +611,24 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Warp-cooperative 16-byte copies of one full tile row (32 cells starting at
 // offset k0, a multiple of 32 elements, so every chunk is 16-byte aligned)
-// of the 32 population planes into the stash: each warp instruction moves
+// of the population planes into the stash: each warp instruction moves
 // 32 / CR planes, lane tx copies chunk tx % CR of plane j * (32 / CR) +
 // tx / CR.  Planes 0-26 (f, h, g) lie contiguously from pin, planes 27-31
-// (l) from lin.  A quarter (FP32) or half (FP64) of the instructions of
-// one copy per element.
+// (l) from lin; with l_all false only planes 0-27 are copied (the rest
+// population l_0 is in place in either layout, l_1..4 are then gathered by
+// the caller).  A quarter (FP32) or half (FP64) of the instructions of one
+// copy per element.
 template <typename T, int BY>
 __device__ __forceinline__ void stash_row_async(T (*stash)[BY][32], int ty, int tx, const T *pin,
-                                                const T *lin, uint32_t P, uint32_t k0) {
+                                                const T *lin, uint32_t P, uint32_t k0, bool l_all) {
     constexpr int CR = 32 * int(sizeof(T)) / 16;    // 16-byte chunks per row
     constexpr int PPJ = 32 / CR;                    // planes per instruction
     constexpr int EPC = 16 / int(sizeof(T));        // elements per chunk
+    static_assert(28 % PPJ == 0, "planes 28-31 start an instruction");
     const int part = tx % CR, sub = tx / CR;
 #pragma unroll
     for (int j = 0; j < CR; j++) {
+        if (j * PPJ >= 28 && !l_all) break;
         const int q = j * PPJ + sub;
         const T *src;
         if (j * PPJ + PPJ <= 27)
@@ -502,18 +653,6 @@ struct StashPops {            // own cell's populations stashed in shared memory
     __device__ __forceinline__ T l(int i) const { return q[27 + i][ty][tx]; }
 };
 
-template <typename T>
-struct RegPops {
-    const T (&f_)[9];
-    const T (&g_)[9];
-    const T (&l_)[5];
-    const T (&h_)[9];
-    __device__ __forceinline__ T f(int i) const { return f_[i]; }
-    __device__ __forceinline__ T g(int i) const { return g_[i]; }
-    __device__ __forceinline__ T l(int i) const { return l_[i]; }
-    __device__ __forceinline__ T h(int i) const { return h_[i]; }
-};
-
 // Wall ghost rows of the stencil tile (readings R17, R19): wetting ghost of
 // psi at the bottom wall, neutral at the top, copies of rho, eps, p, S, and
 // phi mirrored about the electrode potential.
@@ -535,18 +674,20 @@ __device__ __forceinline__ void fill_ghosts(TileSmem<T, BY> &sm, const Consts<T>
 }
 
 // Row a2-a9 for one own cell: stencils from the shared-memory tile, forces,
-// flow macros, the four collisions and the push into the other copy.  PS
+// flow macros, the four collisions and the write-back of the post-collision
+// populations through the AA pattern from phase PH (l: io.lph).  PS
 // supplies the cell's time-n populations (registers or shared memory).
 // EDGE: the tile touches a wall row, so destinations may leave the lattice;
 // interior tiles skip the per-direction wall tests.
-template <typename S, typename T, typename A, int BY, bool EDGE, typename PopSrc, typename OB = NoObs>
+template <typename S, typename T, typename A, int BY, bool EDGE, int PH, typename PopSrc, typename OB = NoObs>
 __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
                                           const TileSmem<T, BY> &sm, const PopSrc &PS, int tx, int ty, int x,
                                           int y, const Macro<T> &m, T fs_prev, T pux_prev, T puy_prev,
                                           OB *ob = nullptr) {
     const int nx = io.nx, ny = io.ny;
     const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
-    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
+    const uint32_t pitch = (uint32_t)io.pitch;
+    const uint32_t k = (uint32_t)y * pitch + (uint32_t)x;
     Refs<T> ro;                               // destination references (half storage)
     const int ex = tx + 1, ey = ty + 1;
     // ---- a2: stencils ----------------------------------------------------
@@ -621,16 +762,8 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     for (int i = 1; i < 9; i++) sh_ += PS.h(i);
     const T p = cs2<T>() / (T(1) - w9<T>(0)) * (sh_ + T(0.5) * Sn + tau_h * R0 + r * s_i<T>(0, ux, uy));
 
-    // ---- collisions + push streaming (a5-a9) -------------------------------
-    // destinations of the push: wrapped columns and rows computed once
+    // ---- collisions + in-place streaming (a5-a9) ---------------------------
     const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
-    const uint32_t r0 = (uint32_t)y * (uint32_t)io.pitch;
-    auto dest = [&](int i, int cxv, int cyv) -> uint32_t {
-        (void)i;
-        const uint32_t row = cyv < 0 ? r0 - (uint32_t)io.pitch : (cyv > 0 ? r0 + (uint32_t)io.pitch : r0);
-        return row + (uint32_t)(cxv < 0 ? xm : (cxv > 0 ? xp : x));
-    };
-
     const T uu_ = ux * ux + uy * uy;
     const T B15 = T(1.5) * uu_;                    // u.u / (2 c_s^2)
 
@@ -661,11 +794,9 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                               r * s_i<T>(i, ux, uy);
                 post = PS.h(i) - (PS.h(i) - heq) / tau_h + pre * Ri;
             }
-            const int yt = y + CY[i];
-            if (EDGE && (yt < 0 || yt >= ny))
-                Pol<S, T>::st(io.h_out + (OPP9[i] * P + k), post, T(0), sh.h_scale);
-            else
-                Pol<S, T>::st(io.h_out + (i * P + dest(i, CX[i], CY[i])), post, T(0), sh.h_scale);
+            bool wall;
+            const uint32_t d = aa_dst<9, EDGE>(PH, i, P, pitch, x, y, xm, xp, ny, wall);
+            Pol<S, T>::st(io.h + d, post, T(0), sh.h_scale);   // walls: half-way bounce-back
         }
     }
     // a5: phase field
@@ -702,16 +833,14 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                 const T Fi = w9<T>(i) * cdot<T>(CX[i], CY[i], ax, ay) / cs2<T>() + w9<T>(i) * ps * mdot;
                 post = PS.f(i) - (PS.f(i) - feq) / c.tau_f + pre * Fi;
             }
-            const int yt = y + CY[i];
-            if (EDGE && (yt < 0 || yt >= ny)) {
-                if constexpr (Pol<typename FStore<S>::type, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<typename FStore<S>::type, T>::st_sr(io.f_out + (OPP9[i] * P + k), post, ro.f[OPP9[i]], sh.f_scale,
-                                                        bits13(rb, i));
-            } else {
-                if constexpr (Pol<typename FStore<S>::type, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<typename FStore<S>::type, T>::st_sr(io.f_out + (i * P + dest(i, CX[i], CY[i])), post, ro.f[i],
-                                                        sh.f_scale, bits13(rb, i));
+            bool wall;
+            const uint32_t d = aa_dst<9, EDGE>(PH, i, P, pitch, x, y, xm, xp, ny, wall);
+            T ref = T(0);
+            if constexpr (Pol<typename FStore<S>::type, T>::shifted) {
+                make_refs<S, T>(ro, sh, c, wall ? y : y + CY[i], ny);
+                ref = wall ? ro.f[OPP9[i]] : ro.f[i];
             }
+            Pol<typename FStore<S>::type, T>::st_sr(io.f + d, post, ref, sh.f_scale, bits13(rb, i));
         }
     }
     // a8: enthalpy (Sec. 3.3)
@@ -743,23 +872,20 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                           (c.Cref / cp + cu / cs2<T>() + (cu * cu - cs2<T>() * uu) / (T(2) * cs2<T>() * cs2<T>()));
                 post = PS.g(i) - (PS.g(i) - geq) / tau_g + pre * (w9<T>(i) * Qn);
             }
-            const int yt = y + CY[i];
-            if (EDGE && yt < 0) {    // cold wall: anti-bounce-back to C_p,ref T_w
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st_sr(io.g_out + (OPP9[i] * P + k),
-                                 -post + T(2) * w9<T>(i) * c.Cref_Tw, ro.g[OPP9[i]], sh.g_scale, bits13(rb, i));
-            } else if (EDGE && yt >= ny) {   // top wall: adiabatic bounce-back
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st_sr(io.g_out + (OPP9[i] * P + k), post, ro.g[OPP9[i]], sh.g_scale,
-                                 bits13(rb, i));
-            } else {
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st_sr(io.g_out + (i * P + dest(i, CX[i], CY[i])), post, ro.g[i], sh.g_scale,
-                                 bits13(rb, i));
+            bool wall;
+            const uint32_t d = aa_dst<9, EDGE>(PH, i, P, pitch, x, y, xm, xp, ny, wall);
+            // cold wall: anti-bounce-back to C_p,ref T_w; top wall: adiabatic bounce-back
+            const T val = (wall && y + CY[i] < 0) ? -post + T(2) * w9<T>(i) * c.Cref_Tw : post;
+            T ref = T(0);
+            if constexpr (Pol<S, T>::shifted) {
+                make_refs<S, T>(ro, sh, c, wall ? y : y + CY[i], ny);
+                ref = wall ? ro.g[OPP9[i]] : ro.g[i];
             }
+            Pol<S, T>::st_sr(io.g + d, val, ref, sh.g_scale, bits13(rb, i));
         }
     }
-    // a6: potential (Sec. 3.4), one sweep inside the fused step
+    // a6: potential (Sec. 3.4), one sweep inside the fused step (l has its
+    // own layout phase, io.lph)
     {
         const T tau_l = FAST ? T(3) * sig + T(0.5) : sig / cs2<T>() + T(0.5);
         const T om = T(1) / tau_l;
@@ -773,17 +899,19 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                 post = PS.l(i) + om * (leq - PS.l(i));
             else
                 post = PS.l(i) - (PS.l(i) - leq) / tau_l;
-            const int yt = y + CY5[i];
-            if (EDGE && (yt < 0 || yt >= ny)) {   // electrodes: anti-bounce-back
-                const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-                Pol<S, T>::st_sr(io.l_out + (OPP5[i] * P + k), -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]],
-                                 sh.l_scale, bits13(rb, i));
-            } else {
-                if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-                Pol<S, T>::st_sr(io.l_out + (i * P + dest(i, CX5[i], CY5[i])), post, ro.l[i], sh.l_scale,
-                                 bits13(rb, i));
+            bool wall;
+            const uint32_t d = aa_dst<5, EDGE>(io.lph, i, P, pitch, x, y, xm, xp, ny, wall);
+            T val = post;
+            if (wall) {                           // electrodes: anti-bounce-back
+                const T phiw = (y + CY5[i] < 0) ? c.phi_bot : c.phi_top;
+                val = -post + T(2) * w5<T>(i) * phiw;
             }
+            T ref = T(0);
+            if constexpr (Pol<S, T>::shifted) {
+                make_refs<S, T>(ro, sh, c, wall ? y : y + CY5[i], ny);
+                ref = wall ? ro.l[OPP5[i]] : ro.l[i];
+            }
+            Pol<S, T>::st_sr(io.l + d, val, ref, sh.l_scale, bits13(rb, i));
         }
     }
     // previous-step fields for the next step
@@ -799,45 +927,74 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
 }
 
 
+// One 32 x BY tile at (x0, y0) from layout phase PH (l: io.lph).
 // ASYNC: the own cell's populations reach the stash by cp.async while the
 // ring cell's loads are in flight (single-instance kernels; the batched
 // kernel's extra live state would spill with it).
-template <typename S, typename T, typename A, int BY, bool ASYNC = false, typename OB = NoObs>
+template <typename S, typename T, typename A, int BY, int PH, bool ASYNC = false, typename OB = NoObs>
 __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Consts<T> &c,
                                           const Shift &sh, TileSmem<T, BY> &sm, T (*stash)[BY][32], int x0,
                                           int y0, OB *ob = nullptr) {
+    constexpr bool OBS = !std::is_same<OB, NoObs>::value;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
     const int nx = io.nx, ny = io.ny;
     const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
+    const uint32_t pitch = (uint32_t)io.pitch;
 
-    const int xg = x0 + tx, y = y0 + ty;
-    const bool own = (xg < nx) && (y < ny);
-    const int x = xg < nx ? xg : xg % nx;       // wrapped slot of a ragged tile
-    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
+    // columns of this tile: 32, or fewer on a ragged last tile, where the
+    // lane right after the last column holds the wrap-around neighbour x = 0
+    const int ncols = nx - x0 < 32 ? nx - x0 : 32;
+    const int y = y0 + ty;
+    const bool own = tx < ncols && y < ny;
+    const bool wrap = tx == ncols && y < ny;     // only when ncols < 32
+    const int x = own ? x0 + tx : 0;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const uint32_t k = (uint32_t)y * pitch + (uint32_t)x;
+    const bool edge = ty == 0 || ty == BY - 1 || y == ny - 1 || tx == 0 || tx == ncols - 1;
     Macro<T> m;
     T fs_prev = T(0), mdot_prev = T(0), Q_prev = T(0), pux_prev = T(0), puy_prev = T(0);
     constexpr int NRING = 2 * 34 + 2 * BY;
     static_assert(NRING <= 32 * BY, "one ring cell per thread at most");
+    // the ring slot of this thread, if any: rows beyond a wall are ghosts,
+    // and on a ragged tile only columns up to the wrap-around one are used
+    int rex = 0, rey = 0, rhx = 0, rhy = 0;
+    bool ring = false;
+    if (tid < NRING) {
+        ring_slot<BY>(tid, rex, rey);
+        rhy = y0 - 1 + rey;
+        // x0 - 1 + ex lies in [-1, nx]: -1 and nx wrap around
+        const int hx = x0 - 1 + rex;
+        rhx = hx < 0 ? hx + nx : (hx >= nx ? hx - nx : hx);
+        ring = rhy >= 0 && rhy < ny && rex <= ncols + 1;
+    }
     if constexpr (ASYNC && std::is_same<S, T>::value && std::is_same<typename FStore<S>::type, S>::value) {
         // ---- phase 1, FP32/FP64: the own cells' populations go straight
-        // from global to the stash (cp.async, no registers; each warp copies
-        // its row in 16-byte chunks), the ring cell's loads are issued
-        // meanwhile, so both wait for memory once
+        // from global to the stash (cp.async, no registers), the ring cell's
+        // loads are issued meanwhile, so both wait for memory once
         T pv = T(0), Sv = T(0);
-        if (y < ny) {
-            if (x0 + 32 <= nx) {
-                stash_row_async<T, BY>(stash, ty, tx, io.f_in, io.l_in, P,
-                                       (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x0);
-            } else {          // ragged last tile: wrapped slots, one element each
+        if (own) {
+            if (PH == 0 && ncols == 32) {
+                // natural layout, full row: each warp copies its row in
+                // 16-byte chunks (l_1..4 gathered if l is swapped)
+                stash_row_async<T, BY>(stash, ty, tx, io.f, io.l, P, (uint32_t)y * pitch + (uint32_t)x0,
+                                       io.lph == 0);
+                if (io.lph != 0) {
+#pragma unroll
+                    for (int i = 1; i < 5; i++)
+                        cp_async_elem(&stash[27 + i][ty][tx], io.l + aa_src<5>(1, i, P, pitch, x, y, xm, xp, ny));
+                }
+            } else {          // swapped layout or ragged tile: one element each
 #pragma unroll
                 for (int i = 0; i < 9; i++) {
-                    cp_async_elem(&stash[i][ty][tx], io.f_in + (i * P + k));
-                    cp_async_elem(&stash[9 + i][ty][tx], io.h_in + (i * P + k));
-                    cp_async_elem(&stash[18 + i][ty][tx], io.g_in + (i * P + k));
+                    const uint32_t o9 = aa_src<9>(PH, i, P, pitch, x, y, xm, xp, ny);
+                    cp_async_elem(&stash[i][ty][tx], io.f + o9);
+                    cp_async_elem(&stash[9 + i][ty][tx], io.h + o9);
+                    cp_async_elem(&stash[18 + i][ty][tx], io.g + o9);
                 }
 #pragma unroll
-                for (int i = 0; i < 5; i++) cp_async_elem(&stash[27 + i][ty][tx], io.l_in + (i * P + k));
+                for (int i = 0; i < 5; i++)
+                    cp_async_elem(&stash[27 + i][ty][tx], io.l + aa_src<5>(io.lph, i, P, pitch, x, y, xm, xp, ny));
             }
             pux_prev = T(io.aux_in[AUX_PUX * P + k]);
             puy_prev = T(io.aux_in[AUX_PUY * P + k]);
@@ -847,24 +1004,12 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             pv = T(io.aux_in[AUX_P * P + k]);
             Sv = T(io.aux_in[AUX_S * P + k]);
         }
-        // the ring cell of this thread, if any
-        int rex = 0, rey = 0;
-        bool ring = false;
         CellLoad<T> rl;
         T rp = T(0), rS = T(0);
-        if (tid < NRING) {
-            ring_slot<BY>(tid, rex, rey);
-            const int hy = y0 - 1 + rey;
-            // x0 - 1 + ex lies in [-1, nx + 32]: beyond nx only on a ragged last tile
-            int hx = x0 - 1 + rex;
-            hx = hx < 0 ? hx + nx : (hx >= nx ? (hx - nx < nx ? hx - nx : (hx - nx) % nx) : hx);
-            ring = hy >= 0 && hy < ny;
-            if (ring)
-                load_ring_cell<S, T, A>(io, c, sh, P, (uint32_t)hy * (uint32_t)io.pitch + (uint32_t)hx, hy, rl, rp, rS);
-        }
-        if (y < ny) {
+        if (ring) load_cell_aa<S, T, A, PH>(io, c, sh, rhx, rhy, rl, rp, rS);
+        if (own) {
             cp_async_wait_all();
-            __syncwarp();     // the row's planes were copied by the whole warp
+            if (ncols == 32) __syncwarp();   // a full row's planes were copied by the whole warp
             T f[9], g[9];
 #pragma unroll
             for (int i = 0; i < 9; i++) {
@@ -878,33 +1023,34 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
             sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
             sm.ps[ty + 1][tx + 1] = {pv, Sv};
-            if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ty + 1, tx + 1, m);
+            if (edge) publish_cell<S, T, A, OBS>(io, k, m);
+            if constexpr (OBS) ob->macro(ty + 1, tx + 1, m);
         }
         if (ring) {
             Macro<T> mr;
-            local_macros<T>(rl.f, rl.g, rl.l1234, rl.fs_prev, rl.mdot_prev, rl.Q_prev, c, mr);
+            resolve_ext<S, T, A, BY, OBS>(io, c, rhx, rhy, rl, mr);
             sm.q[rey][rex] = {mr.psi, mr.rho, mr.eps, mr.phi};
             sm.ps[rey][rex] = {rp, rS};
-            if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(rey, rex, mr);
+            if constexpr (OBS) ob->macro(rey, rex, mr);
         }
-        __syncthreads();
     } else {
         // ---- phase 1: own cell (kept in registers) -------------------------
         Refs<T> rf;
         T f[9], g[9], l[5], h[9];
         const float fsc = 1.0f / sh.f_scale, gsc = 1.0f / sh.g_scale, lsc = 1.0f / sh.l_scale;
         const float hsc = 1.0f / sh.h_scale;
-        if (y < ny) {
+        if (own) {
             make_refs<S, T>(rf, sh, c, y, ny);
 #pragma unroll
             for (int i = 0; i < 9; i++) {
-                f[i] = Pol<typename FStore<S>::type, T>::ld(io.f_in + (i * P + k), rf.f[i], fsc);
-                g[i] = Pol<S, T>::ld(io.g_in + (i * P + k), rf.g[i], gsc);
+                const uint32_t o9 = aa_src<9>(PH, i, P, pitch, x, y, xm, xp, ny);
+                f[i] = Pol<typename FStore<S>::type, T>::ld(io.f + o9, rf.f[i], fsc);
+                g[i] = Pol<S, T>::ld(io.g + o9, rf.g[i], gsc);
+                h[i] = Pol<S, T>::ld(io.h + o9, T(0), hsc);
             }
 #pragma unroll
-            for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(io.l_in + (i * P + k), rf.l[i], lsc);
-#pragma unroll
-            for (int i = 0; i < 9; i++) h[i] = Pol<S, T>::ld(io.h_in + (i * P + k), T(0), hsc);
+            for (int i = 0; i < 5; i++)
+                l[i] = Pol<S, T>::ld(io.l + aa_src<5>(io.lph, i, P, pitch, x, y, xm, xp, ny), rf.l[i], lsc);
             pux_prev = T(io.aux_in[AUX_PUX * P + k]);
             puy_prev = T(io.aux_in[AUX_PUY * P + k]);
             fs_prev = T(io.aux_in[AUX_FS * P + k]);
@@ -925,31 +1071,26 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             for (int i = 0; i < 5; i++) stash[27 + i][ty][tx] = l[i];
             sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
             sm.ps[ty + 1][tx + 1] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
-            if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ty + 1, tx + 1, m);
+            if (edge) publish_cell<S, T, A, OBS>(io, k, m);
+            if constexpr (OBS) ob->macro(ty + 1, tx + 1, m);
         }
-
-        // ---- phase 1: halo ring, recomputed from the neighbours' populations
-        for (int r = tid; r < NRING; r += 32 * BY) {
-            int ex, ey;
-            ring_slot<BY>(r, ex, ey);
-            const int hy = y0 - 1 + ey;
-            if (hy < 0 || hy >= ny) continue;
-            // x0 - 1 + ex lies in [-1, nx + 32]: beyond nx only on a ragged last tile
-            int hx = x0 - 1 + ex;
-            hx = hx < 0 ? hx + nx : (hx >= nx ? (hx - nx < nx ? hx - nx : (hx - nx) % nx) : hx);
-            cell_to_smem<S, T, A, BY>(io, c, sh, sm, ex, ey, hx, hy, ob);
-        }
-        __syncthreads();
+        // ---- phase 1: halo ring, from the neighbours' populations or records
+        if (ring) ext_to_smem<S, T, A, BY, PH, OB>(io, c, sh, sm, rex, rey, rhx, rhy, ob);
     }
-
+    // the wrap-around neighbour of a ragged tile's last column
+    if (wrap) ext_to_smem<S, T, A, BY, PH, OB>(io, c, sh, sm, tx + 1, ty + 1, 0, y, ob);
+    __syncthreads();
+    // the tile's records are stored: publish, then (after the barrier) write
+    if (tid == 0)
+        publish_flag(io.tflag + (uint32_t)(y0 / BY) * (uint32_t)io.tiles_x + (uint32_t)(x0 >> 5), io.epoch);
     fill_ghosts<T, BY>(sm, c, y0, ny, tid);
     __syncthreads();
     if (!own) return;
     const StashPops<T, BY> PS{stash, ty, tx};
     if (y0 == 0 || y0 + BY >= ny)
-        step_cell<S, T, A, BY, true>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
+        step_cell<S, T, A, BY, true, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
     else
-        step_cell<S, T, A, BY, false>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
+        step_cell<S, T, A, BY, false, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
 }
 
 // Blocks per SM the single-precision step asks the register allocator for:
@@ -962,256 +1103,31 @@ constexpr int step_min_blocks() {
 template <typename T, int BY>
 constexpr size_t stash_bytes() { return size_t(NPOP) * BY * 32 * sizeof(T); }
 
-// Opt a step kernel into its dynamic shared memory once per process.
+// Opt a kernel into its dynamic shared memory once per device: `done` holds
+// one bit per device ordinal (the attribute is per device), so handles on
+// several GPUs and threads holding different handles are served.
 template <typename K>
-inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes, bool &done) {
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) done = true;
+inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
     return e;
 }
 
-// Half storage: this step's stochastic rounding used counter rng[cur]; the
-// next step (parities flipped) reads rng[cur ^ 1], which no thread of this
-// step reads, so one thread per instance can write it.
-template <typename S, typename T, typename A>
-__device__ __forceinline__ void sr_advance(unsigned int *rng, int cur, const StepIO<S, T, A> &io, bool leader) {
-    if constexpr (Pol<S, T>::shifted) {
-        if (leader && rng) rng[cur ^ 1] = io.sr_step + 1u;
-    }
-}
-template <typename S, typename T, typename A>
-__device__ __forceinline__ void sr_advance(const DevState &s, int cur, const StepIO<S, T, A> &io, bool leader) {
-    sr_advance(s.rng, cur, io, leader);
-}
-
-// io: step_io() of this launch's parities, resolved on the host; rng, cur:
-// the stochastic-rounding counters and the population parity (half storage).
-template <typename S, typename T, typename A, int BY>
+// io: step_io() of this launch's parities, resolved on the host (PH = cur).
+template <typename S, typename T, typename A, int BY, int PH>
 __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
-    k_step(StepIO<S, T, A> io, unsigned int *rng, int cur, Consts<T> c, Shift sh) {
+    k_step(StepIO<S, T, A> io, Consts<T> c, Shift sh) {
     __shared__ TileSmem<T, BY> sm;
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
-    load_sr_step(io, rng, cur);
-    sr_advance(rng, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
-    step_tile<S, T, A, BY, true>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
-}
-
-// ---------------------------------------------------------------------------
-// TMA form of the step.  One thread issues three 3-D tensor loads that bring
-// the tile and its one-cell halo, for all 32 population planes and the 7
-// auxiliary planes, into shared memory (completion tracked by an mbarrier);
-// the cells then read their populations from shared memory, so no global
-// load sits in a thread's register file and the halo needs no second pass.
-// The box starts 16 bytes left of the tile so its x origin is aligned; the
-// out-of-range columns that the periodic wrap needs (x = -1 and x = nx) are
-// filled from the opposite edge with plain loads.
-// ---------------------------------------------------------------------------
-template <typename S, typename A, int BY>
-struct TmaGeom {
-    static constexpr int PADX = 16 / int(sizeof(S));   // box x origin = x0 - PADX (16-byte aligned)
-    static constexpr int BW = 32 + 2 * PADX;             // box width (population planes)
-    static constexpr int PADA = 16 / int(sizeof(A));
-    static constexpr int BWA = 32 + 2 * PADA;            // box width (auxiliary planes)
-    static constexpr int BH = BY + 2;                    // box height
-    static constexpr int PL = BW * BH;                   // elements per population plane
-    static constexpr int PLA = BWA * BH;                 // elements per auxiliary plane
-    static constexpr size_t fhg_bytes = size_t(PL) * NFHG * sizeof(S);
-    static constexpr size_t l_bytes = size_t(PL) * (NPOP - NFHG) * sizeof(S);
-    static constexpr size_t aux_bytes = size_t(PLA) * NAUX * sizeof(A);
-    static constexpr size_t l_off = (fhg_bytes + 127) / 128 * 128;
-    static constexpr size_t aux_off = (l_off + l_bytes + 127) / 128 * 128;
-    static constexpr size_t total = aux_off + aux_bytes;
-    static constexpr uint32_t tx_bytes = uint32_t(fhg_bytes + l_bytes + aux_bytes);
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
-}
-// Bounded wait on phase `parity`: true once complete, false after the limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, int limit) {
-    for (int it = 0; it < limit; it++) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(mb), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *map, int c0, int c1, int c2, uint32_t mb) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mb)
-        : "memory");
-}
-
-// Populations of one cell read from the shared-memory box.
-template <typename S, typename T>
-struct BoxPops {
-    const S *f_;   // plane 0 of f at the cell
-    const S *l_;   // plane 0 of l at the cell
-    int pl;        // elements per plane
-    Refs<T> rf;
-    float fsc, gsc, hsc, lsc;
-    __device__ __forceinline__ T f(int i) const { return Pol<S, T>::ld(f_ + i * pl, rf.f[i], fsc); }
-    __device__ __forceinline__ T h(int i) const { return Pol<S, T>::ld(f_ + (9 + i) * pl, T(0), hsc); }
-    __device__ __forceinline__ T g(int i) const { return Pol<S, T>::ld(f_ + (18 + i) * pl, rf.g[i], gsc); }
-    __device__ __forceinline__ T l(int i) const { return Pol<S, T>::ld(l_ + i * pl, rf.l[i], lsc); }
-};
-
-constexpr int TMA_WAIT_LIMIT = 1 << 22;   // try_wait rounds before the step gives up
-
-template <typename S, typename T, typename A, int BY>
-__device__ __forceinline__ void step_tile_tma(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
-                                              TileSmem<T, BY> &sm, unsigned char *dsm, unsigned long long *mbar,
-                                              const void *mF, const void *mL, const void *mA, int x0, int y0,
-                                              unsigned int *err) {
-    using G = TmaGeom<S, A, BY>;
-    __shared__ int s_ok;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * 32 + tx;
-    const int nx = io.nx, ny = io.ny;
-    const long long P = io.plane;
-    // tensor-copy destinations must be 128-byte aligned; the launch
-    // requests 128 bytes of slack for this
-    unsigned char *base = dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u);
-    S *bF = reinterpret_cast<S *>(base);
-    S *bL = reinterpret_cast<S *>(base + G::l_off);
-    A *bA = reinterpret_cast<A *>(base + G::aux_off);
-    const uint32_t mb = smem_u32(mbar);
-    if (tid == 0) mbar_init(mb, 1);
-    __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(mb, G::tx_bytes);
-        tma_load_3d(smem_u32(bF), mF, x0 - G::PADX, y0 - 1, 0, mb);
-        tma_load_3d(smem_u32(bL), mL, x0 - G::PADX, y0 - 1, 0, mb);
-        tma_load_3d(smem_u32(bA), mA, x0 - G::PADA, y0 - 1, 0, mb);
-        s_ok = mbar_wait(mb, 0, TMA_WAIT_LIMIT) ? 1 : 0;
-    }
-    __syncthreads();
-    if (!s_ok) {
-        // report, then let the copies in flight land (bounded) before the
-        // block's shared memory is released
-        if (tid == 0) {
-            atomicOr(err, 1u);
-            mbar_wait(mb, 0, TMA_WAIT_LIMIT);
-        }
-        return;
-    }
-    mbar_wait(mb, 0, TMA_WAIT_LIMIT);      // complete: acquire the bytes for this thread
-
-    // periodic wrap: box columns of x = -1 and x = nx come from the far edge
-    {
-        // only the first tile holds x = -1 and only the last one x = nx; the
-        // latter sits at box column nx - x0 + pad <= 32 + pad < box width
-        const bool first = (x0 == 0), last = (nx - x0) <= 32;
-        const int nfix = (NPOP + NAUX) * G::BH;
-        for (int side = 0; side < 2; side++) {
-            if (side == 0 ? !first : !last) continue;
-            const int col = side == 0 ? G::PADX - 1 : nx - x0 + G::PADX;
-            const int cola = side == 0 ? G::PADA - 1 : nx - x0 + G::PADA;
-            const int srcx = side == 0 ? nx - 1 : 0;
-            for (int t = tid; t < nfix; t += 32 * BY) {
-                const int q = t / G::BH, r = t % G::BH;
-                const int yy = y0 - 1 + r;
-                if (yy < 0 || yy >= ny) continue;
-                const long long kk = (long long)yy * io.pitch + srcx;
-                if (q < NFHG)
-                    bF[q * G::PL + r * G::BW + col] = io.f_in[q * P + kk];   // uniform storage: f, h, g contiguous
-                else if (q < NPOP)
-                    bL[(q - NFHG) * G::PL + r * G::BW + col] = io.l_in[(q - NFHG) * P + kk];
-                else
-                    bA[(q - NPOP) * G::PLA + r * G::BWA + cola] = io.aux_in[(q - NPOP) * P + kk];
-            }
-        }
-    }
-    __syncthreads();
-
-    const float fsc = 1.0f / sh.f_scale, gsc = 1.0f / sh.g_scale, lsc = 1.0f / sh.l_scale;
-    const float hsc = 1.0f / sh.h_scale;
-    // macros of one extended-tile cell (ex, ey) from the box
-    auto ext_macros = [&](int ex, int ey, int yy, Macro<T> &mm, T &fs_p) {
-        const int o = ey * G::BW + ex - 1 + G::PADX;
-        const int oa = ey * G::BWA + ex - 1 + G::PADA;
-        BoxPops<S, T> bp{bF + o, bL + o, G::PL, {}, fsc, gsc, hsc, lsc};
-        make_refs<S, T>(bp.rf, sh, c, yy, ny);
-        T f[9], g[9];
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            f[i] = bp.f(i);
-            g[i] = bp.g(i);
-        }
-        T l1234 = T(0);
-#pragma unroll
-        for (int i = 1; i < 5; i++) l1234 += bp.l(i);
-        fs_p = T(bA[AUX_FS * G::PLA + oa]);
-        local_macros(f, g, l1234, fs_p, T(bA[AUX_MDOT * G::PLA + oa]), T(bA[AUX_Q * G::PLA + oa]), c, mm);
-        sm.q[ey][ex] = {mm.psi, mm.rho, mm.eps, mm.phi};
-        sm.ps[ey][ex] = {T(bA[AUX_P * G::PLA + oa]), T(bA[AUX_S * G::PLA + oa])};
-    };
-
-    // ---- phase 1: own cell, then the halo ring --------------------------
-    const int xg = x0 + tx, y = y0 + ty;
-    const bool own = (xg < nx) && (y < ny);
-    Macro<T> m;
-    T fs_prev = T(0);
-    if (y < ny) ext_macros(tx + 1, ty + 1, y, m, fs_prev);
-    constexpr int NRING = 2 * 34 + 2 * BY;
-    for (int r = tid; r < NRING; r += 32 * BY) {
-        int ex, ey;
-        if (r < 34) {
-            ex = r; ey = 0;
-        } else if (r < 68) {
-            ex = r - 34; ey = BY + 1;
-        } else if (r < 68 + BY) {
-            ex = 0; ey = r - 68 + 1;
-        } else {
-            ex = 33; ey = r - 68 - BY + 1;
-        }
-        const int hy = y0 - 1 + ey;
-        if (hy < 0 || hy >= ny) continue;
-        Macro<T> mr;
-        T fsr;
-        ext_macros(ex, ey, hy, mr, fsr);
-    }
-    __syncthreads();
-    fill_ghosts<T, BY>(sm, c, y0, ny, tid);
-    __syncthreads();
-    if (!own) return;
-    const int o = (ty + 1) * G::BW + tx + G::PADX;
-    const int oa = (ty + 1) * G::BWA + tx + G::PADA;
-    BoxPops<S, T> PS{bF + o, bL + o, G::PL, {}, fsc, gsc, hsc, lsc};
-    make_refs<S, T>(PS.rf, sh, c, y, ny);
-    const T pxp = T(bA[AUX_PUX * G::PLA + oa]), pyp = T(bA[AUX_PUY * G::PLA + oa]);
-    if (y0 == 0 || y0 + BY >= ny)
-        step_cell<S, T, A, BY, true>(io, c, sh, sm, PS, tx, ty, xg, y, m, fs_prev, pxp, pyp);
-    else
-        step_cell<S, T, A, BY, false>(io, c, sh, sm, PS, tx, ty, xg, y, m, fs_prev, pxp, pyp);
-}
-
-template <typename S, typename T, typename A, int BY>
-__global__ void __launch_bounds__(32 * BY) k_step_tma(DevState s, int cur, int lcur, int write_sigma, Consts<T> c,
-                                                      Shift sh, const __grid_constant__ CUtensorMap mF,
-                                                      const __grid_constant__ CUtensorMap mL,
-                                                      const __grid_constant__ CUtensorMap mA) {
-    extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ TileSmem<T, BY> sm;
-    __shared__ __align__(8) unsigned long long mbar;
-    const StepIO<S, T, A> io = make_io<S, T, A>(s, cur, lcur, write_sigma);
-    sr_advance(s, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
-    step_tile_tma<S, T, A, BY>(io, c, sh, sm, dsm, &mbar, &mF, &mL, &mA, blockIdx.x * 32, blockIdx.y * BY, s.err);
+    load_counters(io, PH);
+    advance_counters(io, PH, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
+    step_tile<S, T, A, BY, PH, true>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
 }
 
 // Batched form: blocks walk a flat list of tiles of many instances.  The
@@ -1247,22 +1163,29 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_batch_ste
         const BatchItem &it = items[item];
         const int local = t - it.tile_begin;
         const int bx = local % it.tiles_x, by = local / it.tiles_x;
-        const StepIO<S, T, A> io = make_io<S, T, A>(it.s, it.cur ^ flip_cur, it.lcur ^ flip_l, it.write_sigma);
-        sr_advance(it.s, it.cur ^ flip_cur, io, local == 0 && tid == 0);
-        step_tile<S, T, A, BY>(io, s_c, it.sh, sm, stash, bx * 32, by * BY);
+        const int cur = it.cur ^ flip_cur;
+        StepIO<S, T, A> io = step_io<S, T, A>(it.s, cur, it.lcur ^ flip_l, it.write_sigma);
+        load_counters(io, cur);
+        advance_counters(io, cur, local == 0 && tid == 0);
+        if (cur)
+            step_tile<S, T, A, BY, 1>(io, s_c, it.sh, sm, stash, bx * 32, by * BY);
+        else
+            step_tile<S, T, A, BY, 0>(io, s_c, it.sh, sm, stash, bx * 32, by * BY);
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
 // Extra potential sweeps (k_e > 1 and the pre-solve): D2Q5 collide with sigma
-// frozen at time n, push-stream, anti-bounce-back at the electrodes.
+// frozen at time n, streamed in place from layout phase lph, anti-bounce-back
+// at the electrodes.  Purely local: no halo, so no publication is needed.
 // ---------------------------------------------------------------------------
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void sweep_cell(const S *l_in, S *l_out, const A *sigma, int nx, int ny,
-                                           int pitch, long long P, const Consts<T> &c, const Shift &sh,
-                                           int x, int y, uint32_t sr_step, uint32_t sr_sys) {
-    const long long k = (long long)y * pitch + x;
+__device__ __forceinline__ void sweep_cell(S *l, const A *sigma, int nx, int ny, int pitch, uint32_t P,
+                                           const Consts<T> &c, const Shift &sh, int x, int y, int lph,
+                                           uint32_t sr_step, uint32_t sr_sys) {
+    const uint32_t k = (uint32_t)y * (uint32_t)pitch + (uint32_t)x;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     // half storage rounds stochastically here too: rounding to nearest would
     // stall the relaxation once a sweep changes phi by less than half a
     // spacing (sr_sys keeps every sweep's bits apart from the step's)
@@ -1271,44 +1194,46 @@ __device__ __forceinline__ void sweep_cell(const S *l_in, S *l_out, const A *sig
     Refs<T> rf, ro;
     make_refs<S, T>(rf, sh, c, y, ny);
     const float lsc = 1.0f / sh.l_scale;
-    T l[5];
+    T lv[5];
 #pragma unroll
-    for (int i = 0; i < 5; i++) l[i] = Pol<S, T>::ld(l_in + i * P + k, rf.l[i], lsc);
+    for (int i = 0; i < 5; i++)
+        lv[i] = Pol<S, T>::ld(l + aa_src<5>(lph, i, P, (uint32_t)pitch, x, y, xm, xp, ny), rf.l[i], lsc);
     T sl = T(0);
 #pragma unroll
-    for (int i = 1; i < 5; i++) sl += l[i];
+    for (int i = 1; i < 5; i++) sl += lv[i];
     const T phi = sl / (T(1) - w5<T>(0));
     const T tau_l = T(sigma[k]) / cs2<T>() + T(0.5);
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         const T leq = (i == 0) ? (w5<T>(0) - T(1)) * phi : w5<T>(i) * phi;
-        const T post = l[i] - (l[i] - leq) / tau_l;
-        const int yt = y + CY5[i];
-        if (yt < 0 || yt >= ny) {
-            const T phiw = (yt < 0) ? c.phi_bot : c.phi_top;
-            if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, y, ny);
-            Pol<S, T>::st_sr(l_out + OPP5[i] * P + k, -post + T(2) * w5<T>(i) * phiw, ro.l[OPP5[i]], sh.l_scale,
-                             bits13(rb, i));
-        } else {
-            if constexpr (Pol<S, T>::shifted) make_refs<S, T>(ro, sh, c, yt, ny);
-            Pol<S, T>::st_sr(l_out + i * P + (long long)yt * pitch + wrapx<T>(x + CX5[i], nx), post, ro.l[i],
-                             sh.l_scale, bits13(rb, i));
+        const T post = lv[i] - (lv[i] - leq) / tau_l;
+        bool wall;
+        const uint32_t d = aa_dst<5, true>(lph, i, P, (uint32_t)pitch, x, y, xm, xp, ny, wall);
+        T val = post;
+        if (wall) {
+            const T phiw = (y + CY5[i] < 0) ? c.phi_bot : c.phi_top;
+            val = -post + T(2) * w5<T>(i) * phiw;
         }
+        T ref = T(0);
+        if constexpr (Pol<S, T>::shifted) {
+            make_refs<S, T>(ro, sh, c, wall ? y : y + CY5[i], ny);
+            ref = wall ? ro.l[OPP5[i]] : ro.l[i];
+        }
+        Pol<S, T>::st_sr(l + d, val, ref, sh.l_scale, bits13(rb, i));
     }
 }
 
-// cur: the population parity, whose rounding counter (half storage) the
-// sweep reads; sr_sys: this sweep's rounding stream.
+// lcur: the layout phase of l; cur: the population parity, whose rounding
+// counter (half storage) the sweep reads; sr_sys: this sweep's rounding stream.
 template <typename S, typename T, typename A>
 __global__ void k_sweep(DevState s, int lcur, int cur, uint32_t sr_sys, Consts<T> c, Shift sh) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= s.nx || y >= s.ny) return;
-    const S *l_in = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], s.plane).l;
-    S *l_out = Planes<S>::at(lcur ? s.pop[0] : s.pop[1], s.plane).l;
+    S *l = Planes<S>::at(s.pop, s.plane).l;
     const uint32_t sr_step = (Pol<S, T>::shifted && s.rng) ? s.rng[cur] : 0u;
-    sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(s.sigma), s.nx, s.ny, s.pitch, s.plane, c,
-                        sh, x, y, sr_step, sr_sys);
+    sweep_cell<S, T, A>(l, reinterpret_cast<const A *>(s.sigma), s.nx, s.ny, s.pitch, (uint32_t)s.plane, c, sh, x, y,
+                        lcur, sr_step, sr_sys);
 }
 
 // Batched potential sweep over the same work list (32 x 8 cells per tile).
@@ -1324,19 +1249,18 @@ __global__ void __launch_bounds__(256) k_batch_sweep(const BatchItem *__restrict
         const int x = (local % it.sweep_tiles_x) * 32 + threadIdx.x;
         const int y = (local / it.sweep_tiles_x) * 8 + threadIdx.y;
         if (x < it.s.nx && y < it.s.ny) {
-            const int lc = it.lcur ^ flip_l;
-            const S *l_in = Planes<S>::at(lc ? it.s.pop[1] : it.s.pop[0], it.s.plane).l;
-            S *l_out = Planes<S>::at(lc ? it.s.pop[0] : it.s.pop[1], it.s.plane).l;
+            S *l = Planes<S>::at(it.s.pop, it.s.plane).l;
             const uint32_t sr_step = (Pol<S, T>::shifted && it.s.rng) ? it.s.rng[it.cur ^ flip_cur] : 0u;
-            sweep_cell<S, T, A>(l_in, l_out, reinterpret_cast<const A *>(it.s.sigma), it.s.nx, it.s.ny,
-                                it.s.pitch, it.s.plane, consts[ii], it.sh, x, y, sr_step, sr_sys);
+            sweep_cell<S, T, A>(l, reinterpret_cast<const A *>(it.s.sigma), it.s.nx, it.s.ny, it.s.pitch,
+                                (uint32_t)it.s.plane, consts[ii], it.sh, x, y, it.lcur ^ flip_l, sr_step, sr_sys);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
 // Initial state (Sec. 2): equilibria of a resting droplet at T_init with all
-// latent heat held, linear potential between the electrodes.
+// latent heat held, linear potential between the electrodes; natural layout
+// (phase 0).
 // ---------------------------------------------------------------------------
 template <typename S, typename T, typename A>
 __global__ void k_init(DevState s, const double *psi_dev, double R, double xc, double yc, double W,
@@ -1361,7 +1285,7 @@ __global__ void k_init(DevState s, const double *psi_dev, double R, double xc, d
     const T rho0 = chi(T(0), ps, c.rho);
     Refs<T> rf;
     make_refs<S, T>(rf, sh, c, y, s.ny);
-    const Planes<S> pl = Planes<S>::at(s.pop[0], P);
+    const Planes<S> pl = Planes<S>::at(s.pop, P);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         const T feq = w9<T>(i) * ps * (T(1) + T(0) / cs2<T>());

@@ -13,7 +13,7 @@ namespace lbm {
 template <typename S, typename T, typename A, int BY>
 int batch_blocks_per_sm_by() {
     int n = 0;
-    static bool ready = false;
+    static std::atomic<unsigned long long> ready{0ull};
     if (allow_dynamic_smem(k_batch_step<S, T, A, BY>, stash_bytes<T, BY>(), ready) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<S, T, A, BY>, 32 * BY,
                                                       stash_bytes<T, BY>()) != cudaSuccess)
@@ -34,7 +34,7 @@ int batch_blocks_per_sm_t(int tile_rows) {
 template <typename S, typename T, typename A, int BY>
 cudaError_t launch_batch_step_by(const BatchItem *items, const Consts<T> *c, const int *tile_item, int total_tiles,
                                  int grid, int flip_cur, int flip_l, cudaStream_t st) {
-    static bool ready = false;
+    static std::atomic<unsigned long long> ready{0ull};
     cudaError_t e = allow_dynamic_smem(k_batch_step<S, T, A, BY>, stash_bytes<T, BY>(), ready);
     if (e != cudaSuccess) return e;
     k_batch_step<S, T, A, BY><<<grid, dim3(32, BY), stash_bytes<T, BY>(), st>>>(items, c, tile_item, total_tiles,
@@ -60,6 +60,73 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
     const Consts<T> *c = reinterpret_cast<const Consts<T> *>(consts);
     k_batch_sweep<S, T, A><<<grid, dim3(32, 8), 0, st>>>(items, c, n_items, total_tiles, flip_l, flip_cur, sr_sys);
     return cudaGetLastError();
+}
+
+// The fused step of one instance, tile height BY, from layout phase PH.
+template <typename S, typename T, typename A, int BY, int PH>
+cudaError_t launch_step_ph(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, dim3 grid,
+                           cudaStream_t st) {
+    static std::atomic<unsigned long long> ready{0ull};
+    cudaError_t e = allow_dynamic_smem(k_step<S, T, A, BY, PH>, stash_bytes<T, BY>(), ready);
+    if (e != cudaSuccess) return e;
+    k_step<S, T, A, BY, PH><<<grid, dim3(32, BY), stash_bytes<T, BY>(), st>>>(io, c, sh);
+    return cudaGetLastError();
+}
+
+template <typename S, typename T, typename A, int BY>
+cudaError_t launch_step_by(const DevState &s, int cur, int lcur, int write_sigma, const Consts<T> &c, const Shift &sh,
+                           cudaStream_t st) {
+    const dim3 grid((s.nx + 31) / 32, (s.ny + BY - 1) / BY);
+    const StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);
+    return cur ? launch_step_ph<S, T, A, BY, 1>(io, c, sh, grid, st) : launch_step_ph<S, T, A, BY, 0>(io, c, sh, grid, st);
+}
+
+template <typename S, typename T, typename A>
+cudaError_t launch_step_t(const DevState &s, int cur, int lcur, int write_sigma, const void *consts, const Shift &sh,
+                          int tile_rows, cudaStream_t st) {
+    const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);
+    switch (tile_rows) {
+    case 4: return launch_step_by<S, T, A, 4>(s, cur, lcur, write_sigma, c, sh, st);
+    case 8: return launch_step_by<S, T, A, 8>(s, cur, lcur, write_sigma, c, sh, st);
+    case 16: return launch_step_by<S, T, A, 16>(s, cur, lcur, write_sigma, c, sh, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// The step that also reduces the observables of the state it reads.
+template <typename S, typename T, typename A, int BY, int PH>
+cudaError_t launch_step_obs_ph(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, dim3 grid,
+                               const ObsScratch &w, const Scalars &sc, cudaStream_t st) {
+    static std::atomic<unsigned long long> ready{0ull};
+    cudaError_t e = allow_dynamic_smem(k_step_obs<S, T, A, BY, PH>, stash_bytes<T, BY>(), ready);
+    if (e != cudaSuccess) return e;
+    k_step_obs<S, T, A, BY, PH><<<grid, dim3(32, BY), stash_bytes<T, BY>(), st>>>(io, c, sh, w, sc);
+    return cudaGetLastError();
+}
+
+template <typename S, typename T, typename A, int BY>
+cudaError_t launch_step_obs_by(const DevState &s, int cur, int lcur, int write_sigma, const Consts<T> &c,
+                               const Shift &sh, const ObsScratch &ws, const Scalars &sc, cudaStream_t st) {
+    const dim3 grid((s.nx + 31) / 32, (s.ny + BY - 1) / BY);
+    const StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);
+    ObsScratch w = ws;
+    w.nblocks = (int)(grid.x * grid.y);
+    w.ngroups = (w.nblocks + OBS_GROUP - 1) / OBS_GROUP;
+    return cur ? launch_step_obs_ph<S, T, A, BY, 1>(io, c, sh, grid, w, sc, st)
+               : launch_step_obs_ph<S, T, A, BY, 0>(io, c, sh, grid, w, sc, st);
+}
+
+template <typename S, typename T, typename A>
+cudaError_t launch_step_obs_t(const DevState &s, int cur, int lcur, int write_sigma, const void *consts,
+                              const Shift &sh, int tile_rows, const ObsScratch &ws, const Scalars &sc,
+                              cudaStream_t st) {
+    const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);
+    switch (tile_rows) {
+    case 4: return launch_step_obs_by<S, T, A, 4>(s, cur, lcur, write_sigma, c, sh, ws, sc, st);
+    case 8: return launch_step_obs_by<S, T, A, 8>(s, cur, lcur, write_sigma, c, sh, ws, sc, st);
+    case 16: return launch_step_obs_by<S, T, A, 16>(s, cur, lcur, write_sigma, c, sh, ws, sc, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace lbm
@@ -89,71 +156,7 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
     namespace lbm {                                                                                         \
     cudaError_t launch_step_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,                 \
                                      const void *consts, const Shift &sh, int tile_rows, cudaStream_t st) { \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        dim3 grid((s.nx + 31) / 32, (s.ny + tile_rows - 1) / tile_rows);                                   \
-        const StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);                             \
-        static bool r4 = false, r8 = false, r16 = false;                                                    \
-        cudaError_t e = cudaSuccess;                                                                        \
-        switch (tile_rows) {                                                                                \
-        case 4:                                                                                             \
-            e = allow_dynamic_smem(k_step<S, T, A, 4>, stash_bytes<T, 4>(), r4);                            \
-            if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(io, s.rng, cur, c, sh); \
-            break;                                                                                          \
-        case 8:                                                                                             \
-            e = allow_dynamic_smem(k_step<S, T, A, 8>, stash_bytes<T, 8>(), r8);                            \
-            if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(io, s.rng, cur, c, sh); \
-            break;                                                                                          \
-        case 16:                                                                                            \
-            e = allow_dynamic_smem(k_step<S, T, A, 16>, stash_bytes<T, 16>(), r16);                         \
-            if (e == cudaSuccess)                                                                           \
-                k_step<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(io, s.rng, cur, c, sh); \
-            break;                                                                                          \
-        default: return cudaErrorInvalidValue;                                                              \
-        }                                                                                                   \
-        if (e != cudaSuccess) return e;                                                                     \
-        return cudaGetLastError();                                                                          \
-    }                                                                                                       \
-    size_t tma_smem_##SUFFIX(int tile_rows) {                                                              \
-        switch (tile_rows) {                                                                                \
-        case 4: return TmaGeom<S, A, 4>::total + 128;                                                       \
-        case 8: return TmaGeom<S, A, 8>::total + 128;                                                       \
-        case 16: return TmaGeom<S, A, 16>::total + 128;                                                     \
-        default: return 0;                                                                                  \
-        }                                                                                                   \
-    }                                                                                                       \
-    template <int BY>                                                                                       \
-    static cudaError_t launch_tma_by_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,        \
-                                              const Consts<T> &c, const Shift &sh, const TmaMaps &m,        \
-                                              cudaStream_t st) {                                            \
-        if constexpr (!std::is_same<typename FStore<S>::type, S>::value) {                                  \
-            return cudaErrorNotSupported;         /* the tensor boxes assume one storage type */            \
-        } else {                                                                                            \
-            static bool ready = false;                                                                      \
-            if (!ready) {                                                                                   \
-                cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, T, A, BY>,                               \
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,           \
-                                                     (int)TmaGeom<S, A, BY>::total + 128);                  \
-                if (e != cudaSuccess) return e;                                                             \
-                ready = true;                                                                               \
-            }                                                                                               \
-            dim3 grid((s.nx + 31) / 32, (s.ny + BY - 1) / BY);                                              \
-            k_step_tma<S, T, A, BY><<<grid, dim3(32, BY), TmaGeom<S, A, BY>::total + 128, st>>>(            \
-                s, cur, lcur, write_sigma, c, sh, m.fhg[cur], m.l[lcur], m.aux[cur]);                       \
-            return cudaGetLastError();                                                                      \
-        }                                                                                                   \
-    }                                                                                                       \
-    cudaError_t launch_step_tma_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,             \
-                                         const void *consts, const Shift &sh, const TmaMaps &m,             \
-                                         cudaStream_t st) {                                                 \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        switch (m.by) {                                                                                     \
-        case 4: return launch_tma_by_##SUFFIX<4>(s, cur, lcur, write_sigma, c, sh, m, st);                  \
-        case 8: return launch_tma_by_##SUFFIX<8>(s, cur, lcur, write_sigma, c, sh, m, st);                  \
-        case 16: return launch_tma_by_##SUFFIX<16>(s, cur, lcur, write_sigma, c, sh, m, st);                \
-        default: return cudaErrorInvalidValue;                                                              \
-        }                                                                                                   \
+        return launch_step_t<S, T, A>(s, cur, lcur, write_sigma, consts, sh, tile_rows, st);                \
     }                                                                                                       \
     cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, int cur, uint32_t sr_sys,               \
                                       const void *consts, const Shift &sh, cudaStream_t st) {               \
@@ -180,37 +183,7 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
     cudaError_t launch_step_obs_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,             \
                                          const void *consts, const Shift &sh, int tile_rows,                \
                                          const ObsScratch &ws, const Scalars &sc, cudaStream_t st) {        \
-        const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
-        dim3 grid((s.nx + 31) / 32, (s.ny + tile_rows - 1) / tile_rows);                                   \
-        const StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);                             \
-        ObsScratch w = ws;                                                                                  \
-        w.nblocks = (int)(grid.x * grid.y);                                                                 \
-        w.ngroups = (w.nblocks + OBS_GROUP - 1) / OBS_GROUP;                                                \
-        static bool r4 = false, r8 = false, r16 = false;                                                    \
-        cudaError_t e = cudaSuccess;                                                                        \
-        switch (tile_rows) {                                                                                \
-        case 4:                                                                                             \
-            e = allow_dynamic_smem(k_step_obs<S, T, A, 4>, stash_bytes<T, 4>(), r4);                        \
-            if (e == cudaSuccess)                                                                           \
-                k_step_obs<S, T, A, 4><<<grid, dim3(32, 4), stash_bytes<T, 4>(), st>>>(                     \
-                    io, s.rng, cur, c, sh, w, sc);                                                          \
-            break;                                                                                          \
-        case 8:                                                                                             \
-            e = allow_dynamic_smem(k_step_obs<S, T, A, 8>, stash_bytes<T, 8>(), r8);                        \
-            if (e == cudaSuccess)                                                                           \
-                k_step_obs<S, T, A, 8><<<grid, dim3(32, 8), stash_bytes<T, 8>(), st>>>(                     \
-                    io, s.rng, cur, c, sh, w, sc);                                                          \
-            break;                                                                                          \
-        case 16:                                                                                            \
-            e = allow_dynamic_smem(k_step_obs<S, T, A, 16>, stash_bytes<T, 16>(), r16);                     \
-            if (e == cudaSuccess)                                                                           \
-                k_step_obs<S, T, A, 16><<<grid, dim3(32, 16), stash_bytes<T, 16>(), st>>>(                  \
-                    io, s.rng, cur, c, sh, w, sc);                                                          \
-            break;                                                                                          \
-        default: return cudaErrorInvalidValue;                                                              \
-        }                                                                                                   \
-        if (e != cudaSuccess) return e;                                                                     \
-        return cudaGetLastError();                                                                          \
+        return launch_step_obs_t<S, T, A>(s, cur, lcur, write_sigma, consts, sh, tile_rows, ws, sc, st);    \
     }                                                                                                       \
     cudaError_t launch_heat_flux_##SUFFIX(const DevState &s, int cur, int lcur, const void *consts,        \
                                           const Shift &sh, double *out, cudaStream_t st) {                  \
@@ -225,11 +198,20 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
         k_get<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, field, c, sh, out);                      \
         return cudaGetLastError();                                                                          \
     }                                                                                                       \
-    cudaError_t launch_phi_change_##SUFFIX(const DevState &s, int la, int lb, const void *consts,         \
-                                           const Shift &sh, unsigned long long *out, cudaStream_t st) {     \
+    cudaError_t launch_phi_snap_##SUFFIX(const DevState &s, int lcur, const void *consts, const Shift &sh, \
+                                         void *snap, cudaStream_t st) {                                     \
         const Consts<double> &c = *reinterpret_cast<const Consts<double> *>(consts);                      \
         dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
-        k_phi_change<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, la, lb, c, sh, out);                         \
+        k_phi_snap<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, lcur, c, sh, reinterpret_cast<A *>(snap));     \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
+    cudaError_t launch_phi_change_##SUFFIX(const DevState &s, int lcur, const void *consts,                \
+                                           const Shift &sh, const void *snap, unsigned long long *out,      \
+                                           cudaStream_t st) {                                               \
+        const Consts<double> &c = *reinterpret_cast<const Consts<double> *>(consts);                      \
+        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
+        k_phi_change<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, lcur, c, sh, reinterpret_cast<const A *>(snap), \
+                                                            out);                                           \
         return cudaGetLastError();                                                                          \
     }                                                                                                       \
     cudaError_t launch_set_##SUFFIX(const DevState &s, int cur, int lcur, int field, const void *consts,   \

@@ -30,11 +30,9 @@ constexpr size_t kScratchBytes = kPartBytes + kMaxvBytes + kMinvBytes + kU32Byte
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void *g_scratch_dev[kMaxDevices] = {};   // device address of the array, per device
+void *g_scratch_dev[kMaxDevices] = {};   // last looked-up device address of the array, per device
 
 }  // namespace
-
-
 
 // The scratch array.  In host code this name is only a stand-in for the
 // symbol: its device address comes from cudaGetSymbolAddress below.
@@ -42,9 +40,12 @@ static __device__ __align__(256) unsigned char g_obs_scratch[kScratchBytes];
 
 namespace {
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
-int scratch_address(void **out) {
+// Device address of the scratch array on the current device.  The address is
+// looked up on every call (a device reset or a new primary context reloads
+// the module, which moves the array); only while `st` is being captured into
+// a graph, where a lookup could load a module, the value of the last lookup
+// on this device is used, and a capture before any lookup is refused.
+int scratch_address(cudaStream_t st, void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -55,17 +56,29 @@ int scratch_address(void **out) {
         lbm::set_last_error("device ordinal beyond the supported range");
         return LBM_ERR_CUDA;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) {
+        lbm::set_last_error(std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_dev[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_obs_scratch);
-        if (e != cudaSuccess || !p) {
-            lbm::set_last_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    if (cs != cudaStreamCaptureStatusNone) {
+        if (!g_scratch_dev[dev]) {
+            lbm::set_last_error("the first call on a device must come before any stream capture");
             return LBM_ERR_CUDA;
         }
-        g_scratch_dev[dev] = p;
+        *out = g_scratch_dev[dev];
+        return LBM_OK;
     }
-    *out = g_scratch_dev[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_obs_scratch);
+    if (e != cudaSuccess || !p) {
+        lbm::set_last_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    g_scratch_dev[dev] = p;
+    *out = p;
     return LBM_OK;
 }
 
@@ -95,8 +108,18 @@ extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, con
         set_last_error("pitch must be at least nx");
         return LBM_ERR_BADPARAM;
     }
+    // the kernel reads every plane element by element: both arrays must be
+    // aligned to the widest element they hold, and so must the result
+    const uintptr_t pop_align = p->precision == LBM_FP64 ? 8 : 4, aux_align = pop_align;
+    if (reinterpret_cast<uintptr_t>(pop) % pop_align || reinterpret_cast<uintptr_t>(aux) % aux_align ||
+        reinterpret_cast<uintptr_t>(out) % alignof(lbm_obs)) {
+        set_last_error("pop, aux and out must be aligned to their element size (8 bytes for FP64 and lbm_obs, "
+                       "4 for FP32 and half storage)");
+        return LBM_ERR_BADPARAM;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     void *base = nullptr;
-    int rc = scratch_address(&base);
+    int rc = scratch_address(st, &base);
     if (rc != LBM_OK) return rc;
 
     unsigned char *b = static_cast<unsigned char *>(base);
@@ -113,11 +136,14 @@ extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, con
     ws.nblocks = nblocks;
 
     DevState s;
-    s.pop[0] = s.pop[1] = const_cast<void *>(pop);
+    s.pop = const_cast<void *>(pop);          // natural layout (phase 0)
     s.aux[0] = s.aux[1] = const_cast<void *>(aux);
     s.sigma = nullptr;
+    s.pub = s.pub_fs = nullptr;
+    s.tflag = nullptr;
     s.err = nullptr;
     s.rng = nullptr;
+    s.epoch = nullptr;
     s.nx = p->nx;
     s.ny = p->ny;
     s.pitch = pitch;
@@ -128,7 +154,6 @@ extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, con
     sc.alpha_l = p->alpha_l;
     sc.R0 = p->R0;
 
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: reset what must start
     // at the identity of its reduction (0 for maxima and flags, all ones for
     // minima)

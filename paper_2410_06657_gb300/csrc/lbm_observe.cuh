@@ -37,63 +37,84 @@ static __device__ __forceinline__ void atomic_min_pos(unsigned long long *a, dou
     atomicMin(a, (unsigned long long)__double_as_longlong(v));
 }
 
+// An instance's populations read through the in-place layout of phases
+// (ph, lph) (the AA pattern of lbm_kernels.cuh): offsets of the slot that
+// holds population i of cell (x, y).
+template <typename S>
+struct PopView {
+    Planes<S> pl;
+    int ph, lph, nx, ny;
+    uint32_t P, pitch;
+    __host__ __device__ static PopView at(const DevState &s, int cur, int lcur) {
+        PopView v;
+        v.pl = Planes<S>::at(s.pop, s.plane);
+        v.ph = cur;
+        v.lph = lcur;
+        v.nx = s.nx;
+        v.ny = s.ny;
+        v.P = (uint32_t)s.plane;
+        v.pitch = (uint32_t)s.pitch;
+        return v;
+    }
+    __device__ __forceinline__ uint32_t o9(int i, int x, int y) const {
+        return aa_src<9>(ph, i, P, pitch, x, y, x == 0 ? nx - 1 : x - 1, x == nx - 1 ? 0 : x + 1, ny);
+    }
+    __device__ __forceinline__ uint32_t o5(int i, int x, int y) const {
+        return aa_src<5>(lph, i, P, pitch, x, y, x == 0 ? nx - 1 : x - 1, x == nx - 1 ? 0 : x + 1, ny);
+    }
+};
+
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void obs_macros(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
-                                           int y, int ny, const Consts<double> &c, const Shift &sh,
-                                           Macro<double> &m) {
+__device__ __forceinline__ void obs_macros(const PopView<S> &v, const A *aux, int x, int y,
+                                           const Consts<double> &c, const Shift &sh, Macro<double> &m) {
     Refs<T> rf;
     Consts<T> ct;      // only phi_bot/phi_top/ny are used by make_refs
     ct.phi_bot = T(c.phi_bot);
     ct.phi_top = T(c.phi_top);
-    make_refs<S, T>(rf, sh, ct, y, ny);
+    make_refs<S, T>(rf, sh, ct, y, v.ny);
+    const uint32_t k = (uint32_t)y * v.pitch + (uint32_t)x;
     double f[9], g[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        f[i] = double(Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale));
-        g[i] = double(Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale));
+        const uint32_t o = v.o9(i, x, y);
+        f[i] = double(Pol<typename FStore<S>::type, T>::ld(v.pl.f + o, rf.f[i], 1.0f / sh.f_scale));
+        g[i] = double(Pol<S, T>::ld(v.pl.g + o, rf.g[i], 1.0f / sh.g_scale));
     }
     double l1234 = 0.0;
 #pragma unroll
-    for (int i = 1; i < 5; i++) l1234 += double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
-    local_macros<double>(f, g, l1234, double(aux[AUX_FS * P + k]), double(aux[AUX_MDOT * P + k]),
-                         double(aux[AUX_Q * P + k]), c, m);
+    for (int i = 1; i < 5; i++) l1234 += double(Pol<S, T>::ld(v.pl.l + v.o5(i, x, y), rf.l[i], 1.0f / sh.l_scale));
+    local_macros<double>(f, g, l1234, double(aux[AUX_FS * v.P + k]), double(aux[AUX_MDOT * v.P + k]),
+                         double(aux[AUX_Q * v.P + k]), c, m);
 }
 
 
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void load_cell(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
-                                          int y, int ny, const Consts<T> &c, const Shift &sh, CellLoad<T> &o) {
+__device__ __forceinline__ void load_cell(const PopView<S> &v, const A *aux, int x, int y, const Consts<T> &c,
+                                          const Shift &sh, CellLoad<T> &o) {
     Refs<T> rf;
-    make_refs<S, T>(rf, sh, c, y, ny);
+    make_refs<S, T>(rf, sh, c, y, v.ny);
+    const uint32_t k = (uint32_t)y * v.pitch + (uint32_t)x;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        o.f[i] = Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale);
-        o.g[i] = Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale);
+        const uint32_t oo = v.o9(i, x, y);
+        o.f[i] = Pol<typename FStore<S>::type, T>::ld(v.pl.f + oo, rf.f[i], 1.0f / sh.f_scale);
+        o.g[i] = Pol<S, T>::ld(v.pl.g + oo, rf.g[i], 1.0f / sh.g_scale);
     }
     o.l1234 = T(0);
 #pragma unroll
-    for (int i = 1; i < 5; i++) o.l1234 += Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale);
-    o.fs_prev = T(aux[AUX_FS * P + k]);
-    o.mdot_prev = T(aux[AUX_MDOT * P + k]);
-    o.Q_prev = T(aux[AUX_Q * P + k]);
+    for (int i = 1; i < 5; i++) o.l1234 += Pol<S, T>::ld(v.pl.l + v.o5(i, x, y), rf.l[i], 1.0f / sh.l_scale);
+    o.fs_prev = T(aux[AUX_FS * v.P + k]);
+    o.mdot_prev = T(aux[AUX_MDOT * v.P + k]);
+    o.Q_prev = T(aux[AUX_Q * v.P + k]);
 }
 
 // Local macros of one cell in the arithmetic type T (the step's own type).
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void cell_macros_t(const Planes<S> &pc, const S *lb, const A *aux, long long P, long long k,
-                                              int y, int ny, const Consts<T> &c, const Shift &sh, Macro<T> &m) {
-    Refs<T> rf;
-    make_refs<S, T>(rf, sh, c, y, ny);
-    T f[9], g[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        f[i] = Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale);
-        g[i] = Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale);
-    }
-    T l1234 = T(0);
-#pragma unroll
-    for (int i = 1; i < 5; i++) l1234 += Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale);
-    local_macros<T>(f, g, l1234, T(aux[AUX_FS * P + k]), T(aux[AUX_MDOT * P + k]), T(aux[AUX_Q * P + k]), c, m);
+__device__ __forceinline__ void cell_macros_t(const PopView<S> &v, const A *aux, int x, int y, const Consts<T> &c,
+                                              const Shift &sh, Macro<T> &m) {
+    CellLoad<T> o;
+    load_cell<S, T, A>(v, aux, x, y, c, sh, o);
+    local_macros<T>(o.f, o.g, o.l1234, o.fs_prev, o.mdot_prev, o.Q_prev, c, m);
 }
 
 template <int NT>
@@ -187,8 +208,7 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int nx = s.nx, ny = s.ny;
     const long long P = s.plane;
-    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
-    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
+    const PopView<S> pv = PopView<S>::at(s, cur, lcur);
     const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * OBS_BY;
     // fill the extended tile (own + halo), ghost rows as in the step: each
@@ -209,7 +229,7 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
             if (valid[q]) {
                 int xx = x0 - 1 + slot_ex[q];
                 xx = xx < 0 ? xx + nx : (xx >= nx ? (xx - nx < nx ? xx - nx : (xx - nx) % nx) : xx);
-                load_cell<S, T, A>(pc, lb, aux, P, (long long)yy * s.pitch + xx, yy, ny, c, sh, ld[q]);
+                load_cell<S, T, A>(pv, aux, xx, yy, c, sh, ld[q]);
             }
         }
 #pragma unroll
@@ -503,15 +523,15 @@ struct StepObs {
 // One step (rows a1-a9) that also reduces the observables (row a10) of the
 // state it starts from.  io, rng, cur as for k_step; `ws` carries this
 // grid's block and group counts.
-template <typename S, typename T, typename A, int BY>
+template <typename S, typename T, typename A, int BY, int PH>
 __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
-    k_step_obs(StepIO<S, T, A> io, unsigned int *rng, int cur, Consts<T> c, Shift sh, ObsScratch ws, Scalars sc) {
+    k_step_obs(StepIO<S, T, A> io, Consts<T> c, Shift sh, ObsScratch ws, Scalars sc) {
     __shared__ TileSmem<T, BY> sm;
     __shared__ T s_fs[BY + 2][34], s_Tm[BY + 2][34];
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
-    load_sr_step(io, rng, cur);
-    sr_advance(rng, cur, io, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
+    load_counters(io, PH);
+    advance_counters(io, PH, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
     StepObs<T, BY> ob;
     ob.fs = s_fs;
     ob.Tm = s_Tm;
@@ -521,7 +541,7 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
 #pragma unroll
     for (int j = 0; j < OBS_NSUM; j++) ob.v[j] = typename StepObs<T, BY>::R(0);
     ob.rowbits = 0u;
-    step_tile<S, T, A, BY, true, StepObs<T, BY>>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY, &ob);
+    step_tile<S, T, A, BY, PH, true, StepObs<T, BY>>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY, &ob);
     obs_block_finish<32 * BY>(ws, sc, ob.v, ob.rowbits, (int)(blockIdx.y * BY + threadIdx.y), io.nx, io.ny);
 }
 
@@ -531,14 +551,12 @@ template <typename S, typename T, typename A>
 __global__ void k_heat_flux(DevState s, int cur, int lcur, Consts<T> c, Shift sh, double *out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= s.nx) return;
-    const long long P = s.plane;
-    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
-    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
+    const PopView<S> pv = PopView<S>::at(s, cur, lcur);
     const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     Macro<T> m0, m1, m2;
-    cell_macros_t<S, T, A>(pc, lb, aux, P, x, 0, s.ny, c, sh, m0);
-    cell_macros_t<S, T, A>(pc, lb, aux, P, (long long)s.pitch + x, 1, s.ny, c, sh, m1);
-    cell_macros_t<S, T, A>(pc, lb, aux, P, 2LL * s.pitch + x, 2, s.ny, c, sh, m2);
+    cell_macros_t<S, T, A>(pv, aux, x, 0, c, sh, m0);
+    cell_macros_t<S, T, A>(pv, aux, x, 1, c, sh, m1);
+    cell_macros_t<S, T, A>(pv, aux, x, 2, c, sh, m2);
     const T k0 = chi(m0.fs, m0.psi, c.kth);
     out[x] = double(-k0 * (T(4) * m1.T_ - m2.T_ - T(3) * m0.T_) / T(2));
 }
@@ -553,8 +571,7 @@ __global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c
     if (x >= s.nx || y >= s.ny) return;
     const long long P = s.plane, k = (long long)y * s.pitch + x;
     const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
-    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
-    const S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
+    const PopView<S> pv = PopView<S>::at(s, cur, lcur);
     const A *aux = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     Refs<T> rf;
     Consts<T> ct;
@@ -562,21 +579,29 @@ __global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c
     ct.phi_top = T(c.phi_top);
     make_refs<S, T>(rf, sh, ct, y, s.ny);
     if (field == LBM_FIELD_F) {
+#pragma unroll
         for (int i = 0; i < 9; i++)
-            out[i * N + o] = double(Pol<typename FStore<S>::type, T>::ld(pc.f + i * P + k, rf.f[i], 1.0f / sh.f_scale));
+            out[i * N + o] =
+                double(Pol<typename FStore<S>::type, T>::ld(pv.pl.f + pv.o9(i, x, y), rf.f[i], 1.0f / sh.f_scale));
     } else if (field == LBM_FIELD_H) {
-        for (int i = 0; i < 9; i++) out[i * N + o] = double(Pol<S, T>::ld(pc.h + i * P + k, T(0), 1.0f / sh.h_scale));
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            out[i * N + o] = double(Pol<S, T>::ld(pv.pl.h + pv.o9(i, x, y), T(0), 1.0f / sh.h_scale));
     } else if (field == LBM_FIELD_G) {
-        for (int i = 0; i < 9; i++) out[i * N + o] = double(Pol<S, T>::ld(pc.g + i * P + k, rf.g[i], 1.0f / sh.g_scale));
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            out[i * N + o] = double(Pol<S, T>::ld(pv.pl.g + pv.o9(i, x, y), rf.g[i], 1.0f / sh.g_scale));
     } else if (field == LBM_FIELD_L) {
-        for (int i = 0; i < 5; i++) out[i * N + o] = double(Pol<S, T>::ld(lb + i * P + k, rf.l[i], 1.0f / sh.l_scale));
+#pragma unroll
+        for (int i = 0; i < 5; i++)
+            out[i * N + o] = double(Pol<S, T>::ld(pv.pl.l + pv.o5(i, x, y), rf.l[i], 1.0f / sh.l_scale));
     } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
         out[o] = double(aux[(field - LBM_FIELD_FS_PREV) * P + k]);
     } else if (field == LBM_FIELD_SIGMA) {
         out[o] = double(reinterpret_cast<const A *>(s.sigma)[k]);
     } else {
         Macro<double> m;
-        obs_macros<S, T, A>(pc, lb, aux, P, k, y, s.ny, c, sh, m);
+        obs_macros<S, T, A>(pv, aux, x, y, c, sh, m);
         out[o] = field == LBM_FIELD_PSI ? m.psi
                : field == LBM_FIELD_FSOLID ? m.fs
                : field == LBM_FIELD_T ? m.T_
@@ -585,30 +610,40 @@ __global__ void k_get(DevState s, int cur, int lcur, int field, Consts<double> c
     }
 }
 
-// Largest change of phi between the potential populations of copy la and
-// copy lb (the two ends of the last sweep), as the bit pattern of a
-// non-negative double: one atomic maximum per warp.
+// Pre-solve residual.  The populations are streamed in place, so the change
+// of phi over one sweep is measured against a snapshot: k_phi_snap stores phi
+// of the current state (arithmetic type, in a spare auxiliary plane), the
+// sweep runs, and k_phi_change takes the largest |phi - snapshot| as the bit
+// pattern of a non-negative double (one atomic maximum per warp).
 template <typename S, typename T, typename A>
-__global__ void k_phi_change(DevState s, int la, int lb, Consts<double> c, Shift sh, unsigned long long *out) {
+__device__ __forceinline__ T phi_of(const PopView<S> &v, const Consts<double> &c, const Shift &sh, int x, int y) {
+    Refs<T> rf;
+    Consts<T> ct;
+    ct.phi_bot = T(c.phi_bot);
+    ct.phi_top = T(c.phi_top);
+    make_refs<S, T>(rf, sh, ct, y, v.ny);
+    T a = T(0);
+#pragma unroll
+    for (int i = 1; i < 5; i++) a += Pol<S, T>::ld(v.pl.l + v.o5(i, x, y), rf.l[i], 1.0f / sh.l_scale);
+    return a / (T(1) - w5<T>(0));
+}
+
+template <typename S, typename T, typename A>
+__global__ void k_phi_snap(DevState s, int lcur, Consts<double> c, Shift sh, A *snap) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= s.nx || y >= s.ny) return;
+    snap[(long long)y * s.pitch + x] = A(phi_of<S, T, A>(PopView<S>::at(s, 0, lcur), c, sh, x, y));
+}
+
+template <typename S, typename T, typename A>
+__global__ void k_phi_change(DevState s, int lcur, Consts<double> c, Shift sh, const A *snap, unsigned long long *out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     double d = 0.0;
     if (x < s.nx && y < s.ny) {
-        const long long P = s.plane, k = (long long)y * s.pitch + x;
-        const S *l0 = Planes<S>::at(la ? s.pop[1] : s.pop[0], P).l;
-        const S *l1 = Planes<S>::at(lb ? s.pop[1] : s.pop[0], P).l;
-        Refs<T> rf;
-        Consts<T> ct;
-        ct.phi_bot = T(c.phi_bot);
-        ct.phi_top = T(c.phi_top);
-        make_refs<S, T>(rf, sh, ct, y, s.ny);
-        double a = 0.0, b = 0.0;
-#pragma unroll
-        for (int i = 1; i < 5; i++) {
-            a += double(Pol<S, T>::ld(l0 + i * P + k, rf.l[i], 1.0f / sh.l_scale));
-            b += double(Pol<S, T>::ld(l1 + i * P + k, rf.l[i], 1.0f / sh.l_scale));
-        }
-        d = fabs(a - b) / (1.0 - w5<double>(0));
+        const T now = phi_of<S, T, A>(PopView<S>::at(s, 0, lcur), c, sh, x, y);
+        d = fabs(double(now) - double(T(snap[(long long)y * s.pitch + x])));
         if (!(d == d)) d = __longlong_as_double(0x7ff0000000000000ll);    // NaN counts as infinite
     }
     unsigned long long v = (unsigned long long)__double_as_longlong(d);
@@ -627,20 +662,24 @@ __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shi
     if (x >= s.nx || y >= s.ny) return;
     const long long P = s.plane, k = (long long)y * s.pitch + x;
     const long long N = (long long)s.nx * s.ny, o = (long long)y * s.nx + x;
-    const Planes<S> pc = Planes<S>::at(cur ? s.pop[1] : s.pop[0], P);
-    S *lb = Planes<S>::at(lcur ? s.pop[1] : s.pop[0], P).l;
+    const PopView<S> pv = PopView<S>::at(s, cur, lcur);
     A *aux = reinterpret_cast<A *>(cur ? s.aux[1] : s.aux[0]);
     Refs<T> rf;
     make_refs<S, T>(rf, sh, c, y, s.ny);
+    // each value goes to the slot that holds it in the current layout
     if (field == LBM_FIELD_F) {
+#pragma unroll
         for (int i = 0; i < 9; i++)
-            Pol<typename FStore<S>::type, T>::st(pc.f + i * P + k, T(in[i * N + o]), rf.f[i], sh.f_scale);
+            Pol<typename FStore<S>::type, T>::st(pv.pl.f + pv.o9(i, x, y), T(in[i * N + o]), rf.f[i], sh.f_scale);
     } else if (field == LBM_FIELD_H) {
-        for (int i = 0; i < 9; i++) Pol<S, T>::st(pc.h + i * P + k, T(in[i * N + o]), T(0), sh.h_scale);
+#pragma unroll
+        for (int i = 0; i < 9; i++) Pol<S, T>::st(pv.pl.h + pv.o9(i, x, y), T(in[i * N + o]), T(0), sh.h_scale);
     } else if (field == LBM_FIELD_G) {
-        for (int i = 0; i < 9; i++) Pol<S, T>::st(pc.g + i * P + k, T(in[i * N + o]), rf.g[i], sh.g_scale);
+#pragma unroll
+        for (int i = 0; i < 9; i++) Pol<S, T>::st(pv.pl.g + pv.o9(i, x, y), T(in[i * N + o]), rf.g[i], sh.g_scale);
     } else if (field == LBM_FIELD_L) {
-        for (int i = 0; i < 5; i++) Pol<S, T>::st(lb + i * P + k, T(in[i * N + o]), rf.l[i], sh.l_scale);
+#pragma unroll
+        for (int i = 0; i < 5; i++) Pol<S, T>::st(pv.pl.l + pv.o5(i, x, y), T(in[i * N + o]), rf.l[i], sh.l_scale);
     } else if (field >= LBM_FIELD_FS_PREV && field <= LBM_FIELD_S) {
         aux[(field - LBM_FIELD_FS_PREV) * P + k] = A(in[o]);
     } else if (field == LBM_FIELD_SIGMA) {

@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 FP64, FP32, FP16S = 0, 1, 2
-STEP_TMA, STEP_DIRECT = 0, 1
+STEP_DIRECT = 1
 OK, ERR_BADPARAM, ERR_OOM, ERR_DIVERGED, ERR_CUDA, ERR_STATE = 0, -1, -2, -3, -4, -5
 WARN_NOT_CONVERGED = 1
 
@@ -33,7 +33,7 @@ EXPORTS = [
     "lbm_step_count", "lbm_configure", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tile_rows", "lbm_batch_destroy", "lbm_observables_noalloc",
     "lbm_substrate_heat_flux", "lbm_observables_to_host", "lbm_sync", "lbm_observables_deferred",
-    "lbm_presolve",
+    "lbm_presolve", "lbm_device_bytes",
 ]
 
 
@@ -113,6 +113,8 @@ def load(build_if_missing: bool = True):
     L.lbm_configure.argtypes = [vp, C.c_int32, C.c_int32]
     L.lbm_step_count.restype = C.c_int64
     L.lbm_step_count.argtypes = [vp]
+    L.lbm_device_bytes.restype = C.c_size_t
+    L.lbm_device_bytes.argtypes = [vp]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_batch_create.argtypes = [P(vp), C.c_int32, vp, C.c_int32, P(vp)]
     L.lbm_batch_step.argtypes = [vp, C.c_int64]
@@ -265,6 +267,10 @@ class Simulation:
 
     def state_bytes(self) -> int:
         return int(load().lbm_state_bytes(self._h))
+
+    def device_bytes(self) -> int:
+        """Device memory the instance holds (lbm_device_bytes)."""
+        return int(load().lbm_device_bytes(self._h))
 
     def export_state(self, buf=None) -> np.ndarray:
         n = self.state_bytes()

@@ -27,18 +27,21 @@ STORAGE_BYTES = {lbm.FP64: 8, lbm.FP32: 4, lbm.FP16S: 2}
 
 
 def footprint_bytes(params: dict) -> int:
-    """Device bytes of one instance: two population copies (9 f planes and
-    23 h, g, l planes), two copies of the 7 auxiliary planes, sigma, and the
-    reduction workspace, rows padded to 32 elements."""
+    """Device bytes of one instance: ONE population copy (9 f planes and 23
+    h, g, l planes, streamed in place), two copies of the 7 auxiliary planes,
+    sigma, the published edge records (four macros and f_s per cell in the
+    arithmetic type), one flag per 32 x 4 tile and the reduction workspace,
+    rows padded to 32 elements."""
     nx, ny, prec = int(params["nx"]), int(params["ny"]), int(params["precision"])
     pitch = (nx + 31) // 32 * 32
     plane = pitch * ny
     sb = STORAGE_BYTES[prec]
     fb = 8 if prec == lbm.FP64 else 4        # half storage keeps f in single precision
-    ab = 8 if prec == lbm.FP64 else 4
+    ab = 8 if prec == lbm.FP64 else 4        # auxiliary and arithmetic type
     blocks = ((nx + 31) // 32) * ((ny + 7) // 8)
+    flags = ((nx + 31) // 32) * ((ny + 3) // 4) * 4
     ws = blocks * 7 * 8 + (3 * ny + 8) * 8 + nx * 8 + 4096
-    return 2 * (9 * fb + 23 * sb) * plane + 2 * 7 * plane * ab + plane * ab + ws
+    return (9 * fb + 23 * sb) * plane + 2 * 7 * plane * ab + plane * ab + 5 * plane * ab + flags + ws
 
 
 @dataclasses.dataclass
@@ -50,6 +53,14 @@ class Request:
     xc: float
     yc: float
     presolve: int = 0
+    psi: Optional[object] = None    # an initial order-parameter field (ny x nx) instead of the cap
+
+
+def _init(sim, req: "Request"):
+    if req.psi is not None:
+        sim.init_psi(req.psi, req.presolve)
+    else:
+        sim.init_droplet(req.R, req.xc, req.yc, req.presolve)
 
 
 @dataclasses.dataclass
@@ -86,6 +97,7 @@ class Server:
         self.results: List[Result] = []
         self.used = 0
         self.lattice_updates = 0
+        self.gpu_busy_s = 0.0           # device time of the chunks (events on the stream)
         self._batch = None
         self._members = None
         self._t0 = None
@@ -111,7 +123,7 @@ class Server:
                 break                   # first come, first served: wait for memory
             self.pending.pop(0)
             sim = lbm.Simulation(req.params, self.stream)
-            sim.init_droplet(req.R, req.xc, req.yc, req.presolve)
+            _init(sim, req)
             self.active.append((req, sim, now, fp))
             self.used += fp
             admitted = True
@@ -132,10 +144,15 @@ class Server:
                 self._batch.close()
             self._batch = lbm.Batch(sims, self.stream, tile_rows=self.tile_rows)
             self._members = [id(s) for s in sims]
+        ev = _events(self.stream)
+        if ev:
+            ev[0].record(ev[2])
         self._batch.step(self.chunk)
         self.lattice_updates += self.chunk * sum(s.nx * s.ny for s in sims)
         for s in sims:
             s.observables_async()
+        if ev:
+            ev[1].record(ev[2])
         keep, retired = [], 0
         for entry in self.active:
             req, sim, adm, fp = entry
@@ -149,6 +166,8 @@ class Server:
                 retired += 1
             else:
                 keep.append(entry)
+        if ev:
+            self.gpu_busy_s += ev[0].elapsed_time(ev[1]) / 1e3    # the fetches synchronised
         if retired:
             self.active = keep
             self._batch.close()
@@ -171,10 +190,28 @@ class Server:
         return sorted(self.results, key=lambda r: r.id)
 
 
+def _events(stream):
+    """Two timing events and the torch stream to record them on (None
+    without torch or CUDA)."""
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        if stream is None:
+            st = torch.cuda.current_stream()
+        elif isinstance(stream, torch.cuda.Stream):
+            st = stream
+        else:
+            st = torch.cuda.ExternalStream(int(getattr(stream, "cuda_stream", stream)))
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), st
+    except Exception:
+        return None
+
+
 def run_alone(req: Request, chunk: int, frozen_target: float = 0.99, max_steps: int = 2_000_000, stream=None):
     """The same request on its own, observed with the same cadence."""
     sim = lbm.Simulation(req.params, stream)
-    sim.init_droplet(req.R, req.xc, req.yc, req.presolve)
+    _init(sim, req)
     while True:
         sim.step(chunk)
         o = sim.observables()

@@ -118,6 +118,69 @@ def freezing_time(R_sigma, S_eps, CaE, Ste=0.2, rho_sl=0.9, theta=120.0, alpha_l
     return dict(t_fre=ob["t_fre"], height=ob["height"], R_tr=ob["R_tr"])
 
 
+def shifted_layer(T_m, lib=None, ny=192, h0=20.0, rho_sl=0.9, steps=4000, alpha_lg=5.0):
+    """The three-phase Stefan layer of Sec. 4 (liquid on the cold wall under
+    gas, closed box) with the temperature origin at T_m: T_w = T_m - 1 and
+    T_init = T_m.  A tall, weakly conducting gas column (alpha_l / alpha_g = 5)
+    holds most of the compression that the expansion of the freezing liquid
+    causes in the closed box.  Frozen fraction after `steps` steps."""
+    o = _oracle().Oracle(_W().params(nx=4, ny=ny, rho_sl=rho_sl, Ste=0.5, alpha_l=0.1, CaE=0.0, R0=h0,
+                                     theta_deg=90.0, T_m=T_m, T_w=T_m - 1.0, T_init=T_m, alpha_lg=alpha_lg),
+                         lib=lib)
+    o.init_psi(layer_psi(4, ny, h0, 4.0))
+    o.step(steps)
+    ob = o.observables()
+    return dict(T_m=T_m, frozen=ob["frozen_fraction"])
+
+
+def shifted_volume_change(T_m, rho_sl=0.9, h0=20.0, ny=48, steps=8000):
+    """volume_change with the temperature origin at T_m (T_w = T_m - 1)."""
+    o = _oracle().Oracle(_W().params(nx=4, ny=ny, rho_sl=rho_sl, Ste=0.5, alpha_l=0.1, CaE=0.0, R0=h0,
+                                     theta_deg=90.0, T_m=T_m, T_w=T_m - 1.0, T_init=T_m))
+    o.init_psi(layer_psi(4, ny, h0, 4.0))
+    o.step(steps)
+    ob = o.observables()
+    return dict(rho_sl=rho_sl, h0=h0, T_m=T_m, height=ob["height"], frozen=ob["frozen_fraction"])
+
+
+def translating_drop(U=0.1, lib=None, N=64, R=12.0, steps=640):
+    """A drop (density and viscosity ratio 1, no field, no freezing) carried
+    by a uniform flow U along x, periodic in x, in the middle of the channel
+    (the wall boundary layers stay away from it for `steps` steps).  The
+    state starts at the equilibria of that flow, with psi u of the previous
+    step equal to the current one.  Returns the centroid speed over U, the
+    ratio of the summed squared x- and y-gradients of psi (1 for an
+    isotropic interface) and the mass ratio."""
+    W = _W()
+    orc = _oracle()
+    o = orc.Oracle(W.params(nx=N, ny=N, T_w=0.0, T_m=0.0, T_init=0.0, CaE=0.0, R0=R, rho_lg=1.0, mu_lg=1.0),
+                   lib=lib)
+    o.init_droplet(R, N / 2, N / 2, 0)
+    psi = o.get("psi")
+    cx, cy, w = orc.lattice()
+    cu = (cx * U)[:, None, None] * np.ones((1, N, N))
+    o.set("f", w[:, None, None] * psi[None] * (1 + 3 * cu))                      # Sec. 3.1 equilibrium
+    o.set("h", w[:, None, None] * (3 * cu + 4.5 * cu * cu - 1.5 * U * U))         # Sec. 3.2, p = 0, rho = 1
+    o.set("psiux", psi * U)
+    o.set("psiuy", np.zeros_like(psi))
+    m0 = psi.sum()
+
+    def centroid(ps):
+        th = 2 * math.pi * np.arange(N) / N
+        a = (ps.sum(0) * np.exp(1j * th)).sum()
+        return (np.angle(a) % (2 * math.pi)) * N / (2 * math.pi)
+
+    x0 = centroid(psi)
+    o.step(steps)
+    ps = o.get("psi")
+    disp = (centroid(ps) - x0) % N
+    gx = (np.roll(ps, -1, 1) - np.roll(ps, 1, 1)) / 2
+    gy = np.zeros_like(ps)
+    gy[1:-1] = (ps[2:] - ps[:-2]) / 2
+    return dict(U=U, speed=disp / (U * steps), aniso=float((gx ** 2).sum() / (gy ** 2).sum()),
+                mass=float(ps.sum() / m0))
+
+
 def mass_conservation(steps=1000):
     """Sessile drop with the field on and no freezing (T_w = T_m)."""
     W = _W()
@@ -164,6 +227,11 @@ JOBS = {
     "deform_2_5": (deformation, (2.0, 5.0)),
     "front_paper": (droplet_front, (0.62,)),
     "mass": (mass_conservation, ()),
+    "shift_0": (shifted_layer, (0.0,)),
+    "shift_2": (shifted_layer, (2.0,)),
+    "volume_0.9_Tm2": (shifted_volume_change, (2.0,)),
+    "translate_0.1": (translating_drop, (0.1,)),
+    "translate_0.05": (translating_drop, (0.05,)),
     "freeze_off": (freezing_time, (5.0, 2.0, 0.0)),
     "freeze_OB-": (freezing_time, (2.0, 5.0, 1.0)),
     "freeze_PR-": (freezing_time, (5.0, 9.5, 1.0)),
@@ -183,6 +251,7 @@ def run_all(processes=None):
     # longest jobs first so the pool drains evenly
     order = ["freeze_off", "freeze_OB-", "freeze_PR-", "deform_5_2", "deform_2_5", "sensitivity", "laplace_10", "laplace_14", "laplace_18",
              "laplace_14_W5", "angle_60", "angle_90", "angle_120", "front_paper",
-             "mass", "stefan", "stefan_solid_diffusivity", "volume_0.9", "volume_1.1"]
+             "mass", "stefan", "stefan_solid_diffusivity", "volume_0.9", "volume_1.1",
+             "translate_0.1", "translate_0.05", "shift_0", "shift_2", "volume_0.9_Tm2"]
     with ctx.Pool(procs) as pool:
         return dict(pool.map(_run, order, chunksize=1))

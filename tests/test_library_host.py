@@ -110,3 +110,20 @@ def test_philox_matches_published_known_answers(tmp_path):
         words = [int(w, 16) for w in out[:4]]
         block = sum(w << (32 * i) for i, w in enumerate(words))
         assert [int(b) for b in out[4:]] == [(block >> (13 * j)) & 0x1fff for j in range(9)]
+
+
+@pytest.mark.parametrize("prec,pop_off,aux_off,out_off", [
+    (W.FP64, 4, 0, 0), (W.FP64, 0, 4, 0), (W.FP32, 2, 0, 0), (W.FP16S, 0, 2, 0), (W.FP32, 0, 0, 4)])
+def test_noalloc_rejects_misaligned_pointers_without_a_device(prec, pop_off, aux_off, out_off):
+    """The allocation-free observables read every plane element by element:
+    a caller pointer that is not aligned to its element size is refused
+    with LBM_ERR_BADPARAM before any device work (no GPU needed here)."""
+    L = lbm.load()
+    L.lbm_observables_noalloc.argtypes = [C.POINTER(lbm.Params), C.c_void_p, C.c_void_p, C.c_int32,
+                                          C.c_int64, C.c_void_p, C.c_void_p]
+    p = lbm.make_params(W.params(nx=64, ny=32, precision=prec))
+    base = 1 << 20      # never dereferenced: the call must stop at the check
+    rc = L.lbm_observables_noalloc(C.byref(p), C.c_void_p(base + pop_off), C.c_void_p(base + aux_off), 64, 0,
+                                   C.c_void_p(base + out_off), None)
+    assert rc == lbm.ERR_BADPARAM
+    assert b"aligned" in L.lbm_last_error()

@@ -6,7 +6,8 @@ that must not synchronise the device).  It reads a caller-held state and
 writes a caller-provided device lbm_obs, with its scratch in a fixed array of
 the library.  Here the state is a snapshot body uploaded by the test (the
 test itself may allocate; the entry point must not), and the result must
-equal what lbm_observables reports for the same state, on two calls in a row.
+equal what lbm_observables reports for the same state, on three calls in a
+row, and the calls after the first must not change the device's free memory.
 """
 import ctypes as C
 
@@ -53,17 +54,22 @@ def test_noalloc_observables_match_lbm_observables(prec):
     init.Fo_fre = -1.0
     out.copy_(torch.frombuffer(bytearray(bytes(init)), dtype=torch.uint8))
     cp = lbm.make_params(p)
-    for call in range(2):
+    for call in range(3):
         sim.step(60 if call == 0 else 25)
         want = sim.observables()
         snap = sim.export_state()
         body = torch.from_numpy(snap[HEADER_BYTES:HEADER_BYTES + pop_bytes + aux_bytes].copy()).cuda()
         torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = L.lbm_observables_noalloc(C.byref(cp), C.c_void_p(body.data_ptr()),
                                        C.c_void_p(body.data_ptr() + pop_bytes), pitch, sim.t,
                                        C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
         assert rc == 0, L.lbm_last_error()
         torch.cuda.synchronize()
+        # the first call may load the library's module on this device; after
+        # it, a call must leave the device's free memory exactly as it was
+        if call > 0:
+            assert torch.cuda.mem_get_info()[0] == free_before, call
         got = lbm.Obs.from_buffer_copy(out.cpu().numpy().tobytes()).as_dict()
         for k, v in want.items():
             if isinstance(v, float):
