@@ -182,11 +182,10 @@ const char *lbm_last_error(void);
  * 32 populations per cell (f 9, h 9, g 9, l 5) in the precision's storage
  * type, streamed in place (AA pattern: the layout alternates between steps),
  * two copies of 7 per-cell auxiliary fields (previous-step f_s, mdot,
- * rho C_p T mdot, psi u_x, psi u_y, p, S), sigma, a record of four macros
- * and f_s per cell in the arithmetic type (published by the tile edges for
- * their neighbours' halos), one flag per 32 x 4 tile and a small reduction
- * workspace: about 208 bytes per cell in FP32, 162 in LBM_FP16S, 416 in
- * FP64.  `stream` is a cudaStream_t (NULL: the legacy
+ * rho C_p T mdot, psi u_x, psi u_y, p, S), sigma, a stamped record of
+ * (psi, f_s, phi) per cell in the arithmetic type (stored by tile-edge
+ * cells for their neighbours' halos) and a small reduction workspace: about
+ * 204 bytes per cell in FP32, 158 in LBM_FP16S, 424 in FP64.  `stream` is a cudaStream_t (NULL: the legacy
  * default stream); all work of the handle is enqueued there.
  * On success *out owns the memory until lbm_destroy.
  * Errors: BADPARAM, OOM, CUDA.
@@ -316,7 +315,10 @@ int lbm_set_field(struct lbm_handle *h, int32_t field, const double *host_in);
  * counter, the stochastic-rounding counter, t_fre and every stored array in
  * the handle's storage precision, populations always in the natural layout
  * (population i of cell (x, y) in plane i at (x, y), whatever the layout
- * phase of the in-place streaming; export converts on the host).
+ * phase of the in-place streaming; export converts on the host).  The
+ * header records the layout phase the state was in, and import restores
+ * the state into that phase on the device, so a resumed run takes the same
+ * step kernels as the original and reproduces it bit for bit.
  * lbm_state_bytes gives the size; export copies device -> host (synchronous),
  * import copies host -> device and is ordered on the handle's stream: the
  * whole snapshot goes into one of two device buffers on a private copy

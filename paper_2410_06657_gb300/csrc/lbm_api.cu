@@ -49,12 +49,9 @@ size_t pop_cell_bytes(int precision) { return 9 * f_bytes(precision) + (NPOP - 9
 size_t l_offset_bytes(int precision, long long plane) {
     return (size_t)plane * (9 * f_bytes(precision) + 18 * storage_bytes(precision));
 }
-// Published edge macros per cell: a (psi, rho, eps, phi) record and f_s, in
-// the arithmetic type.
-size_t pub_rec_bytes(int precision) { return precision == LBM_FP64 ? 32 : 16; }
-size_t arith_bytes(int precision) { return precision == LBM_FP64 ? 8 : 4; }
-// Step tiles of the tallest grid (4-row tiles): one publication flag each.
-size_t flag_count(int nx, int ny) { return (size_t)((nx + 31) / 32) * (size_t)((ny + 3) / 4); }
+// Record of a tile-edge cell: (psi, f_s, phi) and the epoch stamp, in
+// 16-byte units (FP32 one, FP64 three).
+size_t pub_rec_bytes(int precision) { return precision == LBM_FP64 ? 48 : 16; }
 
 // D2Q9 and D2Q5 velocity sets (Secs. 3.1, 3.4) for the host-side layout
 // conversion of snapshots.
@@ -382,9 +379,9 @@ int ensure_staging(lbm_handle *h) {
 }
 
 // The parities were reset outside a step: the epoch of the next step may
-// repeat one used before, so no tile may still show it.
+// repeat one used before, so no record may still carry it (0 is no epoch).
 int clear_flags(lbm_handle *h) {
-    CK(cudaMemsetAsync(h->s.tflag, 0, flag_count(h->P.nx, h->P.ny) * sizeof(unsigned int), h->st));
+    CK(cudaMemsetAsync(h->s.pub, 0, (size_t)h->s.plane * pub_rec_bytes(h->P.precision), h->st));
     return LBM_OK;
 }
 
@@ -451,10 +448,8 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     const size_t aux_b = round_up((size_t)NAUX * plane * ab, 256);
     const size_t sig_b = round_up((size_t)plane * ab, 256);
     const size_t pub_b = round_up((size_t)plane * pub_rec_bytes(p->precision), 256);
-    const size_t pfs_b = round_up((size_t)plane * arith_bytes(p->precision), 256);
-    const size_t flag_b = round_up(flag_count(nx, ny) * sizeof(unsigned int), 256);
     // one population copy: the step streams in place (AA pattern)
-    h->mem_bytes = pop_b + 2 * aux_b + sig_b + pub_b + pfs_b + flag_b;
+    h->mem_bytes = pop_b + 2 * aux_b + sig_b + pub_b;
     if (cudaMalloc(&h->mem, h->mem_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -466,8 +461,6 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->s.aux[1] = b + pop_b + aux_b;
     h->s.sigma = b + pop_b + 2 * aux_b;
     h->s.pub = b + pop_b + 2 * aux_b + sig_b;
-    h->s.pub_fs = b + pop_b + 2 * aux_b + sig_b + pub_b;
-    h->s.tflag = reinterpret_cast<unsigned int *>(b + pop_b + 2 * aux_b + sig_b + pub_b + pfs_b);
     h->s.nx = nx;
     h->s.ny = ny;
     h->s.pitch = pitch;
@@ -514,7 +507,7 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     const unsigned int first_epochs[2] = {1u, 1u};
     if (cudaMemset(h->err, 0, err_b) != cudaSuccess ||
         cudaMemcpy(h->s.epoch, first_epochs, sizeof first_epochs, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(h->s.tflag, 0, flag_b) != cudaSuccess ||
+        cudaMemset(h->s.pub, 0, pub_b) != cudaSuccess ||
         cudaMemset(h->ws_max_base, 0x00, h->ws_max_bytes) != cudaSuccess ||
         cudaMemset(h->ws_min_base, 0xFF, h->ws_min_bytes) != cudaSuccess ||
         cudaMemset(h->ws_u32_base, 0x00, h->ws_u32_bytes) != cudaSuccess) {
@@ -778,7 +771,8 @@ struct SnapHeader {
     int32_t nx, ny, precision, k_e;
     int64_t body_bytes;
     uint32_t sr_step;      // stochastic-rounding counter of half storage
-    char pad[20];
+    int32_t phase;         // layout phases at export: cur | lcur << 1 (the body is natural)
+    char pad[16];
 };
 static_assert(sizeof(SnapHeader) == 64, "snapshot header is 64 bytes");
 
@@ -813,6 +807,7 @@ int lbm_export_state(lbm_handle *h, void *host, size_t bytes) {
     hd.precision = h->P.precision;
     hd.k_e = h->P.k_e;
     hd.body_bytes = (int64_t)(a + b + c + d + sizeof(lbm_obs));
+    hd.phase = h->cur | (h->lcur << 1);
     char *o = static_cast<char *>(host);
     std::memcpy(o, &hd, sizeof hd);
     CK(cudaMemcpyAsync(o + offsetof(SnapHeader, sr_step), h->s.rng + h->cur, sizeof(uint32_t),
@@ -881,14 +876,27 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
     snap_sizes(h, a, b, c, d);
     const char *o = dev + sizeof hd;
     const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
-    // the snapshot holds the natural layout: both phases restart at 0
-    h->cur = 0;
-    h->lcur = 0;
-    CK(cudaMemcpyAsync(h->s.pop, o, a + b, dd, h->st));
-    CK(cudaMemcpyAsync(h->s.aux[0], o + a + b, c, dd, h->st));
+    // the body holds the natural layout; the state resumes in the layout
+    // phases it was exported at, so the same step kernels follow (single
+    // precision rounds each phase's kernel in its own way)
+    if (hd.phase < 0 || hd.phase > 3) return fail(LBM_ERR_BADPARAM, "snapshot layout phase out of range");
+    h->cur = hd.phase & 1;
+    h->lcur = (hd.phase >> 1) & 1;
+    if (hd.phase == 0) {
+        CK(cudaMemcpyAsync(h->s.pop, o, a + b, dd, h->st));
+    } else {
+        cudaError_t e;
+        switch (h->P.precision) {
+        case LBM_FP64: e = launch_place_f64(h->s, h->cur, h->lcur, o, h->st); break;
+        case LBM_FP32: e = launch_place_f32(h->s, h->cur, h->lcur, o, h->st); break;
+        default: e = launch_place_f16s(h->s, h->cur, h->lcur, o, h->st); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "snapshot placement kernel");
+    }
+    CK(cudaMemcpyAsync(h->s.aux[h->cur], o + a + b, c, dd, h->st));
     CK(cudaMemcpyAsync(h->s.sigma, o + a + b + c, d, dd, h->st));
     CK(cudaMemcpyAsync(h->ws.obs, o + a + b + c + d, sizeof(lbm_obs), dd, h->st));
-    CK(cudaMemcpyAsync(h->s.rng, dev + offsetof(SnapHeader, sr_step), sizeof(uint32_t), dd, h->st));
+    CK(cudaMemcpyAsync(h->s.rng + h->cur, dev + offsetof(SnapHeader, sr_step), sizeof(uint32_t), dd, h->st));
     CK(cudaEventRecord(h->imp_free[j], h->st));
     if (int rc_ = clear_flags(h)) return rc_;
     h->step = hd.step;
@@ -1241,7 +1249,7 @@ int lbm_batch_create(lbm_handle *const *members, int32_t n, void *stream, int32_
                                         save ? static_cast<const void *>(h->err) : static_cast<const void *>(cnt), 64, dd,
                                         b->st);
                 if (e == cudaSuccess && !save)
-                    e = cudaMemsetAsync(h->s.tflag, 0, flag_count(h->P.nx, h->P.ny) * sizeof(unsigned int), b->st);
+                    e = cudaMemsetAsync(h->s.pub, 0, (size_t)h->s.plane * pub_rec_bytes(h->P.precision), b->st);
                 if (e != cudaSuccess) return e;
             }
             return cudaSuccess;

@@ -49,9 +49,7 @@ struct DevState {
     void *pop;             // one copy of NPOP planes, streamed in place (AA pattern)
     void *aux[2];          // two copies of NAUX planes
     void *sigma;           // one plane
-    void *pub;             // one record (psi, rho, eps, phi) per cell, arithmetic type
-    void *pub_fs;          // one plane of f_s, arithmetic type
-    unsigned int *tflag;   // per step tile (4-row tiles: the most): epoch of its last publication
+    void *pub;             // one stamped record (psi, f_s, phi) per cell, arithmetic type
     unsigned int *err;     // device status word (sticky error bits)
     unsigned int *rng;     // [2] stochastic-rounding step counters of half storage (or null)
     unsigned int *epoch;   // [2] step epochs (>= 1), alternating with the parity
@@ -112,6 +110,8 @@ struct Scalars {           // per-call scalars of the observables reduction
                                            const void *consts /* Consts<double> */,           \
                                            const Shift &sh, const void *snap,                  \
                                            unsigned long long *out, cudaStream_t st);          \
+    cudaError_t launch_place_##SUFFIX(const DevState &s, int cur, int lcur, const void *src,   \
+                                      cudaStream_t st);                                        \
     cudaError_t launch_set_##SUFFIX(const DevState &s, int cur, int lcur, int field,           \
                                     const void *consts, const Shift &sh, const double *in,     \
                                     cudaStream_t st);

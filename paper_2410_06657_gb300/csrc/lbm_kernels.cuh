@@ -15,16 +15,15 @@
 //             of the previous step (read by the next step's stencils, so the
 //             step reads copy b and writes copy 1-b)
 //   sigma   : conductivity at time n for the extra potential sweeps
-//   pub     : (psi, rho, eps, phi) of each tile's edge cells at the current
-//             time level, and f_s for observing steps, published by the tile
-//             before it overwrites its slots; tflag: per tile, the epoch of
-//             the step that last published.
+//   pub     : one record per cell, (psi, f_s, phi) of a tile-edge cell at
+//             the current time level stamped with the step's epoch, stored
+//             before the cell overwrites its slots.
 //
 // One step is one launch.  A thread block owns a 32 x BY tile.  Phase 1
 // computes the local macroscopic fields (row a1) of the tile and of its
 // one-cell halo into shared memory: the halo's from the halo cells' own
-// populations, or from their owner's published record once the owner has
-// started to overwrite them (no block waits for another).  Phase 2 applies
+// populations, or from the record a halo cell stored before its owner
+// started to overwrite it (no block waits for another).  Phase 2 applies
 // the radius-1 stencils (a2), forces (a3), flow macros (a4), the four
 // collisions (a5-a8) and writes the post-collision populations back into
 // the slots the cell read, with the wall rules (a9).
@@ -375,56 +374,71 @@ __device__ __forceinline__ uint32_t aa_dst(int ph, int i, uint32_t P, uint32_t p
 }
 
 // ---------------------------------------------------------------------------
-// Publication of tile-edge macros.  The fused step recomputes its halo's
-// macros from the halo cells' populations, which their owner tile (another
-// block) overwrites in place during the same step.  Before it overwrites any
-// slot, the owner stores the macros of its edge cells and then its tile's
-// flag = this step's epoch (publish_flag); a reader loads a halo cell's
-// populations, then -- after a fence -- its owner's flag: if the flag shows
-// this step's epoch, some loaded slot may already hold the new value and the
-// published record is used; otherwise the owner had not started writing when
-// the loads were performed, so they hold the time-n values.  The two routes
-// give the same macros bit for bit (the same code on the same inputs).  No
-// thread waits for another: a reader never depends on an owner's progress.
+// Records of tile-edge cells.  The fused step recomputes its halo's macros
+// from the halo cells' populations, which their owner tile (another block)
+// overwrites in place during the same step.  Before a tile-edge cell
+// overwrites any of its slots, it stores a record (psi, f_s, phi) stamped
+// with this step's epoch, and a fence orders the record before the slot
+// writes (record_fence, placed just before the cell's first global store,
+// long after the record store itself).  A reader loads the halo cell's
+// populations and then -- ordered after them by a data dependency -- its
+// record: a stamp of this epoch means the record holds the cell's time-n
+// macros; any other stamp means the record was not yet stored when it was
+// read, so neither was any slot overwritten when the populations were
+// read: they hold the time-n values.  Either route gives the same macros
+// bit for bit (rho and eps follow from (psi, f_s) by the same property law
+// local_macros applies).  No thread ever waits for another.
+//
+// A record is written with 16-byte stores, each carrying the stamp, and
+// read with 16-byte loads: FP32 (psi, f_s, phi, stamp) in one, FP64 three
+// (value, stamp) pairs.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned int ld_flag(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_flag(unsigned int *p, unsigned int v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ void fence_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-template <typename T>
-struct alignas(4 * sizeof(T)) PubRec { T psi, rho, eps, phi; };
+template <typename T> struct PubRec;
+template <>
+struct alignas(16) PubRec<float> {
+    float psi, fs, phi;
+    uint32_t stamp;
+};
+template <>
+struct alignas(16) PubRec<double> {
+    double psi;
+    unsigned long long s0;
+    double fs;
+    unsigned long long s1;
+    double phi;
+    unsigned long long s2;
+};
 
-__device__ __forceinline__ PubRec<float> ld_pub(const PubRec<float> *p) {
-    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
-    return {v.x, v.y, v.z, v.w};
+__device__ __forceinline__ void st_rec(PubRec<float> *p, float psi, float fs, float phi, uint32_t e) {
+    *reinterpret_cast<uint4 *>(p) = make_uint4(__float_as_uint(psi), __float_as_uint(fs), __float_as_uint(phi), e);
 }
-__device__ __forceinline__ PubRec<double> ld_pub(const PubRec<double> *p) {
-    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
-    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
-    return {a.x, a.y, b.x, b.y};
+__device__ __forceinline__ void st_rec(PubRec<double> *p, double psi, double fs, double phi, uint32_t e) {
+    ulonglong2 *q = reinterpret_cast<ulonglong2 *>(p);
+    q[0] = make_ulonglong2((unsigned long long)__double_as_longlong(psi), e);
+    q[1] = make_ulonglong2((unsigned long long)__double_as_longlong(fs), e);
+    q[2] = make_ulonglong2((unsigned long long)__double_as_longlong(phi), e);
 }
-__device__ __forceinline__ void st_pub(PubRec<float> *p, float psi, float rho, float eps, float phi) {
-    *reinterpret_cast<float4 *>(p) = make_float4(psi, rho, eps, phi);
+// Load of a record (from L2, not L1), and whether it carries epoch e.
+__device__ __forceinline__ bool ld_rec(const PubRec<float> *p, uint32_t e, float &psi, float &fs, float &phi) {
+    const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p));
+    psi = __uint_as_float(v.x);
+    fs = __uint_as_float(v.y);
+    phi = __uint_as_float(v.z);
+    return v.w == e;
 }
-__device__ __forceinline__ void st_pub(PubRec<double> *p, double psi, double rho, double eps, double phi) {
-    reinterpret_cast<double2 *>(p)[0] = make_double2(psi, rho);
-    reinterpret_cast<double2 *>(p)[1] = make_double2(eps, phi);
+__device__ __forceinline__ bool ld_rec(const PubRec<double> *p, uint32_t e, double &psi, double &fs, double &phi) {
+    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
+    const ulonglong2 a = __ldcg(q), b = __ldcg(q + 1), d = __ldcg(q + 2);
+    psi = __longlong_as_double((long long)a.x);
+    fs = __longlong_as_double((long long)b.x);
+    phi = __longlong_as_double((long long)d.x);
+    return a.y == e && b.y == e && d.y == e;
 }
 
-// The tile's records (stored by its threads before the block barrier that
-// precedes this call) become visible before the flag, and the flag before
-// any slot of the tile is overwritten (after the next block barrier).
-__device__ __forceinline__ void publish_flag(unsigned int *flag, unsigned int epoch) {
-    fence_gpu();
-    st_flag(flag, epoch);
-    fence_gpu();
-}
+__device__ __forceinline__ uint32_t low_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ uint32_t low_bits(double v) { return (uint32_t)__double_as_longlong(v); }
 
 // ---------------------------------------------------------------------------
 // The fused step (rows a1-a9) for one 32 x BY tile.
@@ -447,12 +461,10 @@ struct StepIO {
     const A *aux_in;
     A *aux_out;
     A *sigma;
-    PubRec<T> *pub;          // published edge macros of the current time level
-    T *pub_fs;               // published f_s (observing steps)
-    unsigned int *tflag;     // per tile: epoch of its last publication
+    PubRec<T> *pub;          // records of tile-edge cells (stamped with the epoch)
     unsigned int *rng;       // [2] stochastic-rounding counters (half storage) or null
     unsigned int *ep;        // [2] step epochs
-    int nx, ny, pitch, write_sigma, lph, tiles_x;
+    int nx, ny, pitch, write_sigma, lph;
     long long plane;
     uint32_t sr_step;        // this step's stochastic-rounding counter (half storage)
     uint32_t epoch;          // this step's epoch
@@ -475,8 +487,6 @@ __host__ __device__ __forceinline__ StepIO<S, T, A> step_io(const DevState &s, i
     io.aux_out = reinterpret_cast<A *>(cur ? s.aux[0] : s.aux[1]);
     io.sigma = reinterpret_cast<A *>(s.sigma);
     io.pub = reinterpret_cast<PubRec<T> *>(s.pub);
-    io.pub_fs = reinterpret_cast<T *>(s.pub_fs);
-    io.tflag = s.tflag;
     io.rng = s.rng;
     io.ep = s.epoch;
     io.sr_step = 0u;
@@ -486,7 +496,6 @@ __host__ __device__ __forceinline__ StepIO<S, T, A> step_io(const DevState &s, i
     io.pitch = s.pitch;
     io.write_sigma = write_sigma;
     io.lph = lcur;
-    io.tiles_x = (s.nx + 31) / 32;
     io.plane = s.plane;
     return io;
 }
@@ -550,23 +559,45 @@ __device__ __forceinline__ void load_cell_aa(const StepIO<S, T, A> &io, const Co
     Sv = T(io.aux_in[AUX_S * P + k]);
 }
 
-// Macros of a cell outside the tile whose loads (load_cell_aa) have been
-// issued: its owner's published record if the owner has published in this
-// step, else the macros of the loaded values (see publish_flag).  OBS: the
-// record's f_s is needed too.
-template <typename S, typename T, typename A, int BY, bool OBS>
-__device__ __forceinline__ void resolve_ext(const StepIO<S, T, A> &io, const Consts<T> &c, int x, int y,
-                                            const CellLoad<T> &ld, Macro<T> &m) {
-    fence_gpu();      // the loads above are performed before the flag is read
-    const unsigned int e = ld_flag(io.tflag + (uint32_t)(y / BY) * (uint32_t)io.tiles_x + (uint32_t)(x >> 5));
-    if (e == io.epoch) {
-        const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
-        const PubRec<T> r = ld_pub(io.pub + k);
+// A zero that depends on every value of an outside cell's loads: the load
+// of the cell's record, addressed with it, is issued only after all of
+// them have returned (see the record protocol above).
+template <typename T>
+__device__ __forceinline__ uint32_t after_loads(const CellLoad<T> &o) {
+    uint32_t acc = low_bits(o.l1234) | low_bits(o.fs_prev) | low_bits(o.mdot_prev) | low_bits(o.Q_prev);
+#pragma unroll
+    for (int i = 0; i < 9; i++) acc |= low_bits(o.f[i]) | low_bits(o.g[i]);
+    uint32_t z;
+    asm volatile("and.b32 %0, %1, 0;" : "=r"(z) : "r"(acc));
+    return z;
+}
+
+// The record of an outside cell whose loads (load_cell_aa) have been
+// issued, read after them.
+template <typename T>
+struct ExtRec {
+    T psi, fs, phi;
+    bool fresh;
+};
+template <typename S, typename T, typename A>
+__device__ __forceinline__ ExtRec<T> ext_record(const StepIO<S, T, A> &io, int x, int y, const CellLoad<T> &ld) {
+    ExtRec<T> r;
+    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x + after_loads(ld);
+    r.fresh = ld_rec(io.pub + k, io.epoch, r.psi, r.fs, r.phi);
+    return r;
+}
+
+// Macros of an outside cell: from its record if the record carries this
+// step's epoch, else from the loaded values.
+template <typename T>
+__device__ __forceinline__ void resolve_ext(const Consts<T> &c, const CellLoad<T> &ld, const ExtRec<T> &r,
+                                            Macro<T> &m) {
+    if (r.fresh) {
         m.psi = r.psi;
-        m.rho = r.rho;
-        m.eps = r.eps;
+        m.fs = r.fs;
         m.phi = r.phi;
-        m.fs = OBS ? __ldcg(io.pub_fs + k) : T(0);
+        m.rho = chi(m.fs, m.psi, c.rho);      // as local_macros
+        m.eps = chi(m.fs, m.psi, c.eps);
         m.H = T(0);
         m.T_ = T(0);
     } else {
@@ -578,23 +609,22 @@ __device__ __forceinline__ void resolve_ext(const StepIO<S, T, A> &io, const Con
 template <typename S, typename T, typename A, int BY, int PH, typename OB>
 __device__ __forceinline__ void ext_to_smem(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
                                             TileSmem<T, BY> &sm, int ex, int ey, int x, int y, OB *ob) {
-    constexpr bool OBS = !std::is_same<OB, NoObs>::value;
     CellLoad<T> ld;
     T pv, Sv;
     load_cell_aa<S, T, A, PH>(io, c, sh, x, y, ld, pv, Sv);
+    const ExtRec<T> r = ext_record(io, x, y, ld);
     Macro<T> m;
-    resolve_ext<S, T, A, BY, OBS>(io, c, x, y, ld, m);
+    resolve_ext<T>(c, ld, r, m);
     sm.q[ey][ex] = {m.psi, m.rho, m.eps, m.phi};
     sm.ps[ey][ex] = {pv, Sv};
-    if constexpr (OBS) ob->macro(ey, ex, m);
+    if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ey, ex, m);
 }
 
-// An own cell's record, for the halos of its neighbour tiles: cells on the
-// tile's edge only (no other tile reads the inner ones).
-template <typename S, typename T, typename A, bool OBS>
+// A tile-edge cell's record, for the halos of its neighbour tiles (no other
+// tile reads the inner cells).
+template <typename S, typename T, typename A>
 __device__ __forceinline__ void publish_cell(const StepIO<S, T, A> &io, uint32_t k, const Macro<T> &m) {
-    st_pub(io.pub + k, m.psi, m.rho, m.eps, m.phi);
-    if constexpr (OBS) io.pub_fs[k] = m.fs;
+    st_rec(io.pub + k, m.psi, m.fs, m.phi, io.epoch);
 }
 
 // Asynchronous global -> shared copy of one 4- or 8-byte element.
@@ -679,11 +709,13 @@ __device__ __forceinline__ void fill_ghosts(TileSmem<T, BY> &sm, const Consts<T>
 // supplies the cell's time-n populations (registers or shared memory).
 // EDGE: the tile touches a wall row, so destinations may leave the lattice;
 // interior tiles skip the per-direction wall tests.
+// published: the cell stored a record this step, which must be visible
+// before the cell overwrites its first slot.
 template <typename S, typename T, typename A, int BY, bool EDGE, int PH, typename PopSrc, typename OB = NoObs>
 __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
                                           const TileSmem<T, BY> &sm, const PopSrc &PS, int tx, int ty, int x,
                                           int y, const Macro<T> &m, T fs_prev, T pux_prev, T puy_prev,
-                                          OB *ob = nullptr) {
+                                          bool published, OB *ob = nullptr) {
     const int nx = io.nx, ny = io.ny;
     const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
     const uint32_t pitch = (uint32_t)io.pitch;
@@ -764,6 +796,9 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
 
     // ---- collisions + in-place streaming (a5-a9) ---------------------------
     const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
+    // the record (stored in phase 1) before the first slot write; by now the
+    // store has long completed, so the fence waits for nothing
+    if (published) fence_gpu();
     const T uu_ = ux * ux + uy * uy;
     const T B15 = T(1.5) * uu_;                    // u.u / (2 c_s^2)
 
@@ -951,7 +986,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     const int x = own ? x0 + tx : 0;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const uint32_t k = (uint32_t)y * pitch + (uint32_t)x;
-    const bool edge = ty == 0 || ty == BY - 1 || y == ny - 1 || tx == 0 || tx == ncols - 1;
+    const bool edge = tx == 0 || tx == ncols - 1 || ty == 0 || ty == BY - 1;
     Macro<T> m;
     T fs_prev = T(0), mdot_prev = T(0), Q_prev = T(0), pux_prev = T(0), puy_prev = T(0);
     constexpr int NRING = 2 * 34 + 2 * BY;
@@ -1006,7 +1041,11 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         }
         CellLoad<T> rl;
         T rp = T(0), rS = T(0);
-        if (ring) load_cell_aa<S, T, A, PH>(io, c, sh, rhx, rhy, rl, rp, rS);
+        ExtRec<T> rr;
+        if (ring) {
+            load_cell_aa<S, T, A, PH>(io, c, sh, rhx, rhy, rl, rp, rS);
+            rr = ext_record(io, rhx, rhy, rl);    // issued once the ring loads are back
+        }
         if (own) {
             cp_async_wait_all();
             if (ncols == 32) __syncwarp();   // a full row's planes were copied by the whole warp
@@ -1023,12 +1062,12 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
             sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
             sm.ps[ty + 1][tx + 1] = {pv, Sv};
-            if (edge) publish_cell<S, T, A, OBS>(io, k, m);
+            if (edge) publish_cell<S, T, A>(io, k, m);
             if constexpr (OBS) ob->macro(ty + 1, tx + 1, m);
         }
         if (ring) {
             Macro<T> mr;
-            resolve_ext<S, T, A, BY, OBS>(io, c, rhx, rhy, rl, mr);
+            resolve_ext<T>(c, rl, rr, mr);
             sm.q[rey][rex] = {mr.psi, mr.rho, mr.eps, mr.phi};
             sm.ps[rey][rex] = {rp, rS};
             if constexpr (OBS) ob->macro(rey, rex, mr);
@@ -1071,7 +1110,7 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             for (int i = 0; i < 5; i++) stash[27 + i][ty][tx] = l[i];
             sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
             sm.ps[ty + 1][tx + 1] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
-            if (edge) publish_cell<S, T, A, OBS>(io, k, m);
+            if (edge) publish_cell<S, T, A>(io, k, m);
             if constexpr (OBS) ob->macro(ty + 1, tx + 1, m);
         }
         // ---- phase 1: halo ring, from the neighbours' populations or records
@@ -1080,17 +1119,14 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     // the wrap-around neighbour of a ragged tile's last column
     if (wrap) ext_to_smem<S, T, A, BY, PH, OB>(io, c, sh, sm, tx + 1, ty + 1, 0, y, ob);
     __syncthreads();
-    // the tile's records are stored: publish, then (after the barrier) write
-    if (tid == 0)
-        publish_flag(io.tflag + (uint32_t)(y0 / BY) * (uint32_t)io.tiles_x + (uint32_t)(x0 >> 5), io.epoch);
     fill_ghosts<T, BY>(sm, c, y0, ny, tid);
     __syncthreads();
     if (!own) return;
     const StashPops<T, BY> PS{stash, ty, tx};
     if (y0 == 0 || y0 + BY >= ny)
-        step_cell<S, T, A, BY, true, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
+        step_cell<S, T, A, BY, true, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, edge, ob);
     else
-        step_cell<S, T, A, BY, false, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
+        step_cell<S, T, A, BY, false, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, edge, ob);
 }
 
 // Blocks per SM the single-precision step asks the register allocator for:

@@ -214,6 +214,11 @@ cudaError_t launch_step_obs_t(const DevState &s, int cur, int lcur, int write_si
                                                             out);                                           \
         return cudaGetLastError();                                                                          \
     }                                                                                                       \
+    cudaError_t launch_place_##SUFFIX(const DevState &s, int cur, int lcur, const void *src, cudaStream_t st) { \
+        dim3 grid((s.nx + 31) / 32, (s.ny + 7) / 8);                                                        \
+        k_place<S, T, A><<<grid, dim3(32, 8), 0, st>>>(s, cur, lcur, src);                                  \
+        return cudaGetLastError();                                                                          \
+    }                                                                                                       \
     cudaError_t launch_set_##SUFFIX(const DevState &s, int cur, int lcur, int field, const void *consts,   \
                                     const Shift &sh, const double *in, cudaStream_t st) {                   \
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \

@@ -655,6 +655,31 @@ __global__ void k_phi_change(DevState s, int lcur, Consts<double> c, Shift sh, c
     if ((threadIdx.x & 31) == 0) atomicMax(out, v);
 }
 
+// Natural-layout population planes (a snapshot body: f, h, g, l planes of
+// `pitch` x ny elements) written into the in-place layout of phases
+// (cur, lcur): each value goes to the slot that holds it there; raw
+// elements, no conversion (the half-storage references depend on the
+// direction and the reading cell only, the same in both layouts).
+template <typename S, typename T, typename A>
+__global__ void k_place(DevState s, int cur, int lcur, const void *src) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= s.nx || y >= s.ny) return;
+    using F = typename FStore<S>::type;
+    const PopView<S> pv = PopView<S>::at(s, cur, lcur);
+    const Planes<S> in = Planes<S>::at(src, s.plane);
+    const uint32_t P = (uint32_t)s.plane, k = (uint32_t)y * (uint32_t)s.pitch + (uint32_t)x;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const uint32_t o = pv.o9(i, x, y);
+        pv.pl.f[o] = static_cast<const F *>(in.f)[i * P + k];
+        pv.pl.h[o] = in.h[i * P + k];
+        pv.pl.g[o] = in.g[i * P + k];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; i++) pv.pl.l[pv.o5(i, x, y)] = in.l[i * P + k];
+}
+
 template <typename S, typename T, typename A>
 __global__ void k_set(DevState s, int cur, int lcur, int field, Consts<T> c, Shift sh, const double *in) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;

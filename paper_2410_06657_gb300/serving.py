@@ -29,19 +29,18 @@ STORAGE_BYTES = {lbm.FP64: 8, lbm.FP32: 4, lbm.FP16S: 2}
 def footprint_bytes(params: dict) -> int:
     """Device bytes of one instance: ONE population copy (9 f planes and 23
     h, g, l planes, streamed in place), two copies of the 7 auxiliary planes,
-    sigma, the published edge records (four macros and f_s per cell in the
-    arithmetic type), one flag per 32 x 4 tile and the reduction workspace,
-    rows padded to 32 elements."""
+    sigma, the stamped edge records (16 bytes per cell, 48 in FP64) and the
+    reduction workspace, rows padded to 32 elements."""
     nx, ny, prec = int(params["nx"]), int(params["ny"]), int(params["precision"])
     pitch = (nx + 31) // 32 * 32
     plane = pitch * ny
     sb = STORAGE_BYTES[prec]
     fb = 8 if prec == lbm.FP64 else 4        # half storage keeps f in single precision
     ab = 8 if prec == lbm.FP64 else 4        # auxiliary and arithmetic type
+    rec = 48 if prec == lbm.FP64 else 16
     blocks = ((nx + 31) // 32) * ((ny + 7) // 8)
-    flags = ((nx + 31) // 32) * ((ny + 3) // 4) * 4
     ws = blocks * 7 * 8 + (3 * ny + 8) * 8 + nx * 8 + 4096
-    return (9 * fb + 23 * sb) * plane + 2 * 7 * plane * ab + plane * ab + 5 * plane * ab + flags + ws
+    return (9 * fb + 23 * sb) * plane + 2 * 7 * plane * ab + plane * ab + rec * plane + ws
 
 
 @dataclasses.dataclass

@@ -103,19 +103,25 @@ def droplet_front(Fo, Ste=0.2, rho_sl=0.9, theta=120.0, alpha_lg=0.2, R=16.0, nx
 
 
 def freezing_time(R_sigma, S_eps, CaE, Ste=0.2, rho_sl=0.9, theta=120.0, alpha_lg=0.2, R=16.0, nx=96, ny=48,
-                  every=20):
-    """Steps until the frozen fraction reaches 0.99, observed every `every` steps."""
+                  every=20, T_g=0.5, Fo_probe=0.3125):
+    """Steps until the frozen fraction reaches 0.99, observed every `every`
+    steps, with the whole region initially at T_g (T_m = 0, T_w = -1), and
+    the droplet's height and contact-line radius at Fo = Fo_probe."""
     W = _W()
     p = W.params(nx=nx, ny=ny, Ste=Ste, rho_sl=rho_sl, theta_deg=theta, alpha_lg=alpha_lg, CaE=CaE,
-                 R_sigma=R_sigma, S_eps=S_eps, R0=R)
+                 R_sigma=R_sigma, S_eps=S_eps, R0=R, T_init=T_g)
     o = _oracle().Oracle(p)
     xc, yc = W.sessile_center(nx, R, theta)
     o.init_droplet(R, xc, yc, 2000)
     ob = o.observables()
+    probe = int(round(Fo_probe * R * R / p["alpha_l"]))
+    h_probe = r_probe = None
     while ob["t_fre"] < 0 and o.t < 100000:
         o.step(every)
         ob = o.observables()
-    return dict(t_fre=ob["t_fre"], height=ob["height"], R_tr=ob["R_tr"])
+        if h_probe is None and o.t >= probe:
+            h_probe, r_probe = ob["height"], ob["R_tr"]
+    return dict(t_fre=ob["t_fre"], height=ob["height"], R_tr=ob["R_tr"], h_probe=h_probe, R_tr_probe=r_probe)
 
 
 def shifted_layer(T_m, lib=None, ny=192, h0=20.0, rho_sl=0.9, steps=4000, alpha_lg=5.0):
@@ -225,6 +231,9 @@ JOBS = {
     "volume_1.1": (volume_change, (1.1,)),
     "deform_5_2": (deformation, (5.0, 2.0)),
     "deform_2_5": (deformation, (2.0, 5.0)),
+    "deform_5_2_N120": (deformation, (5.0, 2.0, 0.2, 120)),
+    "deform_5_2_N160": (deformation, (5.0, 2.0, 0.2, 160)),
+    "deform_2_5_N160": (deformation, (2.0, 5.0, 0.2, 160)),
     "front_paper": (droplet_front, (0.62,)),
     "mass": (mass_conservation, ()),
     "shift_0": (shifted_layer, (0.0,)),
@@ -235,6 +244,7 @@ JOBS = {
     "freeze_off": (freezing_time, (5.0, 2.0, 0.0)),
     "freeze_OB-": (freezing_time, (2.0, 5.0, 1.0)),
     "freeze_PR-": (freezing_time, (5.0, 9.5, 1.0)),
+    "freeze_PR+": (freezing_time, (2.0, 0.5, 1.0)),
 }
 
 
@@ -249,7 +259,8 @@ def run_all(processes=None):
     ctx = mp.get_context("spawn")
     procs = processes or min(len(JOBS), max(1, os.cpu_count() or 1))
     # longest jobs first so the pool drains evenly
-    order = ["freeze_off", "freeze_OB-", "freeze_PR-", "deform_5_2", "deform_2_5", "sensitivity", "laplace_10", "laplace_14", "laplace_18",
+    order = ["deform_5_2_N160", "deform_2_5_N160", "freeze_off", "freeze_OB-", "freeze_PR-", "freeze_PR+",
+             "deform_5_2_N120", "deform_5_2", "deform_2_5", "sensitivity", "laplace_10", "laplace_14", "laplace_18",
              "laplace_14_W5", "angle_60", "angle_90", "angle_120", "front_paper",
              "mass", "stefan", "stefan_solid_diffusivity", "volume_0.9", "volume_1.1",
              "translate_0.1", "translate_0.05", "shift_0", "shift_2", "volume_0.9_Tm2"]
