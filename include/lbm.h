@@ -114,7 +114,7 @@ typedef struct lbm_params {
 } lbm_params;
 
 /*
- * Observables of one instance (row a10).  The paper measures these from
+ * Observables of one instance.  The paper measures these from
  * its fields but gives no discrete definition; the library's are:
  *   mass = sum psi, enthalpy = sum H, solid = sum f_s, charge = sum q_v with
  *   q_v = div(eps E) by the product rule.  The per-cell terms are evaluated
@@ -182,10 +182,11 @@ const char *lbm_last_error(void);
  * 32 populations per cell (f 9, h 9, g 9, l 5) in the precision's storage
  * type, streamed in place (AA pattern: the layout alternates between steps),
  * two copies of 7 per-cell auxiliary fields (previous-step f_s, mdot,
- * rho C_p T mdot, psi u_x, psi u_y, p, S), sigma, a stamped record of
- * (psi, f_s, phi) per cell in the arithmetic type (stored by tile-edge
- * cells for their neighbours' halos) and a small reduction workspace: about
- * 204 bytes per cell in FP32, 158 in LBM_FP16S, 424 in FP64.  `stream` is a cudaStream_t (NULL: the legacy
+ * rho C_p T mdot, psi u_x, psi u_y, p, S), sigma, a record of
+ * (psi, f_s, phi) per cell in the arithmetic type (each step stores those
+ * of the tile-edge cells first, for their neighbour tiles' halos) and a
+ * small reduction workspace: about 204 bytes per cell in FP32, 158 in
+ * LBM_FP16S, 408 in FP64.  `stream` is a cudaStream_t (NULL: the legacy
  * default stream); all work of the handle is enqueued there.
  * On success *out owns the memory until lbm_destroy.
  * Errors: BADPARAM, OOM, CUDA.
@@ -277,7 +278,7 @@ int lbm_observables_to_host(struct lbm_handle *h, lbm_obs *out);
  * current state (those of lbm_observables, Secs. 4-5) without a pass of
  * their own over the lattice.  The next
  * lbm_step reduces them inside its first step's kernel, which reads exactly
- * this state (rows a1-a3 already evaluate every macro and stencil they
+ * this state (its macro, stencil and force stages evaluate every value they
  * need); any other call on the handle first runs them on their own, as
  * lbm_observables_async would.  out: NULL to fetch the result later with
  * lbm_observables_fetch, or host memory (page-locked for an asynchronous
@@ -337,9 +338,11 @@ int lbm_import_state(struct lbm_handle *h, const void *host, size_t bytes);
 
 /*
  * Step kernel selection (tuning and testing; results do not depend on it in
- * FP64, and differ only by rounding in FP32):
- *   variant LBM_STEP_DIRECT (the one variant): every thread loads its cell
- *     from global memory and stashes it in shared memory for the collisions;
+ * FP64, and differ only by rounding in FP32).  Every step is two launches:
+ * the halo records of the tile-edge cells, then the step kernel:
+ *   variant LBM_STEP_DIRECT (the one variant): one block per tile; every
+ *     thread copies its cell's populations into shared memory for the
+ *     collisions;
  *   tile_rows: 4, 8 or 16 lattice rows per 32-column tile (default 4 in
  *     single precision, 8 in FP64).
  * Errors: BADPARAM (unknown variant or height, NULL).

@@ -49,9 +49,9 @@ size_t pop_cell_bytes(int precision) { return 9 * f_bytes(precision) + (NPOP - 9
 size_t l_offset_bytes(int precision, long long plane) {
     return (size_t)plane * (9 * f_bytes(precision) + 18 * storage_bytes(precision));
 }
-// Record of a tile-edge cell: (psi, f_s, phi) and the epoch stamp, in
-// 16-byte units (FP32 one, FP64 three).
-size_t pub_rec_bytes(int precision) { return precision == LBM_FP64 ? 48 : 16; }
+// Halo record of a tile-edge cell: (psi, f_s, phi) and a pad, in the
+// arithmetic type (FP32 16 bytes, FP64 32).
+size_t halo_rec_bytes(int precision) { return precision == LBM_FP64 ? 32 : 16; }
 
 // D2Q9 and D2Q5 velocity sets (Secs. 3.1, 3.4) for the host-side layout
 // conversion of snapshots.
@@ -248,6 +248,7 @@ struct lbm_handle {
     int64_t step = 0;
     bool inited = false, diverged = false;
     int tile_rows = 4;         // lattice rows per tile (set per precision in lbm_create)
+    int variant = LBM_STEP_DIRECT;   // form of the step kernel (lbm_configure)
     unsigned int *err = nullptr;   // device status word (sticky error bits)
     double *qdot = nullptr;        // nx doubles: substrate heat flux profile
     // graph cache: one per starting parity (cur, lcur)
@@ -298,9 +299,9 @@ cudaError_t do_step(lbm_handle *h, cudaStream_t st, const Scalars *observe = nul
         }
     } else {
         switch (h->P.precision) {
-        case LBM_FP64: e = launch_step_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
-        case LBM_FP32: e = launch_step_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
-        default: e = launch_step_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, st); break;
+        case LBM_FP64: e = launch_step_f64(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->variant, st); break;
+        case LBM_FP32: e = launch_step_f32(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->variant, st); break;
+        default: e = launch_step_f16s(h->s, h->cur, h->lcur, ws, c, h->sh, h->tile_rows, h->variant, st); break;
         }
     }
     if (e != cudaSuccess) return e;
@@ -378,18 +379,10 @@ int ensure_staging(lbm_handle *h) {
     return LBM_OK;
 }
 
-// The parities were reset outside a step: the epoch of the next step may
-// repeat one used before, so no record may still carry it (0 is no epoch).
-int clear_flags(lbm_handle *h) {
-    CK(cudaMemsetAsync(h->s.pub, 0, (size_t)h->s.plane * pub_rec_bytes(h->P.precision), h->st));
-    return LBM_OK;
-}
-
 int finish_init(lbm_handle *h, const double *psi_dev, double R, double xc, double yc, int presolve) {
     if (int rc_ = run_pending_obs(h)) return rc_;
     h->cur = 0;
     h->lcur = 0;
-    if (int rc_ = clear_flags(h)) return rc_;
     const void *c = consts_for(h);
     cudaError_t e;
     switch (h->P.precision) {
@@ -447,9 +440,9 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     (void)sb;
     const size_t aux_b = round_up((size_t)NAUX * plane * ab, 256);
     const size_t sig_b = round_up((size_t)plane * ab, 256);
-    const size_t pub_b = round_up((size_t)plane * pub_rec_bytes(p->precision), 256);
+    const size_t halo_b = round_up((size_t)plane * halo_rec_bytes(p->precision), 256);
     // one population copy: the step streams in place (AA pattern)
-    h->mem_bytes = pop_b + 2 * aux_b + sig_b + pub_b;
+    h->mem_bytes = pop_b + 2 * aux_b + sig_b + halo_b;
     if (cudaMalloc(&h->mem, h->mem_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -460,7 +453,7 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->s.aux[0] = b + pop_b;
     h->s.aux[1] = b + pop_b + aux_b;
     h->s.sigma = b + pop_b + 2 * aux_b;
-    h->s.pub = b + pop_b + 2 * aux_b + sig_b;
+    h->s.halo = b + pop_b + 2 * aux_b + sig_b;
     h->s.nx = nx;
     h->s.ny = ny;
     h->s.pitch = pitch;
@@ -501,13 +494,10 @@ int lbm_create(const lbm_params *p, void *stream, lbm_handle **out) {
     h->err = reinterpret_cast<unsigned int *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b);
     h->s.err = h->err;
     h->s.rng = h->err + 4;     // two counters in the same 256-byte block
-    h->s.epoch = h->err + 8;   // two epochs there too
     h->qdot = reinterpret_cast<double *>(w + part_b + h->ws_max_bytes + h->ws_min_bytes + h->ws_u32_bytes + obs_b +
                                          err_b);
-    const unsigned int first_epochs[2] = {1u, 1u};
     if (cudaMemset(h->err, 0, err_b) != cudaSuccess ||
-        cudaMemcpy(h->s.epoch, first_epochs, sizeof first_epochs, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(h->s.pub, 0, pub_b) != cudaSuccess ||
+        cudaMemset(h->s.halo, 0, halo_b) != cudaSuccess ||
         cudaMemset(h->ws_max_base, 0x00, h->ws_max_bytes) != cudaSuccess ||
         cudaMemset(h->ws_min_base, 0xFF, h->ws_min_bytes) != cudaSuccess ||
         cudaMemset(h->ws_u32_base, 0x00, h->ws_u32_bytes) != cudaSuccess) {
@@ -898,7 +888,6 @@ int lbm_import_state(lbm_handle *h, const void *host, size_t bytes) {
     CK(cudaMemcpyAsync(h->ws.obs, o + a + b + c + d, sizeof(lbm_obs), dd, h->st));
     CK(cudaMemcpyAsync(h->s.rng + h->cur, dev + offsetof(SnapHeader, sr_step), sizeof(uint32_t), dd, h->st));
     CK(cudaEventRecord(h->imp_free[j], h->st));
-    if (int rc_ = clear_flags(h)) return rc_;
     h->step = hd.step;
     h->inited = true;
     h->diverged = false;
@@ -982,6 +971,7 @@ int lbm_configure(lbm_handle *h, int32_t variant, int32_t tile_rows) {
     if (tile_rows != 4 && tile_rows != 8 && tile_rows != 16) return fail(LBM_ERR_BADPARAM, "tile_rows must be 4, 8 or 16");
     CK(cudaStreamSynchronize(h->st));
     h->tile_rows = tile_rows;
+    h->variant = variant;
     drop_graphs(h);
     return LBM_OK;
 }
@@ -1052,11 +1042,11 @@ static void free_list(WorkList &L) {
 }
 
 // Device bytes a member's step touches: the populations (one copy, in
-// place), both auxiliary copies, sigma and the published records.
+// place), both auxiliary copies, sigma and the halo records.
 static size_t member_state_bytes(const lbm_handle *h) {
     const int prec = h->P.precision;
     const size_t ab = aux_bytes(prec);
-    return (size_t)h->s.plane * (pop_cell_bytes(prec) + 2 * NAUX * ab + ab + pub_rec_bytes(prec));
+    return (size_t)h->s.plane * (pop_cell_bytes(prec) + 2 * NAUX * ab + ab + halo_rec_bytes(prec));
 }
 
 static int build_list(lbm_batch *b, const std::vector<int> &idx, int tile_rows, int sms, WorkList &L) {
@@ -1212,8 +1202,7 @@ int lbm_batch_create(lbm_handle *const *members, int32_t n, void *stream, int32_
         // (six steps per height, an even number: the layout phases return)
         // and overwrite both auxiliary copies; the state they started from
         // (populations, auxiliary copies, sigma, counters) is saved first
-        // and put back after, with every publication flag cleared (the
-        // epochs will repeat).
+        // and put back after.
         std::vector<size_t> pop_sz(n), sig_sz(n), aux_sz(n);
         size_t total = 0;
         for (int i = 0; i < n; i++) {
@@ -1243,13 +1232,11 @@ int lbm_batch_create(lbm_handle *const *members, int32_t n, void *stream, int32_
                     e = cudaMemcpyAsync(save ? x0 : h->s.aux[0], save ? h->s.aux[0] : x0, aux_sz[i], dd, b->st);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(save ? x1 : h->s.aux[1], save ? h->s.aux[1] : x1, aux_sz[i], dd, b->st);
-                // the status word, rounding counters and epochs
+                // the status word and rounding counters
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(save ? static_cast<void *>(cnt) : static_cast<void *>(h->err),
                                         save ? static_cast<const void *>(h->err) : static_cast<const void *>(cnt), 64, dd,
                                         b->st);
-                if (e == cudaSuccess && !save)
-                    e = cudaMemsetAsync(h->s.pub, 0, (size_t)h->s.plane * pub_rec_bytes(h->P.precision), b->st);
                 if (e != cudaSuccess) return e;
             }
             return cudaSuccess;

@@ -49,10 +49,9 @@ struct DevState {
     void *pop;             // one copy of NPOP planes, streamed in place (AA pattern)
     void *aux[2];          // two copies of NAUX planes
     void *sigma;           // one plane
-    void *pub;             // one stamped record (psi, f_s, phi) per cell, arithmetic type
+    void *halo;            // one record (psi, f_s, phi) per cell, arithmetic type
     unsigned int *err;     // device status word (sticky error bits)
     unsigned int *rng;     // [2] stochastic-rounding step counters of half storage (or null)
-    unsigned int *epoch;   // [2] step epochs (>= 1), alternating with the parity
     int nx, ny, pitch;     // pitch: elements per row (multiple of 32)
     long long plane;       // elements per plane (pitch * ny)
 };
@@ -83,7 +82,7 @@ struct Scalars {           // per-call scalars of the observables reduction
 #define LBM_DECLARE_LAUNCHERS(SUFFIX)                                                         \
     cudaError_t launch_step_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,    \
                                      const void *consts, const Shift &sh, int tile_rows,       \
-                                     cudaStream_t st);                                         \
+                                     int variant, cudaStream_t st);                            \
     cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, int cur, uint32_t sr_sys,   \
                                       const void *consts, const Shift &sh, cudaStream_t st);  \
     cudaError_t launch_init_##SUFFIX(const DevState &s, const double *psi_dev, double R,       \

@@ -15,18 +15,19 @@
 //             of the previous step (read by the next step's stencils, so the
 //             step reads copy b and writes copy 1-b)
 //   sigma   : conductivity at time n for the extra potential sweeps
-//   pub     : one record per cell, (psi, f_s, phi) of a tile-edge cell at
-//             the current time level stamped with the step's epoch, stored
-//             before the cell overwrites its slots.
+//   halo    : (psi, f_s, phi) of every tile-edge cell at the current time
+//             level, one 16-byte (FP64: 32-byte) record per cell
 //
-// One step is one launch.  A thread block owns a 32 x BY tile.  Phase 1
-// computes the local macroscopic fields (row a1) of the tile and of its
-// one-cell halo into shared memory: the halo's from the halo cells' own
-// populations, or from the record a halo cell stored before its owner
-// started to overwrite it (no block waits for another).  Phase 2 applies
-// the radius-1 stencils (a2), forces (a3), flow macros (a4), the four
-// collisions (a5-a8) and writes the post-collision populations back into
-// the slots the cell read, with the wall rules (a9).
+// One step is two launches over the same 32 x BY tiles.  k_halo computes
+// the local macroscopic fields of every tile-edge cell (the cells another
+// tile's one-cell ring holds) into the halo records.  k_step then computes
+// the local macroscopic fields of its own cells into shared memory and takes
+// its ring from the records (rho and eps follow from (psi, f_s) by the
+// property law), applies the radius-1 stencils, forces, flow macros, the
+// four collisions and writes the post-collision populations back into the
+// slots the cell read, with the wall rules.  The launch boundary orders
+// every record store before every population is overwritten, so no block
+// ever reads a value another block of the same launch writes.
 #pragma once
 
 #include <cuda.h>
@@ -93,7 +94,7 @@ template <>
 struct Pol<__half, float> {
     static constexpr bool shifted = true;
     __device__ static __forceinline__ float ld(const __half *p, float ref, float inv_scale) {
-        return __half2float(*p) * inv_scale + ref;
+        return __fmaf_rn(__half2float(*p), inv_scale, ref);    // one rounding in every context
     }
     __device__ static __forceinline__ void st(__half *p, float v, float ref, float scale) {
         *p = __float2half_rn((v - ref) * scale);
@@ -141,6 +142,17 @@ struct Planes {
     }
 };
 
+// Separately rounded product, sum and difference: the compiler never fuses
+// these into an FMA, so a value built from them has the same bits wherever
+// it is evaluated (a tile-edge cell's macros are computed by the halo kernel
+// for its neighbour tiles and again by the step for the cell itself).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
 // Per-cell reference values of the weight-shifted half storage.
 template <typename T>
 struct Refs {
@@ -153,13 +165,13 @@ __device__ __forceinline__ void make_refs(Refs<T> &r, const Shift &sh, const Con
     if constexpr (Pol<S, T>::shifted) {
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            r.f[i] = w9<T>(i) * T(sh.f_ref);
-            r.g[i] = (i == 0) ? T(sh.g0_ref) : w9<T>(i) * T(sh.g_ref);
+            r.f[i] = mul_rn(w9<T>(i), T(sh.f_ref));
+            r.g[i] = (i == 0) ? T(sh.g0_ref) : mul_rn(w9<T>(i), T(sh.g_ref));
         }
         // linear potential between the electrodes
-        T phil = c.phi_bot + (c.phi_top - c.phi_bot) * (T(y) + T(0.5)) / T(ny);
+        T phil = add_rn(c.phi_bot, mul_rn(sub_rn(c.phi_top, c.phi_bot), T(y) + T(0.5)) / T(ny));
 #pragma unroll
-        for (int i = 0; i < 5; i++) r.l[i] = (i == 0) ? (w5<T>(0) - T(1)) * phil : w5<T>(i) * phil;
+        for (int i = 0; i < 5; i++) r.l[i] = mul_rn((i == 0) ? w5<T>(0) - T(1) : w5<T>(i), phil);
     }
 }
 
@@ -167,29 +179,33 @@ __device__ __forceinline__ void make_refs(Refs<T> &r, const Shift &sh, const Con
 // Pointwise physics (shared by the step, observables and field kernels).
 // ---------------------------------------------------------------------------
 
-// Eq. (Computed): three-phase property law.
+// Eq. (Computed): three-phase property law, evaluated left to right.
 template <typename T>
 __device__ __forceinline__ T chi(T fs, T psi, const T v[3]) {
-    return fs * v[0] + (T(1) - fs) * psi * v[1] + (T(1) - fs) * (T(1) - psi) * v[2];
+    const T ls = sub_rn(T(1), fs);
+    const T a = mul_rn(fs, v[0]);
+    const T b = mul_rn(mul_rn(ls, psi), v[1]);
+    const T d = mul_rn(mul_rn(ls, sub_rn(T(1), psi)), v[2]);
+    return add_rn(add_rn(a, b), d);
 }
 
 // Eq. (Hfl) with H_s = C_p T_m, latent heat carried by the liquid part
 // (L_eff = psi L): liquid fraction and temperature from total enthalpy.
 template <typename T>
 __device__ __forceinline__ void enthalpy_inversion(T H, T psi, T cp, T Tm, T L, T &fl, T &Tt) {
-    T Hs = cp * Tm;
-    T Leff = psi * L;
-    T Hl = Hs + Leff;
+    T Hs = mul_rn(cp, Tm);
+    T Leff = mul_rn(psi, L);
+    T Hl = add_rn(Hs, Leff);
     if (H < Hs)
         Tt = H / cp;
     else if (H <= Hl)
         Tt = Tm;
     else
-        Tt = Tm + (H - Hl) / cp;
+        Tt = add_rn(Tm, sub_rn(H, Hl) / cp);
     if (Leff < T(1e-12)) {
         fl = T(1);
     } else {
-        T r = (H - Hs) / Leff;
+        T r = sub_rn(H, Hs) / Leff;
         fl = r < T(0) ? T(0) : (r > T(1) ? T(1) : r);
     }
 }
@@ -199,7 +215,7 @@ struct Macro {
     T psi, H, T_, fs, rho, eps, phi;
 };
 
-// Row a1: local macroscopic quantities from the populations at time n
+// Local macroscopic quantities from the populations at time n
 // (psi and H use the previous step's mdot and rho C_p T mdot).
 template <typename T>
 __device__ __forceinline__ void local_macros(const T f[9], const T g[9], T l1234, T fs_prev,
@@ -208,15 +224,15 @@ __device__ __forceinline__ void local_macros(const T f[9], const T g[9], T l1234
     T sf = T(0);
 #pragma unroll
     for (int i = 0; i < 9; i++) sf += f[i];
-    m.psi = sf / (T(1) - T(0.5) * mdot_prev);             // Eq. (Computed_psi)
+    m.psi = sf / sub_rn(T(1), mul_rn(T(0.5), mdot_prev));  // Eq. (Computed_psi)
     T sg = T(0);
 #pragma unroll
     for (int i = 0; i < 9; i++) sg += g[i];
-    m.H = sg + T(0.5) * Q_prev;                           // Sec. 3.3
+    m.H = add_rn(sg, mul_rn(T(0.5), Q_prev));              // Sec. 3.3
     T cp_lev = chi(fs_prev, m.psi, c.cp);
     T fl;
     enthalpy_inversion(m.H, m.psi, cp_lev, c.T_m, c.L, fl, m.T_);
-    m.fs = m.psi * (T(1) - fl);
+    m.fs = mul_rn(m.psi, sub_rn(T(1), fl));
     m.rho = chi(m.fs, m.psi, c.rho);
     m.eps = chi(m.fs, m.psi, c.eps);
     m.phi = l1234 / (T(1) - w5<T>(0));                    // Eq. (Computed_phi)
@@ -374,74 +390,51 @@ __device__ __forceinline__ uint32_t aa_dst(int ph, int i, uint32_t P, uint32_t p
 }
 
 // ---------------------------------------------------------------------------
-// Records of tile-edge cells.  The fused step recomputes its halo's macros
-// from the halo cells' populations, which their owner tile (another block)
-// overwrites in place during the same step.  Before a tile-edge cell
-// overwrites any of its slots, it stores a record (psi, f_s, phi) stamped
-// with this step's epoch, and a fence orders the record before the slot
-// writes (record_fence, placed just before the cell's first global store,
-// long after the record store itself).  A reader loads the halo cell's
-// populations and then -- ordered after them by a data dependency -- its
-// record: a stamp of this epoch means the record holds the cell's time-n
-// macros; any other stamp means the record was not yet stored when it was
-// read, so neither was any slot overwritten when the populations were
-// read: they hold the time-n values.  Either route gives the same macros
-// bit for bit (rho and eps follow from (psi, f_s) by the same property law
-// local_macros applies).  No thread ever waits for another.
-//
-// A record is written with 16-byte stores, each carrying the stamp, and
-// read with 16-byte loads: FP32 (psi, f_s, phi, stamp) in one, FP64 three
-// (value, stamp) pairs.
+// Halo records: (psi, f_s, phi) of a tile-edge cell at time n, written by
+// k_halo and read by the step kernel of the same step.  FP32 packs them in
+// one 16-byte vector, FP64 in two.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void fence_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
-template <typename T> struct PubRec;
-template <>
-struct alignas(16) PubRec<float> {
-    float psi, fs, phi;
-    uint32_t stamp;
-};
-template <>
-struct alignas(16) PubRec<double> {
-    double psi;
-    unsigned long long s0;
-    double fs;
-    unsigned long long s1;
-    double phi;
-    unsigned long long s2;
+template <typename T>
+struct alignas(4 * sizeof(T)) HaloRec {
+    T psi, fs, phi, pad;
 };
 
-__device__ __forceinline__ void st_rec(PubRec<float> *p, float psi, float fs, float phi, uint32_t e) {
-    *reinterpret_cast<uint4 *>(p) = make_uint4(__float_as_uint(psi), __float_as_uint(fs), __float_as_uint(phi), e);
+__device__ __forceinline__ void st_halo(HaloRec<float> *p, float psi, float fs, float phi) {
+    *reinterpret_cast<float4 *>(p) = make_float4(psi, fs, phi, 0.0f);
 }
-__device__ __forceinline__ void st_rec(PubRec<double> *p, double psi, double fs, double phi, uint32_t e) {
-    ulonglong2 *q = reinterpret_cast<ulonglong2 *>(p);
-    q[0] = make_ulonglong2((unsigned long long)__double_as_longlong(psi), e);
-    q[1] = make_ulonglong2((unsigned long long)__double_as_longlong(fs), e);
-    q[2] = make_ulonglong2((unsigned long long)__double_as_longlong(phi), e);
+__device__ __forceinline__ void st_halo(HaloRec<double> *p, double psi, double fs, double phi) {
+    double2 *q = reinterpret_cast<double2 *>(p);
+    q[0] = make_double2(psi, fs);
+    q[1] = make_double2(phi, 0.0);
 }
-// Load of a record (from L2, not L1), and whether it carries epoch e.
-__device__ __forceinline__ bool ld_rec(const PubRec<float> *p, uint32_t e, float &psi, float &fs, float &phi) {
-    const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p));
-    psi = __uint_as_float(v.x);
-    fs = __uint_as_float(v.y);
-    phi = __uint_as_float(v.z);
-    return v.w == e;
+// Loaded from L2: the records change every step.
+__device__ __forceinline__ void ld_halo(const HaloRec<float> *p, float &psi, float &fs, float &phi) {
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    psi = v.x;
+    fs = v.y;
+    phi = v.z;
 }
-__device__ __forceinline__ bool ld_rec(const PubRec<double> *p, uint32_t e, double &psi, double &fs, double &phi) {
-    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
-    const ulonglong2 a = __ldcg(q), b = __ldcg(q + 1), d = __ldcg(q + 2);
-    psi = __longlong_as_double((long long)a.x);
-    fs = __longlong_as_double((long long)b.x);
-    phi = __longlong_as_double((long long)d.x);
-    return a.y == e && b.y == e && d.y == e;
+__device__ __forceinline__ void ld_halo(const HaloRec<double> *p, double &psi, double &fs, double &phi) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    psi = a.x;
+    fs = a.y;
+    phi = b.x;
 }
 
-__device__ __forceinline__ uint32_t low_bits(float v) { return __float_as_uint(v); }
-__device__ __forceinline__ uint32_t low_bits(double v) { return (uint32_t)__double_as_longlong(v); }
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may be scheduled while the kernel before it in the stream
+// drains; grid_dep_wait() returns once that kernel has completed and its
+// stores are visible, and grid_dep_release() lets the next such kernel be
+// scheduled.  Every kernel of a step waits before its first global load, so
+// only the launch latency overlaps.  Both are no-ops in a kernel launched
+// without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 
 // ---------------------------------------------------------------------------
-// The fused step (rows a1-a9) for one 32 x BY tile.
+// The fused step for one 32 x BY tile.
 // ---------------------------------------------------------------------------
 template <typename T, int BY>
 struct TileSmem {
@@ -461,13 +454,11 @@ struct StepIO {
     const A *aux_in;
     A *aux_out;
     A *sigma;
-    PubRec<T> *pub;          // records of tile-edge cells (stamped with the epoch)
+    HaloRec<T> *hm;          // halo records of the tile-edge cells
     unsigned int *rng;       // [2] stochastic-rounding counters (half storage) or null
-    unsigned int *ep;        // [2] step epochs
     int nx, ny, pitch, write_sigma, lph;
     long long plane;
     uint32_t sr_step;        // this step's stochastic-rounding counter (half storage)
-    uint32_t epoch;          // this step's epoch
 };
 
 // The step's pointers and sizes for the parities (cur, lcur): cur is the
@@ -486,11 +477,9 @@ __host__ __device__ __forceinline__ StepIO<S, T, A> step_io(const DevState &s, i
     io.aux_in = reinterpret_cast<const A *>(cur ? s.aux[1] : s.aux[0]);
     io.aux_out = reinterpret_cast<A *>(cur ? s.aux[0] : s.aux[1]);
     io.sigma = reinterpret_cast<A *>(s.sigma);
-    io.pub = reinterpret_cast<PubRec<T> *>(s.pub);
+    io.hm = reinterpret_cast<HaloRec<T> *>(s.halo);
     io.rng = s.rng;
-    io.ep = s.epoch;
     io.sr_step = 0u;
-    io.epoch = 0u;
     io.nx = s.nx;
     io.ny = s.ny;
     io.pitch = s.pitch;
@@ -508,7 +497,6 @@ __device__ __forceinline__ void load_counters(StepIO<S, T, A> &io, int cur) {
     if constexpr (Pol<S, T>::shifted) {
         if (io.rng) io.sr_step = io.rng[cur];
     }
-    io.epoch = io.ep[cur];
 }
 template <typename S, typename T, typename A>
 __device__ __forceinline__ void advance_counters(const StepIO<S, T, A> &io, int cur, bool leader) {
@@ -516,7 +504,6 @@ __device__ __forceinline__ void advance_counters(const StepIO<S, T, A> &io, int 
     if constexpr (Pol<S, T>::shifted) {
         if (io.rng) io.rng[cur ^ 1] = io.sr_step + 1u;
     }
-    io.ep[cur ^ 1] = io.epoch + 1u;
 }
 
 // Observation hooks of a step: a plain step observes nothing.  A step that
@@ -559,72 +546,49 @@ __device__ __forceinline__ void load_cell_aa(const StepIO<S, T, A> &io, const Co
     Sv = T(io.aux_in[AUX_S * P + k]);
 }
 
-// A zero that depends on every value of an outside cell's loads: the load
-// of the cell's record, addressed with it, is issued only after all of
-// them have returned (see the record protocol above).
-template <typename T>
-__device__ __forceinline__ uint32_t after_loads(const CellLoad<T> &o) {
-    uint32_t acc = low_bits(o.l1234) | low_bits(o.fs_prev) | low_bits(o.mdot_prev) | low_bits(o.Q_prev);
-#pragma unroll
-    for (int i = 0; i < 9; i++) acc |= low_bits(o.f[i]) | low_bits(o.g[i]);
-    uint32_t z;
-    asm volatile("and.b32 %0, %1, 0;" : "=r"(z) : "r"(acc));
-    return z;
-}
-
-// The record of an outside cell whose loads (load_cell_aa) have been
-// issued, read after them.
-template <typename T>
-struct ExtRec {
-    T psi, fs, phi;
-    bool fresh;
-};
-template <typename S, typename T, typename A>
-__device__ __forceinline__ ExtRec<T> ext_record(const StepIO<S, T, A> &io, int x, int y, const CellLoad<T> &ld) {
-    ExtRec<T> r;
-    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x + after_loads(ld);
-    r.fresh = ld_rec(io.pub + k, io.epoch, r.psi, r.fs, r.phi);
-    return r;
-}
-
-// Macros of an outside cell: from its record if the record carries this
-// step's epoch, else from the loaded values.
-template <typename T>
-__device__ __forceinline__ void resolve_ext(const Consts<T> &c, const CellLoad<T> &ld, const ExtRec<T> &r,
-                                            Macro<T> &m) {
-    if (r.fresh) {
-        m.psi = r.psi;
-        m.fs = r.fs;
-        m.phi = r.phi;
-        m.rho = chi(m.fs, m.psi, c.rho);      // as local_macros
-        m.eps = chi(m.fs, m.psi, c.eps);
-        m.H = T(0);
-        m.T_ = T(0);
-    } else {
-        local_macros<T>(ld.f, ld.g, ld.l1234, ld.fs_prev, ld.mdot_prev, ld.Q_prev, c, m);
-    }
-}
-
-// Macros of an outside cell into the extended tile slot (ex, ey).
-template <typename S, typename T, typename A, int BY, int PH, typename OB>
-__device__ __forceinline__ void ext_to_smem(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
-                                            TileSmem<T, BY> &sm, int ex, int ey, int x, int y, OB *ob) {
+// The halo record of a tile-edge cell: its time-n macros from its own
+// populations, exactly as the cell's owner computes them.
+template <typename S, typename T, typename A, int PH>
+__device__ __forceinline__ void halo_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, int x,
+                                          int y) {
     CellLoad<T> ld;
     T pv, Sv;
     load_cell_aa<S, T, A, PH>(io, c, sh, x, y, ld, pv, Sv);
-    const ExtRec<T> r = ext_record(io, x, y, ld);
     Macro<T> m;
-    resolve_ext<T>(c, ld, r, m);
-    sm.q[ey][ex] = {m.psi, m.rho, m.eps, m.phi};
-    sm.ps[ey][ex] = {pv, Sv};
-    if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ey, ex, m);
+    local_macros<T>(ld.f, ld.g, ld.l1234, ld.fs_prev, ld.mdot_prev, ld.Q_prev, c, m);
+    st_halo(io.hm + (size_t)y * io.pitch + x, m.psi, m.fs, m.phi);
 }
 
-// A tile-edge cell's record, for the halos of its neighbour tiles (no other
-// tile reads the inner cells).
+// The ring cell (x, y) of a tile, loaded from its halo record and its
+// previous-step (p, S).
+template <typename T>
+struct RingLoad {
+    T psi, fs, phi, p, S;
+};
 template <typename S, typename T, typename A>
-__device__ __forceinline__ void publish_cell(const StepIO<S, T, A> &io, uint32_t k, const Macro<T> &m) {
-    st_rec(io.pub + k, m.psi, m.fs, m.phi, io.epoch);
+__device__ __forceinline__ void ring_load(const StepIO<S, T, A> &io, int x, int y, RingLoad<T> &r) {
+    const uint32_t P = (uint32_t)io.plane;
+    const uint32_t k = (uint32_t)y * (uint32_t)io.pitch + (uint32_t)x;
+    ld_halo(io.hm + k, r.psi, r.fs, r.phi);
+    r.p = T(io.aux_in[AUX_P * P + k]);
+    r.S = T(io.aux_in[AUX_S * P + k]);
+}
+// ... into the extended tile slot (ex, ey): rho and eps by the property law
+// from (psi, f_s), as local_macros evaluates them.
+template <typename T, int BY, typename OB>
+__device__ __forceinline__ void ring_to_smem(const Consts<T> &c, const RingLoad<T> &r, TileSmem<T, BY> &sm, int ex,
+                                             int ey, OB *ob) {
+    Macro<T> m;
+    m.psi = r.psi;
+    m.fs = r.fs;
+    m.phi = r.phi;
+    m.rho = chi(m.fs, m.psi, c.rho);
+    m.eps = chi(m.fs, m.psi, c.eps);
+    m.H = T(0);
+    m.T_ = T(0);
+    sm.q[ey][ex] = {m.psi, m.rho, m.eps, m.phi};
+    sm.ps[ey][ex] = {r.p, r.S};
+    if constexpr (!std::is_same<OB, NoObs>::value) ob->macro(ey, ex, m);
 }
 
 // Asynchronous global -> shared copy of one 4- or 8-byte element.
@@ -703,19 +667,17 @@ __device__ __forceinline__ void fill_ghosts(TileSmem<T, BY> &sm, const Consts<T>
     }
 }
 
-// Row a2-a9 for one own cell: stencils from the shared-memory tile, forces,
+// The rest of the step for one own cell: stencils from the shared-memory tile, forces,
 // flow macros, the four collisions and the write-back of the post-collision
 // populations through the AA pattern from phase PH (l: io.lph).  PS
 // supplies the cell's time-n populations (registers or shared memory).
 // EDGE: the tile touches a wall row, so destinations may leave the lattice;
 // interior tiles skip the per-direction wall tests.
-// published: the cell stored a record this step, which must be visible
-// before the cell overwrites its first slot.
 template <typename S, typename T, typename A, int BY, bool EDGE, int PH, typename PopSrc, typename OB = NoObs>
 __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh,
                                           const TileSmem<T, BY> &sm, const PopSrc &PS, int tx, int ty, int x,
                                           int y, const Macro<T> &m, T fs_prev, T pux_prev, T puy_prev,
-                                          bool published, OB *ob = nullptr) {
+                                          OB *ob = nullptr) {
     const int nx = io.nx, ny = io.ny;
     const uint32_t P = (uint32_t)io.plane;   // 32-bit offsets (checked at creation)
     const uint32_t pitch = (uint32_t)io.pitch;
@@ -794,11 +756,8 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     for (int i = 1; i < 9; i++) sh_ += PS.h(i);
     const T p = cs2<T>() / (T(1) - w9<T>(0)) * (sh_ + T(0.5) * Sn + tau_h * R0 + r * s_i<T>(0, ux, uy));
 
-    // ---- collisions + in-place streaming (a5-a9) ---------------------------
+    // ---- collisions + in-place streaming ---------------------------------
     const int xm = (x == 0) ? nx - 1 : x - 1, xp = (x == nx - 1) ? 0 : x + 1;
-    // the record (stored in phase 1) before the first slot write; by now the
-    // store has long completed, so the fence waits for nothing
-    if (published) fence_gpu();
     const T uu_ = ux * ux + uy * uy;
     const T B15 = T(1.5) * uu_;                    // u.u / (2 c_s^2)
 
@@ -986,7 +945,6 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
     const int x = own ? x0 + tx : 0;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const uint32_t k = (uint32_t)y * pitch + (uint32_t)x;
-    const bool edge = tx == 0 || tx == ncols - 1 || ty == 0 || ty == BY - 1;
     Macro<T> m;
     T fs_prev = T(0), mdot_prev = T(0), Q_prev = T(0), pux_prev = T(0), puy_prev = T(0);
     constexpr int NRING = 2 * 34 + 2 * BY;
@@ -1039,13 +997,8 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             pv = T(io.aux_in[AUX_P * P + k]);
             Sv = T(io.aux_in[AUX_S * P + k]);
         }
-        CellLoad<T> rl;
-        T rp = T(0), rS = T(0);
-        ExtRec<T> rr;
-        if (ring) {
-            load_cell_aa<S, T, A, PH>(io, c, sh, rhx, rhy, rl, rp, rS);
-            rr = ext_record(io, rhx, rhy, rl);    // issued once the ring loads are back
-        }
+        RingLoad<T> rl;
+        if (ring) ring_load(io, rhx, rhy, rl);
         if (own) {
             cp_async_wait_all();
             if (ncols == 32) __syncwarp();   // a full row's planes were copied by the whole warp
@@ -1062,16 +1015,9 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             local_macros(f, g, l1234, fs_prev, mdot_prev, Q_prev, c, m);
             sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
             sm.ps[ty + 1][tx + 1] = {pv, Sv};
-            if (edge) publish_cell<S, T, A>(io, k, m);
             if constexpr (OBS) ob->macro(ty + 1, tx + 1, m);
         }
-        if (ring) {
-            Macro<T> mr;
-            resolve_ext<T>(c, rl, rr, mr);
-            sm.q[rey][rex] = {mr.psi, mr.rho, mr.eps, mr.phi};
-            sm.ps[rey][rex] = {rp, rS};
-            if constexpr (OBS) ob->macro(rey, rex, mr);
-        }
+        if (ring) ring_to_smem<T, BY, OB>(c, rl, sm, rex, rey, ob);
     } else {
         // ---- phase 1: own cell (kept in registers) -------------------------
         Refs<T> rf;
@@ -1110,23 +1056,30 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
             for (int i = 0; i < 5; i++) stash[27 + i][ty][tx] = l[i];
             sm.q[ty + 1][tx + 1] = {m.psi, m.rho, m.eps, m.phi};
             sm.ps[ty + 1][tx + 1] = {T(io.aux_in[AUX_P * P + k]), T(io.aux_in[AUX_S * P + k])};
-            if (edge) publish_cell<S, T, A>(io, k, m);
             if constexpr (OBS) ob->macro(ty + 1, tx + 1, m);
         }
-        // ---- phase 1: halo ring, from the neighbours' populations or records
-        if (ring) ext_to_smem<S, T, A, BY, PH, OB>(io, c, sh, sm, rex, rey, rhx, rhy, ob);
+        // ---- phase 1: halo ring, from the halo records
+        if (ring) {
+            RingLoad<T> rl;
+            ring_load(io, rhx, rhy, rl);
+            ring_to_smem<T, BY, OB>(c, rl, sm, rex, rey, ob);
+        }
     }
     // the wrap-around neighbour of a ragged tile's last column
-    if (wrap) ext_to_smem<S, T, A, BY, PH, OB>(io, c, sh, sm, tx + 1, ty + 1, 0, y, ob);
+    if (wrap) {
+        RingLoad<T> rl;
+        ring_load(io, 0, y, rl);
+        ring_to_smem<T, BY, OB>(c, rl, sm, tx + 1, ty + 1, ob);
+    }
     __syncthreads();
     fill_ghosts<T, BY>(sm, c, y0, ny, tid);
     __syncthreads();
     if (!own) return;
     const StashPops<T, BY> PS{stash, ty, tx};
     if (y0 == 0 || y0 + BY >= ny)
-        step_cell<S, T, A, BY, true, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, edge, ob);
+        step_cell<S, T, A, BY, true, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
     else
-        step_cell<S, T, A, BY, false, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, edge, ob);
+        step_cell<S, T, A, BY, false, PH>(io, c, sh, sm, PS, tx, ty, x, y, m, fs_prev, pux_prev, puy_prev, ob);
 }
 
 // Blocks per SM the single-precision step asks the register allocator for:
@@ -1161,9 +1114,53 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
     __shared__ TileSmem<T, BY> sm;
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
+    grid_dep_wait();                   // k_halo's records (and every earlier store)
+    grid_dep_release();                // the next step's k_halo waits for this grid's end
     load_counters(io, PH);
     advance_counters(io, PH, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
     step_tile<S, T, A, BY, PH, true>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
+}
+
+// The tile-edge cells of the 32 x BY tile at (x0, y0), one per thread of a
+// HALO_THREADS block: its bottom and top rows, then the inner cells of its
+// first and last columns.
+constexpr int HALO_THREADS = 128;
+template <typename S, typename T, typename A, int BY, int PH>
+__device__ __forceinline__ void halo_tile(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, int x0,
+                                          int y0, int j) {
+    static_assert(2 * 32 + 2 * (BY - 2) <= HALO_THREADS, "one edge cell per thread");
+    const int ncols = io.nx - x0 < 32 ? io.nx - x0 : 32;
+    int tx, ty;
+    if (j < ncols) {
+        tx = j;
+        ty = 0;
+    } else if (j < 2 * ncols) {
+        tx = j - ncols;
+        ty = BY - 1;
+    } else {
+        const int r = j - 2 * ncols;
+        if (r < BY - 2) {
+            tx = 0;
+            ty = 1 + r;
+        } else if (r < 2 * (BY - 2) && ncols > 1) {
+            tx = ncols - 1;
+            ty = 1 + r - (BY - 2);
+        } else {
+            return;
+        }
+    }
+    const int y = y0 + ty;
+    if (y >= io.ny) return;
+    halo_cell<S, T, A, PH>(io, c, sh, x0 + tx, y);
+}
+
+// First launch of a step: the halo records of every tile-edge cell, from
+// the populations the step before left (layout phase PH, l: io.lph).
+template <typename S, typename T, typename A, int BY, int PH>
+__global__ void __launch_bounds__(HALO_THREADS) k_halo(StepIO<S, T, A> io, Consts<T> c, Shift sh) {
+    grid_dep_wait();                   // the populations of the step before
+    grid_dep_release();
+    halo_tile<S, T, A, BY, PH>(io, c, sh, blockIdx.x * 32, blockIdx.y * BY, threadIdx.x);
 }
 
 // Batched form: blocks walk a flat list of tiles of many instances.  The
@@ -1192,6 +1189,8 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_batch_ste
     constexpr int NC = int(sizeof(Consts<T>) / sizeof(T));
     static_assert(sizeof(Consts<T>) == NC * sizeof(T), "Consts holds only T");
     const int tid = threadIdx.y * 32 + threadIdx.x;
+    grid_dep_wait();
+    grid_dep_release();
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
         const int item = tile_item[t];
         if (tid < NC) reinterpret_cast<T *>(&s_c)[tid] = reinterpret_cast<const T *>(consts + item)[tid];
@@ -1208,6 +1207,28 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_batch_ste
         else
             step_tile<S, T, A, BY, 0>(io, s_c, it.sh, sm, stash, bx * 32, by * BY);
         __syncthreads();
+    }
+}
+
+// Batched form of k_halo over the same work list.
+template <typename S, typename T, typename A, int BY>
+__global__ void __launch_bounds__(HALO_THREADS) k_batch_halo(const BatchItem *__restrict__ items,
+                                                             const Consts<T> *__restrict__ consts,
+                                                             const int *__restrict__ tile_item, int total_tiles,
+                                                             int flip_cur, int flip_l) {
+    grid_dep_wait();
+    grid_dep_release();
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const int item = tile_item[t];
+        const BatchItem &it = items[item];
+        const int local = t - it.tile_begin;
+        const int bx = local % it.tiles_x, by = local / it.tiles_x;
+        const int cur = it.cur ^ flip_cur;
+        const StepIO<S, T, A> io = step_io<S, T, A>(it.s, cur, it.lcur ^ flip_l, it.write_sigma);
+        if (cur)
+            halo_tile<S, T, A, BY, 1>(io, consts[item], it.sh, bx * 32, by * BY, threadIdx.x);
+        else
+            halo_tile<S, T, A, BY, 0>(io, consts[item], it.sh, bx * 32, by * BY, threadIdx.x);
     }
 }
 

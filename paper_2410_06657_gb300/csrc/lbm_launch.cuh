@@ -2,10 +2,31 @@
 // S, T, A) defines the launch_*_SUFFIX functions declared in lbm_internal.h.
 #pragma once
 
+#include <utility>
+
 #include "lbm_kernels.cuh"
 #include "lbm_observe.cuh"
 
 namespace lbm {
+
+// Launch with programmatic stream serialisation: the kernel may start while
+// the one before it in the stream drains, and synchronises with it through
+// grid_dep_wait() (lbm_kernels.cuh) before it reads what that kernel wrote.
+template <typename... P, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Resident blocks per SM of the batched step: the persistent grid is exactly
 // the device's resident capacity, so every block starts at once and the
@@ -37,9 +58,12 @@ cudaError_t launch_batch_step_by(const BatchItem *items, const Consts<T> *c, con
     static std::atomic<unsigned long long> ready{0ull};
     cudaError_t e = allow_dynamic_smem(k_batch_step<S, T, A, BY>, stash_bytes<T, BY>(), ready);
     if (e != cudaSuccess) return e;
-    k_batch_step<S, T, A, BY><<<grid, dim3(32, BY), stash_bytes<T, BY>(), st>>>(items, c, tile_item, total_tiles,
-                                                                                flip_cur, flip_l);
-    return cudaGetLastError();
+    const int hgrid = total_tiles < 4 * grid ? total_tiles : 4 * grid;
+    e = launch_dependent(k_batch_halo<S, T, A, BY>, dim3(hgrid), dim3(HALO_THREADS), 0, st, items, c, tile_item,
+                         total_tiles, flip_cur, flip_l);
+    if (e != cudaSuccess) return e;
+    return launch_dependent(k_batch_step<S, T, A, BY>, dim3(grid), dim3(32, BY), stash_bytes<T, BY>(), st, items, c,
+                            tile_item, total_tiles, flip_cur, flip_l);
 }
 
 template <typename S, typename T, typename A>
@@ -62,33 +86,43 @@ cudaError_t launch_batch_sweep_t(const BatchItem *items, const void *consts, int
     return cudaGetLastError();
 }
 
-// The fused step of one instance, tile height BY, from layout phase PH.
+// The halo records of a step (first launch of every step).
+template <typename S, typename T, typename A, int BY, int PH>
+cudaError_t launch_halo_ph(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, dim3 grid,
+                           cudaStream_t st) {
+    return launch_dependent(k_halo<S, T, A, BY, PH>, grid, dim3(HALO_THREADS), 0, st, io, c, sh);
+}
+
+// The fused step of one instance, tile height BY, from layout phase PH:
+// its halo records, then the step itself.
 template <typename S, typename T, typename A, int BY, int PH>
 cudaError_t launch_step_ph(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, dim3 grid,
                            cudaStream_t st) {
     static std::atomic<unsigned long long> ready{0ull};
     cudaError_t e = allow_dynamic_smem(k_step<S, T, A, BY, PH>, stash_bytes<T, BY>(), ready);
     if (e != cudaSuccess) return e;
-    k_step<S, T, A, BY, PH><<<grid, dim3(32, BY), stash_bytes<T, BY>(), st>>>(io, c, sh);
-    return cudaGetLastError();
+    e = launch_halo_ph<S, T, A, BY, PH>(io, c, sh, grid, st);
+    if (e != cudaSuccess) return e;
+    return launch_dependent(k_step<S, T, A, BY, PH>, grid, dim3(32, BY), stash_bytes<T, BY>(), st, io, c, sh);
 }
 
 template <typename S, typename T, typename A, int BY>
 cudaError_t launch_step_by(const DevState &s, int cur, int lcur, int write_sigma, const Consts<T> &c, const Shift &sh,
-                           cudaStream_t st) {
+                           int variant, cudaStream_t st) {
     const dim3 grid((s.nx + 31) / 32, (s.ny + BY - 1) / BY);
     const StepIO<S, T, A> io = step_io<S, T, A>(s, cur, lcur, write_sigma);
+    if (variant != LBM_STEP_DIRECT) return cudaErrorInvalidValue;
     return cur ? launch_step_ph<S, T, A, BY, 1>(io, c, sh, grid, st) : launch_step_ph<S, T, A, BY, 0>(io, c, sh, grid, st);
 }
 
 template <typename S, typename T, typename A>
 cudaError_t launch_step_t(const DevState &s, int cur, int lcur, int write_sigma, const void *consts, const Shift &sh,
-                          int tile_rows, cudaStream_t st) {
+                          int tile_rows, int variant, cudaStream_t st) {
     const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);
     switch (tile_rows) {
-    case 4: return launch_step_by<S, T, A, 4>(s, cur, lcur, write_sigma, c, sh, st);
-    case 8: return launch_step_by<S, T, A, 8>(s, cur, lcur, write_sigma, c, sh, st);
-    case 16: return launch_step_by<S, T, A, 16>(s, cur, lcur, write_sigma, c, sh, st);
+    case 4: return launch_step_by<S, T, A, 4>(s, cur, lcur, write_sigma, c, sh, variant, st);
+    case 8: return launch_step_by<S, T, A, 8>(s, cur, lcur, write_sigma, c, sh, variant, st);
+    case 16: return launch_step_by<S, T, A, 16>(s, cur, lcur, write_sigma, c, sh, variant, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -100,8 +134,10 @@ cudaError_t launch_step_obs_ph(const StepIO<S, T, A> &io, const Consts<T> &c, co
     static std::atomic<unsigned long long> ready{0ull};
     cudaError_t e = allow_dynamic_smem(k_step_obs<S, T, A, BY, PH>, stash_bytes<T, BY>(), ready);
     if (e != cudaSuccess) return e;
-    k_step_obs<S, T, A, BY, PH><<<grid, dim3(32, BY), stash_bytes<T, BY>(), st>>>(io, c, sh, w, sc);
-    return cudaGetLastError();
+    e = launch_halo_ph<S, T, A, BY, PH>(io, c, sh, grid, st);
+    if (e != cudaSuccess) return e;
+    return launch_dependent(k_step_obs<S, T, A, BY, PH>, grid, dim3(32, BY), stash_bytes<T, BY>(), st, io, c, sh, w,
+                            sc);
 }
 
 template <typename S, typename T, typename A, int BY>
@@ -155,8 +191,9 @@ cudaError_t launch_step_obs_t(const DevState &s, int cur, int lcur, int write_si
 #define LBM_DEFINE_LAUNCHERS(SUFFIX, S, T, A)                                                              \
     namespace lbm {                                                                                         \
     cudaError_t launch_step_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,                 \
-                                     const void *consts, const Shift &sh, int tile_rows, cudaStream_t st) { \
-        return launch_step_t<S, T, A>(s, cur, lcur, write_sigma, consts, sh, tile_rows, st);                \
+                                     const void *consts, const Shift &sh, int tile_rows, int variant,       \
+                                     cudaStream_t st) {                                                     \
+        return launch_step_t<S, T, A>(s, cur, lcur, write_sigma, consts, sh, tile_rows, variant, st);       \
     }                                                                                                       \
     cudaError_t launch_sweep_##SUFFIX(const DevState &s, int lcur, int cur, uint32_t sr_sys,               \
                                       const void *consts, const Shift &sh, cudaStream_t st) {               \

@@ -139,10 +139,9 @@ extern "C" int lbm_observables_noalloc(const lbm_params *p, const void *pop, con
     s.pop = const_cast<void *>(pop);          // natural layout (phase 0)
     s.aux[0] = s.aux[1] = const_cast<void *>(aux);
     s.sigma = nullptr;
-    s.pub = nullptr;
+    s.halo = nullptr;
     s.err = nullptr;
     s.rng = nullptr;
-    s.epoch = nullptr;
     s.nx = p->nx;
     s.ny = p->ny;
     s.pitch = pitch;

@@ -1,4 +1,4 @@
-// Observables (row a10), the substrate heat flux and field access of the
+// Observables, the substrate heat flux and field access of the
 // phase-field LB electrofreezing step (arXiv 2410.06657), templated like
 // the step kernels in lbm_kernels.cuh (storage type S, arithmetic type T,
 // auxiliary type A).  Included once by each precision's translation unit,
@@ -10,7 +10,7 @@
 namespace lbm {
 
 // ---------------------------------------------------------------------------
-// Observables (row a10): FP64 reductions over the tile grid.  Each block
+// Observables: FP64 reductions over the tile grid.  Each block
 // handles a 32 x 8 tile plus a one-cell halo (for q_v's stencils and the
 // interface crossings) and leaves block partial sums and order-independent
 // max/min candidates in the workspace; the last block of each group of
@@ -520,7 +520,7 @@ struct StepObs {
     }
 };
 
-// One step (rows a1-a9) that also reduces the observables (row a10) of the
+// One step that also reduces the observables of the
 // state it starts from.  io, rng, cur as for k_step; `ws` carries this
 // grid's block and group counts.
 template <typename S, typename T, typename A, int BY, int PH>
@@ -530,6 +530,8 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
     __shared__ T s_fs[BY + 2][34], s_Tm[BY + 2][34];
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
+    grid_dep_wait();
+    grid_dep_release();
     load_counters(io, PH);
     advance_counters(io, PH, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
     StepObs<T, BY> ob;

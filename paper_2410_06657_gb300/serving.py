@@ -29,7 +29,7 @@ STORAGE_BYTES = {lbm.FP64: 8, lbm.FP32: 4, lbm.FP16S: 2}
 def footprint_bytes(params: dict) -> int:
     """Device bytes of one instance: ONE population copy (9 f planes and 23
     h, g, l planes, streamed in place), two copies of the 7 auxiliary planes,
-    sigma, the stamped edge records (16 bytes per cell, 48 in FP64) and the
+    sigma, the halo records (16 bytes per cell, 32 in FP64) and the
     reduction workspace, rows padded to 32 elements."""
     nx, ny, prec = int(params["nx"]), int(params["ny"]), int(params["precision"])
     pitch = (nx + 31) // 32 * 32
@@ -37,7 +37,7 @@ def footprint_bytes(params: dict) -> int:
     sb = STORAGE_BYTES[prec]
     fb = 8 if prec == lbm.FP64 else 4        # half storage keeps f in single precision
     ab = 8 if prec == lbm.FP64 else 4        # auxiliary and arithmetic type
-    rec = 48 if prec == lbm.FP64 else 16
+    rec = 32 if prec == lbm.FP64 else 16
     blocks = ((nx + 31) // 32) * ((ny + 7) // 8)
     ws = blocks * 7 * 8 + (3 * ny + 8) * 8 + nx * 8 + 4096
     return (9 * fb + 23 * sb) * plane + 2 * 7 * plane * ab + plane * ab + rec * plane + ws
