@@ -612,7 +612,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // population l_0 is in place in either layout, l_1..4 are then gathered by
 // the caller).  A quarter (FP32) or half (FP64) of the instructions of one
 // copy per element.
-template <typename T, int BY>
+// CG: the copies bypass L1 (cp.async.cg).
+template <typename T, int BY, bool CG = false>
 __device__ __forceinline__ void stash_row_async(T (*stash)[BY][32], int ty, int tx, const T *pin,
                                                 const T *lin, uint32_t P, uint32_t k0, bool l_all) {
     constexpr int CR = 32 * int(sizeof(T)) / 16;    // 16-byte chunks per row
@@ -632,7 +633,10 @@ __device__ __forceinline__ void stash_row_async(T (*stash)[BY][32], int ty, int 
         else
             src = q < 27 ? pin + ((uint32_t)q * P + k0) : lin + ((uint32_t)(q - 27) * P + k0);
         const unsigned d = (unsigned)__cvta_generic_to_shared(&stash[q][ty][part * EPC]);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + part * EPC) : "memory");
+        if constexpr (CG)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + part * EPC) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + part * EPC) : "memory");
     }
 }
 
@@ -924,8 +928,13 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
 // One 32 x BY tile at (x0, y0) from layout phase PH (l: io.lph).
 // ASYNC: the own cell's populations reach the stash by cp.async while the
 // ring cell's loads are in flight (single-instance kernels; the batched
-// kernel's extra live state would spill with it).
-template <typename S, typename T, typename A, int BY, int PH, bool ASYNC = false, typename OB = NoObs>
+// kernel's extra live state would spill with it).  EARLY: the kernel was
+// launched as a dependent of k_halo and has not waited for it yet; a full
+// row in the natural layout is then copied from L2 (bypassing L1, whose
+// lines may predate the step before) before the wait, so the copies overlap
+// the end of k_halo, and everything else is read after it.
+template <typename S, typename T, typename A, int BY, int PH, bool ASYNC = false, typename OB = NoObs,
+          bool EARLY = false>
 __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Consts<T> &c,
                                           const Shift &sh, TileSmem<T, BY> &sm, T (*stash)[BY][32], int x0,
                                           int y0, OB *ob = nullptr) {
@@ -966,8 +975,12 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
         // from global to the stash (cp.async, no registers), the ring cell's
         // loads are issued meanwhile, so both wait for memory once
         T pv = T(0), Sv = T(0);
+        const bool early = EARLY && PH == 0 && ncols == 32 && io.lph == 0;
+        if (EARLY && !early) grid_dep_wait();
         if (own) {
-            if (PH == 0 && ncols == 32) {
+            if (early) {
+                stash_row_async<T, BY, true>(stash, ty, tx, io.f, io.l, P, (uint32_t)y * pitch + (uint32_t)x0, true);
+            } else if (PH == 0 && ncols == 32) {
                 // natural layout, full row: each warp copies its row in
                 // 16-byte chunks (l_1..4 gathered if l is swapped)
                 stash_row_async<T, BY>(stash, ty, tx, io.f, io.l, P, (uint32_t)y * pitch + (uint32_t)x0,
@@ -989,14 +1002,25 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
                 for (int i = 0; i < 5; i++)
                     cp_async_elem(&stash[27 + i][ty][tx], io.l + aa_src<5>(io.lph, i, P, pitch, x, y, xm, xp, ny));
             }
-            pux_prev = T(io.aux_in[AUX_PUX * P + k]);
-            puy_prev = T(io.aux_in[AUX_PUY * P + k]);
-            fs_prev = T(io.aux_in[AUX_FS * P + k]);
-            mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
-            Q_prev = T(io.aux_in[AUX_Q * P + k]);
-            pv = T(io.aux_in[AUX_P * P + k]);
-            Sv = T(io.aux_in[AUX_S * P + k]);
+            if (early) {
+                pux_prev = T(__ldcg(io.aux_in + (AUX_PUX * P + k)));
+                puy_prev = T(__ldcg(io.aux_in + (AUX_PUY * P + k)));
+                fs_prev = T(__ldcg(io.aux_in + (AUX_FS * P + k)));
+                mdot_prev = T(__ldcg(io.aux_in + (AUX_MDOT * P + k)));
+                Q_prev = T(__ldcg(io.aux_in + (AUX_Q * P + k)));
+                pv = T(__ldcg(io.aux_in + (AUX_P * P + k)));
+                Sv = T(__ldcg(io.aux_in + (AUX_S * P + k)));
+            } else {
+                pux_prev = T(io.aux_in[AUX_PUX * P + k]);
+                puy_prev = T(io.aux_in[AUX_PUY * P + k]);
+                fs_prev = T(io.aux_in[AUX_FS * P + k]);
+                mdot_prev = T(io.aux_in[AUX_MDOT * P + k]);
+                Q_prev = T(io.aux_in[AUX_Q * P + k]);
+                pv = T(io.aux_in[AUX_P * P + k]);
+                Sv = T(io.aux_in[AUX_S * P + k]);
+            }
         }
+        if (EARLY && early) grid_dep_wait();      // k_halo's records
         RingLoad<T> rl;
         if (ring) ring_load(io, rhx, rhy, rl);
         if (own) {
@@ -1114,17 +1138,24 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
     __shared__ TileSmem<T, BY> sm;
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
-    grid_dep_wait();                   // k_halo's records (and every earlier store)
+    // FP32 and FP64 wait for k_halo inside step_tile (after copying what
+    // does not depend on it); half storage reads its rounding counter first
+    constexpr bool EARLY = std::is_same<S, T>::value && std::is_same<typename FStore<S>::type, S>::value;
+    if constexpr (!EARLY) grid_dep_wait();
     grid_dep_release();                // the next step's k_halo waits for this grid's end
     load_counters(io, PH);
     advance_counters(io, PH, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
-    step_tile<S, T, A, BY, PH, true>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
+    step_tile<S, T, A, BY, PH, true, NoObs, EARLY>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY);
 }
 
 // The tile-edge cells of the 32 x BY tile at (x0, y0), one per thread of a
 // HALO_THREADS block: its bottom and top rows, then the inner cells of its
 // first and last columns.
-constexpr int HALO_THREADS = 128;
+constexpr int HALO_THREADS = 96;
+// Blocks per SM the halo kernels ask the register allocator for: each
+// thread only loads and sums, so many blocks keep more loads in flight.
+template <typename T>
+constexpr int halo_min_blocks() { return sizeof(T) == 8 ? 8 : 16; }
 template <typename S, typename T, typename A, int BY, int PH>
 __device__ __forceinline__ void halo_tile(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, int x0,
                                           int y0, int j) {
@@ -1157,7 +1188,8 @@ __device__ __forceinline__ void halo_tile(const StepIO<S, T, A> &io, const Const
 // First launch of a step: the halo records of every tile-edge cell, from
 // the populations the step before left (layout phase PH, l: io.lph).
 template <typename S, typename T, typename A, int BY, int PH>
-__global__ void __launch_bounds__(HALO_THREADS) k_halo(StepIO<S, T, A> io, Consts<T> c, Shift sh) {
+__global__ void __launch_bounds__(HALO_THREADS, halo_min_blocks<T>()) k_halo(StepIO<S, T, A> io, Consts<T> c,
+                                                                             Shift sh) {
     grid_dep_wait();                   // the populations of the step before
     grid_dep_release();
     halo_tile<S, T, A, BY, PH>(io, c, sh, blockIdx.x * 32, blockIdx.y * BY, threadIdx.x);
@@ -1212,7 +1244,7 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>()) k_batch_ste
 
 // Batched form of k_halo over the same work list.
 template <typename S, typename T, typename A, int BY>
-__global__ void __launch_bounds__(HALO_THREADS) k_batch_halo(const BatchItem *__restrict__ items,
+__global__ void __launch_bounds__(HALO_THREADS, halo_min_blocks<T>()) k_batch_halo(const BatchItem *__restrict__ items,
                                                              const Consts<T> *__restrict__ consts,
                                                              const int *__restrict__ tile_item, int total_tiles,
                                                              int flip_cur, int flip_l) {
