@@ -317,18 +317,19 @@ def run_gpu(args, world, rank, local):
     flush_l2 = L2Flush()
 
     obs_every = args.obs_every
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # the clock sampler starts before the warm-up steps, so the timed steps
+    # follow the warm-up without an idle gap
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    sampler.start()
+    time.sleep(0.3)
     for i in range(args.warmup):
         flush_l2()
         if i % obs_every == 0:
             sim.observables_deferred()
         sim.step(1)
     torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
-    sampler.start()
-    time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
     # two events bracket each step.  Every obs_every-th step also reduces the

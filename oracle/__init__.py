@@ -6,8 +6,9 @@ package.  The GPU library never calls it and shares no code with it: the C
 source in ``lbm_oracle.c`` is a separate, slow, loop-by-loop transcription of
 the paper's equations (Secs. 2-3, Algorithm 1) in double precision.
 
-Functions whose parity is not pinned by a closed form or invariant say so in
-their docstring ("parity unpinned").
+Every function is pinned by a closed form, an invariant or a value the
+paper prints (tests/test_oracle_pins.py); tests/test_oracle_mutants.py
+checks that those pins reject copies with a term dropped or flipped.
 """
 from __future__ import annotations
 
