@@ -13,6 +13,14 @@ Every member advances by whole chunks from its own admission, so its
 observables are taken at the same step counts as when it runs alone with the
 same cadence: in FP64 the results are identical alone and in the mix.
 
+The host works one chunk behind the GPU: a tick enqueues the next chunk
+(and the copy of every member's observables into page-locked host memory)
+before it reads the observables of the chunk before, so the GPU is never
+idle while the host decides retirements and admissions.  A member that
+turns out to be finished has then run one more chunk, which is discarded;
+its result is the observation that finished it, and its memory is freed
+once that extra chunk has completed.
+
 Scheduling is host logic only; all arithmetic runs in the library's kernels.
 """
 from __future__ import annotations
@@ -100,6 +108,9 @@ class Server:
         self._batch = None
         self._members = None
         self._t0 = None
+        self._inflight = None           # (members, events, host buffers) of the chunk on the GPU
+        self._retiring = []             # (simulation, bytes) to free once the in-flight chunk is done
+        self._old_batches = []          # batches whose launches may still be in flight
 
     # -- time ------------------------------------------------------------
     def now(self) -> float:
@@ -130,47 +141,81 @@ class Server:
 
     # -- one chunk of work ------------------------------------------------
     def tick(self) -> int:
-        """Admit what has arrived, advance every resident member by one chunk,
-        observe them and retire the frozen ones.  Returns members retired."""
+        """Admit what has arrived, enqueue one chunk for every resident
+        member with its observables, then read the observables of the
+        chunk before and retire the finished members.  Returns members
+        retired."""
         if self._t0 is None:
             self._t0 = self.clock()
         changed = self._admit(self.now())
-        if not self.active:
-            return 0
-        sims = [s for _, s, _, _ in self.active]
-        if changed or self._batch is None or self._members != [id(s) for s in sims]:
-            if self._batch is not None:
-                self._batch.close()
-            self._batch = lbm.Batch(sims, self.stream, tile_rows=self.tile_rows)
-            self._members = [id(s) for s in sims]
+        launched = None
+        if self.active:
+            sims = [s for _, s, _, _ in self.active]
+            if changed or self._batch is None or self._members != [id(s) for s in sims]:
+                if self._batch is not None:
+                    self._old_batches.append(self._batch)
+                self._batch = lbm.Batch(sims, self.stream, tile_rows=self.tile_rows)
+                self._members = [id(s) for s in sims]
+            launched = self._enqueue(list(self.active))
+        retired = self._collect()
+        self._inflight = launched
+        return retired
+
+    def _enqueue(self, members):
+        """One chunk of the current batch and every member's observables,
+        bracketed by two events; the observables land in page-locked host
+        memory (or are fetched synchronously without torch)."""
         ev = _events(self.stream)
+        bufs = _pinned(len(members)) if ev else None
         if ev:
             ev[0].record(ev[2])
         self._batch.step(self.chunk)
-        self.lattice_updates += self.chunk * sum(s.nx * s.ny for s in sims)
-        for s in sims:
-            s.observables_async()
+        for j, (_, sim, _, _) in enumerate(members):
+            if bufs is not None:
+                sim.observables_to_host(bufs.data_ptr() + j * _OBS_BYTES)
+            else:
+                sim.observables_async()
         if ev:
             ev[1].record(ev[2])
-        keep, retired = [], 0
-        for entry in self.active:
-            req, sim, adm, fp = entry
-            o = sim.observables_fetch()
-            done = o["t_fre"] >= 0 or o["frozen_fraction"] >= self.target
-            if done or sim.t >= self.max_steps or o["status"] != 0:
-                self.results.append(Result(req.id, req.arrival, adm, self.now(), sim.t, o["t_fre"],
-                                           done and o["status"] == 0, o))
-                sim.close()
-                self.used -= fp
-                retired += 1
-            else:
-                keep.append(entry)
+        return members, ev, bufs
+
+    def _collect(self) -> int:
+        """Wait for the chunk before, free what retired before it, read its
+        observations and retire the finished members."""
+        if self._inflight is None:
+            return 0
+        members, ev, bufs = self._inflight
+        self._inflight = None
         if ev:
-            self.gpu_busy_s += ev[0].elapsed_time(ev[1]) / 1e3    # the fetches synchronised
+            ev[1].synchronize()
+            self.gpu_busy_s += ev[0].elapsed_time(ev[1]) / 1e3
+        for sim, fp in self._retiring:      # their last chunk is the one just finished
+            sim.close()
+            self.used -= fp
+        self._retiring = []
+        for b in self._old_batches:
+            b.close()
+        self._old_batches = []
+        active_ids = {id(e[1]) for e in self.active}
+        retired = 0
+        for j, (req, sim, adm, fp) in enumerate(members):
+            if id(sim) not in active_ids:
+                continue                    # retired at the chunk before: this chunk is discarded
+            self.lattice_updates += self.chunk * sim.nx * sim.ny    # work that counts
+            if bufs is not None:
+                o = lbm.Obs.from_address(bufs.data_ptr() + j * _OBS_BYTES).as_dict()
+            else:
+                o = sim.observables_fetch()
+            done = o["t_fre"] >= 0 or o["frozen_fraction"] >= self.target
+            if done or o["step"] >= self.max_steps or o["status"] != 0:
+                self.results.append(Result(req.id, req.arrival, adm, self.now(), o["step"], o["t_fre"],
+                                           done and o["status"] == 0, o))
+                # the chunk enqueued after this one may still use its memory
+                self._retiring.append((sim, fp))
+                retired += 1
         if retired:
-            self.active = keep
-            self._batch.close()
-            self._batch = None
+            gone = {id(sim) for sim, _ in self._retiring}
+            self.active = [e for e in self.active if id(e[1]) not in gone]
         return retired
 
     def run(self, requests: Optional[List[Request]] = None, idle_sleep: float = 1e-3) -> List[Result]:
@@ -178,15 +223,45 @@ class Server:
         for r in requests or []:
             self.submit(r)
         self._t0 = self.clock()
-        while self.pending or self.active:
-            if not self.active and self.pending and self.pending[0].arrival > self.now():
+        while self.pending or self.active or self._inflight is not None:
+            if (not self.active and self._inflight is None and self.pending
+                    and self.pending[0].arrival > self.now()):
                 time.sleep(min(idle_sleep, self.pending[0].arrival - self.now()))
                 continue
             self.tick()
-        if self._batch is not None:
+        self.drain()
+        return sorted(self.results, key=lambda r: r.id)
+
+    def drain(self):
+        """Wait for the GPU and free everything retired."""
+        while self._inflight is not None:
+            self._collect()
+        # nothing was enqueued after the chunk just collected
+        for sim, fp in self._retiring:
+            sim.close()
+            self.used -= fp
+        self._retiring = []
+        for b in self._old_batches:
+            b.close()
+        self._old_batches = []
+        if self._batch is not None and not self.active:
             self._batch.close()
             self._batch = None
-        return sorted(self.results, key=lambda r: r.id)
+
+
+_OBS_BYTES = 0
+
+
+def _pinned(n: int):
+    """Page-locked host memory for n lbm_obs records (None without torch)."""
+    global _OBS_BYTES
+    try:
+        import ctypes
+        import torch
+        _OBS_BYTES = ctypes.sizeof(lbm.Obs)
+        return torch.empty(max(1, n) * _OBS_BYTES, dtype=torch.uint8, pin_memory=True)
+    except Exception:
+        return None
 
 
 def _events(stream):
