@@ -744,22 +744,36 @@ def run_regimes(args, world, rank, local):
     lbm.load()
     stream = torch.cuda.current_stream()
     prec = W.PRECISIONS[args.precision]
-    cases = [("field off", None, 0.0), ("PR+", "PR+", 0.2), ("OB-", "OB-", 0.2)]
+    # the configuration of Sec. 5.4, Fig. 14(b) (Ste = 0.2, theta = 120,
+    # CaE = 1, the whole region initially at T_m + (T_m - T_w) / 2) on the
+    # 512 x 256 lattice, R = 80
+    cases = [("field off", None, 0.0), ("OB-", "OB-", 1.0), ("PR-", "PR-", 1.0), ("PR+", "PR+", 1.0)]
     out, lu, t_gpu = [], 0, 0.0
+    t_off = None
     for name, regime, ca in cases:
         w = W.production(precision=prec, regime=regime, CaE=ca)
-        p = w["params"]
+        p = dict(w["params"], Ste=0.2, theta_deg=120.0, alpha_lg=0.2, rho_sl=0.9,
+                 T_init=0.5 * (w["params"]["T_m"] - w["params"]["T_w"]) + w["params"]["T_m"])
         sim = lbm.Simulation(p, stream)
         xc, yc = W.sessile_center(p["nx"], w["R"], p["theta_deg"])
         sim.init_droplet(w["R"], xc, yc, 0)
+        sim.presolve(1e-6, 200000)
+        probe = int(round(0.3125 * w["R"] ** 2 / p["alpha_l"]))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        o = _freeze(sim, 200, 400000)
+        sim.step(probe)
+        op = sim.observables()
+        o = _freeze(sim, 50, 1000000)
         torch.cuda.synchronize()
         t_gpu += time.perf_counter() - t0
         lu += p["nx"] * p["ny"] * sim.t
+        if regime is None:
+            t_off = o["t_fre"]
         rec = {"case": name, "t_fre": o["t_fre"], "Fo_fre": o["Fo_fre"], "aspect": o["aspect"],
-               "height": o["height"], "frozen_fraction": o["frozen_fraction"]}
+               "height": o["height"], "frozen_fraction": o["frozen_fraction"],
+               "height_at_Fo_0.3125": op["height"], "R_tr_at_Fo_0.3125": op["R_tr"]}
+        if t_off and o["t_fre"] > 0:
+            rec["t_star"] = (o["t_fre"] - t_off) / t_off
         if args.with_oracle and rank == 0:
             import oracle
             pc = dict(p, nx=128, ny=64, R0=w["R"] / 4, precision=W.FP64)
@@ -782,9 +796,10 @@ def run_regimes(args, world, rank, local):
             "metric": "MLUPS", "value": world * lu / t_gpu / 1e6, "unit": "MLUPS", "n_gpus": world,
             "steps": int(lu), "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": "production droplet 512x256 run to frozen fraction 0.99: field off, "
-                                   "PR+ (R_sigma=2, S=0.5), OB- (R_sigma=2, S=5), CaE=0.2",
-                       "observables_every": 200},
+            "config": {"workload": "droplet 512x256, R=80, run to frozen fraction 0.99 in the configuration of "
+                                   "Fig. 14(b): Ste=0.2, theta=120, CaE=1, initial T = T_m + (T_m - T_w)/2; "
+                                   "field off, OB- (R_sigma=2, S=5), PR- (5, 9.5), PR+ (2, 0.5)",
+                       "observables_every": 50},
             "cases": out,
         }))
 
