@@ -47,6 +47,7 @@ namespace lbm {
 __device__ constexpr int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 __device__ constexpr int OPP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+__device__ constexpr int PAIR9[4] = {1, 2, 5, 6};   // one direction of each opposite pair
 // D2Q5 (Sec. 3.4): rest; E, N, W, S.
 __device__ constexpr int CX5[5] = {0, 1, 0, -1, 0};
 __device__ constexpr int CY5[5] = {0, 0, 1, 0, -1};
@@ -769,32 +770,45 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
     {
         const T om = T(1) / tau_h;
         const T pre = FAST ? T(1) - T(0.5) * om : T(1) - T(1) / (T(2) * tau_h);
-        const T A3 = T(3) * p;                      // p / c_s^2
-        const T S3 = Sn - T(3) * uF;                // S - u.F~ / c_s^2
-        const T Gx = Fx + rfx, Gy = Fy + rfy;
+        auto put = [&](int i, T post) {
+            bool wall;
+            const uint32_t d = aa_dst<9, EDGE>(PH, i, P, pitch, x, y, xm, xp, ny, wall);
+            Pol<S, T>::st(io.h + d, post, T(0), sh.h_scale);   // walls: half-way bounce-back
+        };
+        if constexpr (FAST) {
+            // the rest direction, then every direction with its opposite:
+            // the parts of h_eq and R_i even in c_i are shared by the pair,
+            // the odd parts change sign
+            const T omc = T(1) - om;
+            const T A3 = T(3) * p;                      // p / c_s^2
+            const T S3 = Sn - T(3) * uF;                // S - u.F~ / c_s^2
+            const T Gx = Fx + rfx, Gy = Fy + rfy;
+            const T base = A3 - r * B15;
+            put(0, omc * PS.h(0) + om * (w9<T>(0) * base - A3) + pre * (w9<T>(0) * S3));
 #pragma unroll
-        for (int i = 0; i < 9; i++) {
-            T post;
-            if constexpr (FAST) {
+            for (int j = 0; j < 4; j++) {
+                const int i = PAIR9[j], o = OPP9[i];
+                const T w = w9<T>(i);
                 const T cu = cdot<T>(CX[i], CY[i], ux, uy);
                 const T cF = cdot<T>(CX[i], CY[i], Ftx, Fty);
                 const T cG = cdot<T>(CX[i], CY[i], Gx, Gy);
-                const T t = cu * (T(3) + T(4.5) * cu);   // c.u/c_s^2 + (c.u)^2/(2 c_s^4)
-                const T heq = (i == 0) ? w9<T>(0) * (A3 - r * B15) - A3 : w9<T>(i) * (A3 + r * (t - B15));
-                const T Ri = w9<T>(i) * (S3 + T(3) * cG + T(9) * cu * cF);
-                post = PS.h(i) + om * (heq - PS.h(i)) + pre * Ri;
-            } else {
+                // h_eq = w (A3 + r (3 c.u + 4.5 (c.u)^2 - B15)), R_i = w (S3 + 3 c.G + 9 (c.u)(c.F~))
+                const T ev = om * (w * (base + T(4.5) * r * cu * cu)) + pre * (w * (S3 + T(9) * cu * cF));
+                const T od = om * (T(3) * w * r * cu) + pre * (T(3) * w * cG);
+                put(i, omc * PS.h(i) + (ev + od));
+                put(o, omc * PS.h(o) + (ev - od));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
                 const T cu = cdot<T>(CX[i], CY[i], ux, uy);
                 const T cF = cdot<T>(CX[i], CY[i], Ftx, Fty);
                 const T Ri = w9<T>(i) * (Sn + cdot<T>(CX[i], CY[i], Fx + rfx, Fy + rfy) / cs2<T>() +
                                          (cu * cF - cs2<T>() * uF) / (cs2<T>() * cs2<T>()));
                 const T heq = ((i == 0) ? p / cs2<T>() * (w9<T>(0) - T(1)) : p / cs2<T>() * w9<T>(i)) +
                               r * s_i<T>(i, ux, uy);
-                post = PS.h(i) - (PS.h(i) - heq) / tau_h + pre * Ri;
+                put(i, PS.h(i) - (PS.h(i) - heq) / tau_h + pre * Ri);
             }
-            bool wall;
-            const uint32_t d = aa_dst<9, EDGE>(PH, i, P, pitch, x, y, xm, xp, ny, wall);
-            Pol<S, T>::st(io.h + d, post, T(0), sh.h_scale);   // walls: half-way bounce-back
         }
     }
     // a5: phase field
@@ -817,20 +831,7 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         const T pmd = ps * mdot;
         uint32_t rb[4] = {0u, 0u, 0u, 0u};
         if constexpr (Pol<typename FStore<S>::type, T>::shifted) sr_block(rb, k, io.sr_step, 0u);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            T post;
-            if constexpr (FAST) {
-                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-                const T feq = w9<T>(i) * ps * (T(1) + T(3) * cu);
-                const T Fi = w9<T>(i) * (T(3) * cdot<T>(CX[i], CY[i], ax, ay) + pmd);
-                post = PS.f(i) + om * (feq - PS.f(i)) + pre * Fi;
-            } else {
-                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-                const T feq = w9<T>(i) * ps * (T(1) + cu / cs2<T>());
-                const T Fi = w9<T>(i) * cdot<T>(CX[i], CY[i], ax, ay) / cs2<T>() + w9<T>(i) * ps * mdot;
-                post = PS.f(i) - (PS.f(i) - feq) / c.tau_f + pre * Fi;
-            }
+        auto put = [&](int i, T post) {
             bool wall;
             const uint32_t d = aa_dst<9, EDGE>(PH, i, P, pitch, x, y, xm, xp, ny, wall);
             T ref = T(0);
@@ -839,6 +840,30 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                 ref = wall ? ro.f[OPP9[i]] : ro.f[i];
             }
             Pol<typename FStore<S>::type, T>::st_sr(io.f + d, post, ref, sh.f_scale, bits13(rb, i));
+        };
+        if constexpr (FAST) {
+            // f_eq = w psi (1 + 3 c.u), F_i = w (3 c.a + psi mdot): even parts
+            // w (om psi + pre psi mdot) per weight, odd parts 3 w (om psi c.u + pre c.a)
+            const T omc = T(1) - om;
+            const T evw = om * ps + pre * pmd;
+            put(0, omc * PS.f(0) + w9<T>(0) * evw);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int i = PAIR9[j], o = OPP9[i];
+                const T w = w9<T>(i);
+                const T ev = w * evw;
+                const T od = T(3) * w * (om * ps * cdot<T>(CX[i], CY[i], ux, uy) + pre * cdot<T>(CX[i], CY[i], ax, ay));
+                put(i, omc * PS.f(i) + (ev + od));
+                put(o, omc * PS.f(o) + (ev - od));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                const T feq = w9<T>(i) * ps * (T(1) + cu / cs2<T>());
+                const T Fi = w9<T>(i) * cdot<T>(CX[i], CY[i], ax, ay) / cs2<T>() + w9<T>(i) * ps * mdot;
+                put(i, PS.f(i) - (PS.f(i) - feq) / c.tau_f + pre * Fi);
+            }
         }
     }
     // a8: enthalpy (Sec. 3.3)
@@ -852,24 +877,7 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
         const T CT = c.Cref * m.T_, cpT = cp * m.T_;
         uint32_t rb[4] = {0u, 0u, 0u, 0u};
         if constexpr (Pol<S, T>::shifted) sr_block(rb, k, io.sr_step, 2u);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            T post;
-            if constexpr (FAST) {
-                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-                const T t = cu * (T(3) + T(4.5) * cu);
-                const T geq = (i == 0) ? m.H - CT + w9<T>(0) * (CT - cpT * B15) : w9<T>(i) * (CT + cpT * (t - B15));
-                post = PS.g(i) + om * (geq - PS.g(i)) + pre * (w9<T>(i) * Qn);
-            } else {
-                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
-                T geq;
-                if (i == 0)
-                    geq = m.H - c.Cref * m.T_ + w9<T>(0) * cp * m.T_ * (c.Cref / cp - uu / (T(2) * cs2<T>()));
-                else
-                    geq = w9<T>(i) * cp * m.T_ *
-                          (c.Cref / cp + cu / cs2<T>() + (cu * cu - cs2<T>() * uu) / (T(2) * cs2<T>() * cs2<T>()));
-                post = PS.g(i) - (PS.g(i) - geq) / tau_g + pre * (w9<T>(i) * Qn);
-            }
+        auto put = [&](int i, T post) {
             bool wall;
             const uint32_t d = aa_dst<9, EDGE>(PH, i, P, pitch, x, y, xm, xp, ny, wall);
             // cold wall: anti-bounce-back to C_p,ref T_w; top wall: adiabatic bounce-back
@@ -880,6 +888,35 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
                 ref = wall ? ro.g[OPP9[i]] : ro.g[i];
             }
             Pol<S, T>::st_sr(io.g + d, val, ref, sh.g_scale, bits13(rb, i));
+        };
+        if constexpr (FAST) {
+            // g_eq = w (C T + C_p T (3 c.u + 4.5 (c.u)^2 - B15)): even part
+            // shared by a direction and its opposite, odd part 3 w C_p T c.u
+            const T omc = T(1) - om;
+            const T base = CT - cpT * B15;
+            put(0, omc * PS.g(0) + om * (m.H - CT + w9<T>(0) * base) + pre * (w9<T>(0) * Qn));
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int i = PAIR9[j], o = OPP9[i];
+                const T w = w9<T>(i);
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                const T ev = om * (w * (base + T(4.5) * cpT * cu * cu)) + pre * (w * Qn);
+                const T od = om * (T(3) * w * cpT * cu);
+                put(i, omc * PS.g(i) + (ev + od));
+                put(o, omc * PS.g(o) + (ev - od));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                const T cu = cdot<T>(CX[i], CY[i], ux, uy);
+                T geq;
+                if (i == 0)
+                    geq = m.H - c.Cref * m.T_ + w9<T>(0) * cp * m.T_ * (c.Cref / cp - uu / (T(2) * cs2<T>()));
+                else
+                    geq = w9<T>(i) * cp * m.T_ *
+                          (c.Cref / cp + cu / cs2<T>() + (cu * cu - cs2<T>() * uu) / (T(2) * cs2<T>() * cs2<T>()));
+                put(i, PS.g(i) - (PS.g(i) - geq) / tau_g + pre * (w9<T>(i) * Qn));
+            }
         }
     }
     // a6: potential (Sec. 3.4), one sweep inside the fused step (l has its

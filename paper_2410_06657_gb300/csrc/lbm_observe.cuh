@@ -530,7 +530,9 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
     __shared__ T s_fs[BY + 2][34], s_Tm[BY + 2][34];
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values
     T(*stash)[BY][32] = reinterpret_cast<T(*)[BY][32]>(dsm_stash);
-    grid_dep_wait();
+    // as k_step: FP32 and FP64 wait for k_halo inside step_tile
+    constexpr bool EARLY = std::is_same<S, T>::value && std::is_same<typename FStore<S>::type, S>::value;
+    if constexpr (!EARLY) grid_dep_wait();
     grid_dep_release();
     load_counters(io, PH);
     advance_counters(io, PH, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
@@ -543,7 +545,8 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
 #pragma unroll
     for (int j = 0; j < OBS_NSUM; j++) ob.v[j] = typename StepObs<T, BY>::R(0);
     ob.rowbits = 0u;
-    step_tile<S, T, A, BY, PH, true, StepObs<T, BY>>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY, &ob);
+    step_tile<S, T, A, BY, PH, true, StepObs<T, BY>, EARLY>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY,
+                                                            &ob);
     obs_block_finish<32 * BY>(ws, sc, ob.v, ob.rowbits, (int)(blockIdx.y * BY + threadIdx.y), io.nx, io.ny);
 }
 
