@@ -324,9 +324,11 @@ def run_gpu(args, world, rank, local):
     sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     sampler.start()
     time.sleep(0.3)
+    # the warm-up's first two steps both observe, so the observing kernels of
+    # both layout phases are loaded before the timed steps
     for i in range(args.warmup):
         flush_l2()
-        if i % obs_every == 0:
+        if i % obs_every == 0 or i < 2:
             sim.observables_deferred()
         sim.step(1)
     torch.cuda.synchronize()
@@ -401,6 +403,13 @@ def run_gpu(args, world, rank, local):
     k_e2e = max(10, min(args.steps, 200))
     osz = ctypes.sizeof(lbm.Obs)
     obs_host = torch.zeros(k_e2e * osz, dtype=torch.uint8, pin_memory=True)
+    # untimed: the first import allocates its device buffers, and both layout
+    # phases of the observables kernel get loaded
+    for i in range(2):
+        sim.import_state(host.data_ptr())
+        sim.step(1)
+        sim.observables_to_host(obs_host.data_ptr() + i * osz)
+    sim.sync()
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
