@@ -222,6 +222,7 @@ JOBS = {
     "laplace_14": (laplace, (14.0,)),
     "laplace_18": (laplace, (18.0,)),
     "laplace_14_W5": (laplace, (14.0, 5.0)),
+    "laplace_21_W6": (laplace, (21.0, 6.0, 96, 11250)),
     "angle_60": (contact_angle, (60.0,)),
     "angle_90": (contact_angle, (90.0,)),
     "angle_120": (contact_angle, (120.0,)),
@@ -260,6 +261,7 @@ def run_all(processes=None):
     procs = processes or min(len(JOBS), max(1, os.cpu_count() or 1))
     # longest jobs first so the pool drains evenly
     order = ["deform_5_2_N160", "deform_2_5_N160", "freeze_off", "freeze_OB-", "freeze_PR-", "freeze_PR+",
+             "laplace_21_W6",
              "deform_5_2_N120", "deform_5_2", "deform_2_5", "sensitivity", "laplace_10", "laplace_14", "laplace_18",
              "laplace_14_W5", "angle_60", "angle_90", "angle_120", "front_paper",
              "mass", "stefan", "stefan_solid_diffusivity", "volume_0.9", "volume_1.1",
