@@ -79,17 +79,18 @@ struct Pol {
 // probability equal to the distance from the value truncated towards zero,
 // in units of the half spacing, so the stored value is unbiased.  r13 holds
 // 13 uniform random bits (the number of mantissa bits a float has beyond a
-// half's).
+// half's).  The conversion is the PTX cvt with stochastic rounding (.rs),
+// which takes the random bits from the caller: for a normal half it adds
+// them to the 13 mantissa bits the half drops and truncates; in the
+// subnormal half range (spacing 2^-24) the value moves by r13 * 2^-37
+// towards larger magnitude before truncation; .satfinite keeps a value
+// beyond the half range at the largest finite half, as truncation does.
+// The f16x2 form converts two values at once, its second operand with bits
+// 0-12 of the random word; one value goes in that slot.
 __device__ __forceinline__ __half half_sr(float v, uint32_t r13) {
-    uint32_t b = __float_as_uint(v);
-    const uint32_t mag = b & 0x7fffffffu;
-    if (mag >= 0x38800000u) {       // |v| >= 2^-14: a normal half keeps 10 of the 23 mantissa bits
-        b = (b & 0x80000000u) | ((mag + r13) & ~0x1fffu);
-        return __float2half_rz(__uint_as_float(b));
-    }
-    // subnormal half range: fixed spacing 2^-24
-    const float u = float(r13) * 7.2759576141834259e-12f;    // r13 * 2^-37, in [0, 2^-24)
-    return __float2half_rz(v + copysignf(u, v));
+    uint32_t d;
+    asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(0.0f), "f"(v), "r"(r13));
+    return __ushort_as_half((unsigned short)(d & 0xffffu));
 }
 template <>
 struct Pol<__half, float> {
