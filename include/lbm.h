@@ -401,6 +401,31 @@ int lbm_observables_noalloc(const lbm_params *p, const void *pop, const void *au
  */
 int lbm_substrate_heat_flux(struct lbm_handle *h, double *host_out);
 
+/*
+ * The stochastic rounding of half storage (LBM_FP16S, Sec. 3's populations
+ * g and l kept as weight-shifted halves), exposed so that the conversion
+ * the step uses can be checked against its definition: out[i] receives the
+ * 16 bits of v[i] rounded to half with the 13 random bits r[i] & 0x1fff
+ * (the step draws them from Philox4x32-10; here the caller supplies them).
+ *   |v| in the normal half range [2^-14, 65504]: with s the half spacing at
+ *     |v| and d the 13 bits of |v| below it (|v| = (q + d / 2^13) s, q an
+ *     integer), the magnitude is (q + 1) s if d + r >= 2^13, else q s;
+ *   |v| < 2^-14 (subnormal halves, spacing 2^-24): |v| + r 2^-37, rounded
+ *     to single precision, truncated to a multiple of 2^-24;
+ *   beyond the half range: the largest finite half, 65504; the sign is
+ *     kept; NaN stays NaN.
+ * So over the 8192 values of r the mean of the normal-range result is v
+ * exactly: the rounding is unbiased.
+ *   v, r, out  device arrays of n elements (v float, 4-byte aligned; r
+ *              uint32, 4-byte aligned; out uint16, 2-byte aligned), owned
+ *              by the caller
+ *   stream     cudaStream_t on which the work is enqueued (the call returns
+ *              without waiting)
+ * Errors: BADPARAM (n < 0, NULL or misaligned pointers with n > 0), CUDA
+ * (launch failure).  n = 0 enqueues nothing.
+ */
+int lbm_round_half_sr(const float *v, const uint32_t *r, uint16_t *out, int64_t n, void *stream);
+
 /* Steps taken since the last init.  */
 int64_t lbm_step_count(const struct lbm_handle *h);
 

@@ -26,6 +26,7 @@ UNITS = {
     "step_f64.cu": ["-fmad=false"],
     "step_f32.cu": FAST32,
     "step_f16s.cu": FAST32,
+    "half_round.cu": FAST32,
     "lbm_noalloc.cu": [],
 }
 

@@ -956,6 +956,26 @@ int lbm_presolve(lbm_handle *h, double tol, int32_t max_sweeps, int32_t *sweeps,
 
 int64_t lbm_step_count(const lbm_handle *h) { return h ? h->step : -1; }
 
+}  // extern "C"
+
+namespace lbm {
+// half_round.cu (built with the half-storage step's flags)
+cudaError_t launch_round_half_sr(const float *v, const uint32_t *r, uint16_t *out, long long n, cudaStream_t st);
+}
+
+extern "C" {
+
+int lbm_round_half_sr(const float *v, const uint32_t *r, uint16_t *out, int64_t n, void *stream) {
+    if (n < 0) return fail(LBM_ERR_BADPARAM, "negative count");
+    if (n == 0) return LBM_OK;
+    if (!v || !r || !out) return fail(LBM_ERR_BADPARAM, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(v) % 4 || reinterpret_cast<uintptr_t>(r) % 4 ||
+        reinterpret_cast<uintptr_t>(out) % 2)
+        return fail(LBM_ERR_BADPARAM, "misaligned pointer");
+    CK(launch_round_half_sr(v, r, out, (long long)n, static_cast<cudaStream_t>(stream)));
+    return LBM_OK;
+}
+
 size_t lbm_device_bytes(const lbm_handle *h) {
     if (!h) return 0;
     size_t n = h->mem_bytes + h->ws_mem_bytes;

@@ -33,7 +33,7 @@ EXPORTS = [
     "lbm_step_count", "lbm_configure", "lbm_destroy", "lbm_batch_create", "lbm_batch_step",
     "lbm_batch_tile_rows", "lbm_batch_destroy", "lbm_observables_noalloc",
     "lbm_substrate_heat_flux", "lbm_observables_to_host", "lbm_sync", "lbm_observables_deferred",
-    "lbm_presolve", "lbm_device_bytes",
+    "lbm_presolve", "lbm_device_bytes", "lbm_round_half_sr",
 ]
 
 
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_tile_rows.argtypes = [vp]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_substrate_heat_flux.argtypes = [vp, P(C.c_double)]
+    L.lbm_round_half_sr.argtypes = [vp, vp, vp, C.c_int64, vp]
     _lib = L
     return L
 
@@ -159,6 +160,23 @@ def _stream_handle(stream):
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
     return int(stream)
+
+
+def round_half_sr(v, r, stream=None):
+    """The half-storage stochastic rounding of the float32 device tensor v
+    with the random bits r (int32 device tensor of the same length; its low
+    13 bits are used): the 16 bits of each half, as an int16 device tensor.
+    Enqueued on `stream` (default: torch's current stream)."""
+    import torch
+    if v.dtype != torch.float32 or r.dtype != torch.int32 or not v.is_cuda or not r.is_cuda:
+        raise ValueError("v must be a float32 and r an int32 CUDA tensor")
+    if v.numel() != r.numel() or not v.is_contiguous() or not r.is_contiguous():
+        raise ValueError("v and r must be contiguous and of the same length")
+    out = torch.empty(v.numel(), dtype=torch.int16, device=v.device)
+    L = load()
+    _check(L.lbm_round_half_sr(C.c_void_p(v.data_ptr()), C.c_void_p(r.data_ptr()), C.c_void_p(out.data_ptr()),
+                               v.numel(), C.c_void_p(_stream_handle(stream))))
+    return out
 
 
 class Simulation:

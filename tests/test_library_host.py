@@ -127,3 +127,16 @@ def test_noalloc_rejects_misaligned_pointers_without_a_device(prec, pop_off, aux
                                    C.c_void_p(base + out_off), None)
     assert rc == lbm.ERR_BADPARAM
     assert b"aligned" in L.lbm_last_error()
+
+
+@pytest.mark.parametrize("v_off,r_off,out_off,n", [(2, 0, 0, 8), (0, 2, 0, 8), (0, 0, 1, 8), (0, 0, 0, -1)])
+def test_half_rounding_entry_rejects_bad_arguments_without_a_device(v_off, r_off, out_off, n):
+    """The half-rounding check entry refuses misaligned pointers and a
+    negative count with LBM_ERR_BADPARAM before any device work; a count of
+    zero enqueues nothing and succeeds."""
+    L = lbm.load()
+    base = 1 << 20      # never dereferenced
+    rc = L.lbm_round_half_sr(C.c_void_p(base + v_off), C.c_void_p(base + r_off), C.c_void_p(base + out_off), n,
+                             None)
+    assert rc == lbm.ERR_BADPARAM
+    assert L.lbm_round_half_sr(None, None, None, 0, None) == lbm.OK
