@@ -452,7 +452,8 @@ def run_gpu(args, world, rank, local):
                 "d2h_bytes_per_step": ctypes.sizeof(lbm.Obs), "steps": k_e2e,
                 "note": "per step: lbm_import_state from pinned host memory, lbm_step(1), "
                         "lbm_observables_to_host into pinned host memory; one lbm_sync at the end"},
-        "gpu_launches": args.steps * (p["k_e"] + 1),     # halo records + step, k_e - 1 sweeps
+        # halo records + step (k_e - 1 sweeps more), and the finish launch of each observing step
+        "gpu_launches": args.steps * (p["k_e"] + 1) + sum(observe),
         "clocks": clocks,
         "steady_state": {"value": ss_mlups, "unit": "MLUPS",
                          "note": f"lbm_step({n_ss}) graph replay, state resident in L2 (informational)"},

@@ -127,6 +127,13 @@ cudaError_t launch_step_t(const DevState &s, int cur, int lcur, int write_sigma,
     }
 }
 
+// The finish of an observation (group sums, then the observables), after
+// the launch that wrote the block partials of ws.nblocks blocks.
+inline cudaError_t launch_obs_finish(int nx, int ny, const ObsScratch &ws, const Scalars &sc, cudaStream_t st) {
+    return launch_dependent(k_obs_finish<OBS_FINISH_THREADS>, dim3(ws.ngroups), dim3(OBS_FINISH_THREADS), 0, st, nx,
+                            ny, ws, sc);
+}
+
 // The step that also reduces the observables of the state it reads.
 template <typename S, typename T, typename A, int BY, int PH>
 cudaError_t launch_step_obs_ph(const StepIO<S, T, A> &io, const Consts<T> &c, const Shift &sh, dim3 grid,
@@ -136,8 +143,10 @@ cudaError_t launch_step_obs_ph(const StepIO<S, T, A> &io, const Consts<T> &c, co
     if (e != cudaSuccess) return e;
     e = launch_halo_ph<S, T, A, BY, PH>(io, c, sh, grid, st);
     if (e != cudaSuccess) return e;
-    return launch_dependent(k_step_obs<S, T, A, BY, PH>, grid, dim3(32, BY), stash_bytes<T, BY>(), st, io, c, sh, w,
-                            sc);
+    e = launch_dependent(k_step_obs<S, T, A, BY, PH>, grid, dim3(32, BY), stash_bytes<T, BY>(), st, io, c, sh, w,
+                         sc);
+    if (e != cudaSuccess) return e;
+    return launch_obs_finish(io.nx, io.ny, w, sc, st);
 }
 
 template <typename S, typename T, typename A, int BY>
@@ -215,7 +224,8 @@ cudaError_t launch_step_obs_t(const DevState &s, int cur, int lcur, int write_si
         const Consts<T> &c = *reinterpret_cast<const Consts<T> *>(consts);                                \
         dim3 grid((s.nx + 31) / 32, (s.ny + OBS_BY - 1) / OBS_BY);                                          \
         k_obs<S, T, A><<<grid, dim3(32, OBS_BY), 0, st>>>(s, cur, lcur, c, sh, ws, sc);                     \
-        return cudaGetLastError();                                                                          \
+        const cudaError_t e = cudaGetLastError();                                                           \
+        return e != cudaSuccess ? e : launch_obs_finish(s.nx, s.ny, ws, sc, st);                            \
     }                                                                                                       \
     cudaError_t launch_step_obs_##SUFFIX(const DevState &s, int cur, int lcur, int write_sigma,             \
                                          const void *consts, const Shift &sh, int tile_rows,                \

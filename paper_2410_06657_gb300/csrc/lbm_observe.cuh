@@ -121,20 +121,16 @@ template <int NT>
 static __device__ __forceinline__ void obs_final(int nx, int ny, const ObsScratch &ws, const Scalars &sc);
 
 // Sum of n values of quantity j at src[i * OBS_NSUM + j] (i < n), by one warp
-// (warp j of the block) in a fixed order: lane l adds i = l, l + 32, ...,
-// then a binary tree in shared memory.  Returns the sum in lane 0.
-static __device__ __forceinline__ double warp_sum_fixed(const double *src, int n, int j, double *scratch32) {
+// in a fixed order: lane l adds i = l, l + 32, ..., then a butterfly of
+// shuffles.  Every lane returns the sum; lane 0 stores it in *out32.
+static __device__ __forceinline__ double warp_sum_fixed(const double *src, int n, int j, double *out32) {
     const int lane = threadIdx.x & 31;
     double v = lane < n ? __ldcg(src + (long long)lane * OBS_NSUM + j) : 0.0;
     for (int i = lane + 32; i < n; i += 32) v += __ldcg(src + (long long)i * OBS_NSUM + j);
-    scratch32[lane] = v;
-    __syncwarp();
 #pragma unroll
-    for (int h = 16; h > 0; h >>= 1) {
-        if (lane < h) scratch32[lane] += scratch32[lane + h];
-        __syncwarp();
-    }
-    return scratch32[0];
+    for (int h = 16; h > 0; h >>= 1) v += __shfl_xor_sync(0xffffffffu, v, h);
+    if (lane == 0) out32[0] = v;
+    return v;
 }
 
 // First level: the last block of group g sums the group's block partials
@@ -151,11 +147,10 @@ static __device__ __forceinline__ void obs_group(const ObsScratch &ws, int g, in
 }
 
 // The end of one block's part of the reduction (NT threads, one warp per
-// lattice row y): row flags, block sums (warp sums in R, warps combined in
-// FP64 in a fixed order) and the two-level finish.  FP64 adds run at a small
-// fraction of the FP32 rate on this part, so they are spread over many SMs:
-// the last block of each group of OBS_GROUP blocks sums its group, the last
-// group to finish sums the groups.  Every sum runs in a fixed order.
+// lattice row y): row flags and the block sums (warp sums in R, warps
+// combined in FP64 in a fixed order), written as the block's partials.
+// The finish is a launch of its own (k_obs_finish), so the blocks of the
+// reducing kernel end without a fence or a counter.
 template <int NT, typename R>
 static __device__ __forceinline__ void obs_block_finish(const ObsScratch &ws, const Scalars &sc, const R (&v)[OBS_NSUM],
                                                         unsigned int rowbits, int y, int nx, int ny) {
@@ -181,19 +176,27 @@ static __device__ __forceinline__ void obs_block_finish(const ObsScratch &ws, co
         for (int w = 1; w < NT / 32; w++) t += s_red[tid][w];
         ws.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * OBS_NSUM + tid] = t;
     }
-    const int blk = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
-    const int grp = blk / OBS_GROUP, gsize = min(OBS_GROUP, nblk - grp * OBS_GROUP);
-    __shared__ bool s_glast, s_last;
+}
+
+// The two-level finish of an observation, after the kernel that wrote the
+// block partials (its grid of ws.nblocks blocks).  FP64 adds run at a small
+// fraction of the FP32 rate on this part, so they are spread over many SMs:
+// block g of this launch (ws.ngroups blocks of NT threads) sums group g of
+// OBS_GROUP block partials, and the last of them to finish sums the groups
+// and writes the observables.  Every sum runs in a fixed order.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_obs_finish(int nx, int ny, ObsScratch ws, Scalars sc) {
+    grid_dep_wait();                   // the partials, crossings and flags of the reducing kernel
+    grid_dep_release();
+    const int g = blockIdx.x, gsize = min(OBS_GROUP, ws.nblocks - g * OBS_GROUP);
+    obs_group<NT>(ws, g, gsize);
+    __shared__ bool s_last;
     __syncthreads();
-    if (tid == 0) s_glast = atom_add_acq_rel(ws.gcount + grp, 1u) == (unsigned int)gsize - 1u;
-    __syncthreads();
-    if (!s_glast) return;
-    obs_group<NT>(ws, grp, gsize);
-    __syncthreads();
-    if (tid == 0) s_last = atom_add_acq_rel(ws.bad + 2, 1u) == (unsigned int)ws.ngroups - 1u;
+    if (threadIdx.x == 0) s_last = atom_add_acq_rel(ws.bad + 2, 1u) == (unsigned int)ws.ngroups - 1u;
     __syncthreads();
     if (s_last) obs_final<NT>(nx, ny, ws, sc);
 }
+constexpr int OBS_FINISH_THREADS = 256;      // a warp per quantity
 
 template <typename S, typename T, typename A>
 __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lcur, Consts<T> c, Shift sh,
