@@ -615,7 +615,7 @@ int lbm_observables_async(lbm_handle *h) {
     int rc = run_pending_obs(h);       // an earlier request that no step has taken
     if (rc) return rc;
     // the workspace starts at the identities of its reductions (set at
-    // creation) and the reduction's last block restores them
+    // creation) and the finish launch's last block restores them
     Scalars sc;
     sc.step = h->step;
     sc.alpha_l = h->P.alpha_l;

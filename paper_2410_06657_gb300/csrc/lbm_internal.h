@@ -62,12 +62,12 @@ constexpr int OBS_GROUP = 32;        // blocks per first-level group of the fina
 struct ObsScratch {
     double *partials;               // [nblocks][OBS_NSUM]
     double *gpartials;              // [ngroups][OBS_NSUM]: sums of each group of OBS_GROUP blocks
-    unsigned int *gcount;           // [ngroups]: blocks of each group finished
+    unsigned int *gcount;           // [ngroups]: kept at zero (the finish launch has one block per group)
     unsigned long long *maxv;       // [2 + ny]: height, (unused), rightmost crossing of row y
     unsigned long long *minv;       // [1 + ny]: front crossing, leftmost crossing of row y
     unsigned int *rowany;           // [ny]: bit0 liquid, bit1 left crossing, bit2 right crossing
     unsigned int *bad;              // [3]: non-finite seen, centre-column bottom cell frozen,
-                                    //      blocks finished (the last one reduces)
+                                    //      finish blocks done (the last one writes the observables)
     lbm_obs *obs;                   // device-side result (keeps t_fre)
     int nblocks, ngroups;
 };

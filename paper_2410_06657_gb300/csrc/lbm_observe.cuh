@@ -133,8 +133,8 @@ static __device__ __forceinline__ double warp_sum_fixed(const double *src, int n
     return v;
 }
 
-// First level: the last block of group g sums the group's block partials
-// (warp w sums quantities w, w + NT/32, ...) and restores the group's counter.
+// First level: block g of the finish launch sums group g's block partials
+// (warp w sums quantities w, w + NT/32, ...).
 template <int NT>
 static __device__ __forceinline__ void obs_group(const ObsScratch &ws, int g, int gsize) {
     __shared__ double s_g[OBS_NSUM][32];
@@ -143,7 +143,6 @@ static __device__ __forceinline__ void obs_group(const ObsScratch &ws, int g, in
         const double v = warp_sum_fixed(ws.partials + (long long)g * OBS_GROUP * OBS_NSUM, gsize, j, s_g[j]);
         if (lane == 0) ws.gpartials[(long long)g * OBS_NSUM + j] = v;
     }
-    if (threadIdx.x == 0 && threadIdx.y == 0) ws.gcount[g] = 0u;
 }
 
 // The end of one block's part of the reduction (NT threads, one warp per
