@@ -151,8 +151,8 @@ static __device__ __forceinline__ void obs_group(const ObsScratch &ws, int g, in
 // The finish is a launch of its own (k_obs_finish), so the blocks of the
 // reducing kernel end without a fence or a counter.
 template <int NT, typename R>
-static __device__ __forceinline__ void obs_block_finish(const ObsScratch &ws, const Scalars &sc, const R (&v)[OBS_NSUM],
-                                                        unsigned int rowbits, int y, int nx, int ny) {
+static __device__ __forceinline__ void obs_block_finish(const ObsScratch &ws, const R (&v)[OBS_NSUM],
+                                                        unsigned int rowbits, int y, int ny) {
     __shared__ double s_red[OBS_NSUM][NT / 32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     // row flags: OR across the warp (all lanes share the row), one atomic
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
         }
     }
     const R v[OBS_NSUM] = {v_psi, v_H, v_fs, v_q, v_liq, v_liqu, v_qdot};
-    obs_block_finish<32 * OBS_BY, R>(ws, sc, v, rowbits, y, nx, ny);
+    obs_block_finish<32 * OBS_BY, R>(ws, v, rowbits, y, ny);
 }
 
 // psi = 1/2 extent of row y: 0 without liquid, nx without a left or right
@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
     ob.rowbits = 0u;
     step_tile<S, T, A, BY, PH, true, StepObs<T, BY>, EARLY>(io, c, sh, sm, stash, blockIdx.x * 32, blockIdx.y * BY,
                                                             &ob);
-    obs_block_finish<32 * BY>(ws, sc, ob.v, ob.rowbits, (int)(blockIdx.y * BY + threadIdx.y), io.nx, io.ny);
+    obs_block_finish<32 * BY>(ws, ob.v, ob.rowbits, (int)(blockIdx.y * BY + threadIdx.y), io.ny);
 }
 
 // Local substrate heat flux (R24), one thread per column, in the step's
