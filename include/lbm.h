@@ -236,8 +236,9 @@ int lbm_presolve(struct lbm_handle *h, double tol, int32_t max_sweeps, int32_t *
 /*
  * Advance n >= 0 time steps (Algorithm 1 under a Jacobi reading: every
  * system collides with time-n fields, then all stream, then the walls act).
- * Each step is one fused kernel launch over the lattice, streaming in place,
- * plus k_e - 1 potential-only sweeps (sigma frozen at time n).  Enqueues asynchronously
+ * Each step is two launches over the lattice (the halo records of the
+ * tile-edge cells, then the fused step, streaming in place), plus k_e - 1
+ * potential-only sweeps (sigma frozen at time n).  Enqueues asynchronously
  * on the handle's stream (long runs replay a captured CUDA graph).
  * Errors: STATE (not initialised), DIVERGED (an earlier observables call
  * saw non-finite values), BADPARAM (n < 0), CUDA.
@@ -279,7 +280,8 @@ int lbm_observables_to_host(struct lbm_handle *h, lbm_obs *out);
  * their own over the lattice.  The next
  * lbm_step reduces them inside its first step's kernel, which reads exactly
  * this state (its macro, stencil and force stages evaluate every value they
- * need); any other call on the handle first runs them on their own, as
+ * need), and a small finish launch after it sums the kernel's block
+ * partials; any other call on the handle first runs them on their own, as
  * lbm_observables_async would.  out: NULL to fetch the result later with
  * lbm_observables_fetch, or host memory (page-locked for an asynchronous
  * copy) that receives it behind that kernel, as lbm_observables_to_host.
