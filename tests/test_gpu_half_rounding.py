@@ -103,3 +103,15 @@ def test_rounding_is_unbiased_over_the_random_bits():
         mean = got.sum(axis=1) / 8192.0
         err = np.abs(mean - v[::8192].astype(np.float64))
         assert err.max() <= tol, (lo, err.max())
+
+
+def test_long_ragged_array_is_rounded_element_for_element():
+    """More elements than the launch has threads (the grid-stride loop goes
+    round more than once) and a count that is no multiple of the block."""
+    rng = np.random.default_rng(2410068)
+    n = 1_000_003
+    v = magnitudes(rng, n, 100, 145)
+    r = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    got, want = run(v, r), definition(v, r)
+    assert np.array_equal(got, want)
+    assert np.array_equal(run(v[:1], r[:1]), want[:1])
