@@ -252,32 +252,24 @@ __device__ __forceinline__ T cdot(int cx, int cy, T a, T b) {
     return r;
 }
 
-// Isotropic stencils (Eqs. eqtidi1-2) on a shared-memory tile: the sums
-// over i = 1..8 of w_i c_i z(x + c_i) and 2 w_i (z(x + c_i) - z(x)), in
-// the order of i, with the zero terms of the gradient left out.
-template <typename T, int W>
-__device__ __forceinline__ void grad_s(const T (*z)[W], int ex, int ey, T &gx, T &gy) {
-    const T wa = T(1.0 / 9.0), wd = T(1.0 / 36.0);
-    const T v1 = z[ey][ex + 1], v2 = z[ey + 1][ex], v3 = z[ey][ex - 1], v4 = z[ey - 1][ex];
-    const T v5 = z[ey + 1][ex + 1], v6 = z[ey + 1][ex - 1], v7 = z[ey - 1][ex - 1], v8 = z[ey - 1][ex + 1];
-    T sx = wa * v1;
-    sx = sx - wa * v3;
-    sx = sx + wd * v5;
-    sx = sx - wd * v6;
-    sx = sx - wd * v7;
-    sx = sx + wd * v8;
-    T sy = wa * v2;
-    sy = sy - wa * v4;
-    sy = sy + wd * v5;
-    sy = sy + wd * v6;
-    sy = sy - wd * v7;
-    sy = sy - wd * v8;
-    gx = sx / cs2<T>();
-    gy = sy / cs2<T>();
-}
-// The same stencils on the nine values v[i] = z(x + c_i) already loaded.
-template <typename T>
+// Isotropic stencils (Eqs. eqtidi1-2) on the nine values v[i] = z(x + c_i):
+// the sums over i = 1..8 of w_i c_i v_i and 2 w_i (v_i - v_0), divided by
+// c_s^2, in the order of i with the zero terms of the gradient left out.
+// RED (single-precision storage only): an algebraically equal form with
+// opposite neighbours differenced first, the diagonal differences shared by
+// both components and 1/c_s^2 = 3 folded into the weights.
+template <typename S>
+constexpr bool reduced_stencils() { return std::is_same<S, float>::value; }
+
+template <typename T, bool RED = false>
 __device__ __forceinline__ void grad_v(const T v[9], T &gx, T &gy) {
+    if constexpr (RED && sizeof(T) == 4) {
+        const T d13 = v[1] - v[3], d24 = v[2] - v[4];
+        const T d57 = v[5] - v[7], d86 = v[8] - v[6];
+        gx = T(1.0 / 3.0) * d13 + T(1.0 / 12.0) * (d57 + d86);
+        gy = T(1.0 / 3.0) * d24 + T(1.0 / 12.0) * (d57 - d86);
+        return;
+    }
     const T wa = T(1.0 / 9.0), wd = T(1.0 / 36.0);
     T sx = wa * v[1];
     sx = sx - wa * v[3];
@@ -294,21 +286,38 @@ __device__ __forceinline__ void grad_v(const T v[9], T &gx, T &gy) {
     gx = sx / cs2<T>();
     gy = sy / cs2<T>();
 }
-template <typename T>
+template <typename T, bool RED = false>
 __device__ __forceinline__ T lap_v(const T v[9]) {
+    if constexpr (RED && sizeof(T) == 4) {
+        // 6 (w_a sum of the axis neighbours + w_d sum of the diagonal ones) - 6 (4 w_a + 4 w_d) v_0
+        const T sa = (v[1] + v[3]) + (v[2] + v[4]);
+        const T sd = (v[5] + v[7]) + (v[6] + v[8]);
+        return T(2.0 / 3.0) * sa + (T(1.0 / 6.0) * sd - T(10.0 / 3.0) * v[0]);
+    }
     T acc = T(0);
 #pragma unroll
     for (int i = 1; i < 9; i++) acc += T(2) * w9<T>(i) * (v[i] - v[0]);
     return acc / cs2<T>();
 }
 
+// The same stencils on a shared-memory tile, so a stencil evaluated by the
+// observables kernel and by the step gives the same bits.
 template <typename T, int W>
-__device__ __forceinline__ T lap_s(const T (*z)[W], int ex, int ey) {
-    const T z0 = z[ey][ex];
-    T acc = T(0);
+__device__ __forceinline__ void load9(const T (*z)[W], int ex, int ey, T v[9]) {
 #pragma unroll
-    for (int i = 1; i < 9; i++) acc += T(2) * w9<T>(i) * (z[ey + CY[i]][ex + CX[i]] - z0);
-    return acc / cs2<T>();
+    for (int i = 0; i < 9; i++) v[i] = z[ey + CY[i]][ex + CX[i]];
+}
+template <typename T, int W, bool RED = false>
+__device__ __forceinline__ void grad_s(const T (*z)[W], int ex, int ey, T &gx, T &gy) {
+    T v[9];
+    load9<T, W>(z, ex, ey, v);
+    grad_v<T, RED>(v, gx, gy);
+}
+template <typename T, int W, bool RED = false>
+__device__ __forceinline__ T lap_s(const T (*z)[W], int ex, int ey) {
+    T v[9];
+    load9<T, W>(z, ex, ey, v);
+    return lap_v<T, RED>(v);
 }
 
 // s_i(u) of Sec. 3.2.
@@ -701,14 +710,15 @@ __device__ __forceinline__ void step_cell(const StepIO<S, T, A> &io, const Const
             vpsi[i] = a.psi; vrho[i] = a.rho; veps[i] = a.eps; vphi[i] = a.phi;
             vp[i] = b.p; vS[i] = b.S;
         }
-        grad_v<T>(vpsi, gpsix, gpsiy);
-        lpsi = lap_v<T>(vpsi);
-        grad_v<T>(vrho, grhox, grhoy);
-        grad_v<T>(veps, gepsx, gepsy);
-        grad_v<T>(vphi, gphix, gphiy);
-        lphi = lap_v<T>(vphi);
-        grad_v<T>(vp, gpx, gpy);
-        grad_v<T>(vS, gSx, gSy);
+        constexpr bool RED = reduced_stencils<S>();
+        grad_v<T, RED>(vpsi, gpsix, gpsiy);
+        lpsi = lap_v<T, RED>(vpsi);
+        grad_v<T, RED>(vrho, grhox, grhoy);
+        grad_v<T, RED>(veps, gepsx, gepsy);
+        grad_v<T, RED>(vphi, gphix, gphiy);
+        lphi = lap_v<T, RED>(vphi);
+        grad_v<T, RED>(vp, gpx, gpy);
+        grad_v<T, RED>(vS, gSx, gSy);
     }
 
     // ---- a3: forces (Eq. Fs with the chemical potential of Sec. 2; Eq. Fe)
@@ -1145,10 +1155,12 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
 }
 
 // Blocks per SM the single-precision step asks the register allocator for:
-// with 4-row tiles, 7 blocks (28 warps) hold a 512 x 256 lattice in one wave.
-template <typename T, int BY>
+// with 4-row tiles 8 blocks (32 warps, 64 registers) for single-precision
+// storage and 7 (28 warps, 72 registers) for half storage, whose rounding
+// and shifts slow down with fewer registers.
+template <typename S, typename T, int BY>
 constexpr int step_min_blocks() {
-    return sizeof(T) == 8 ? 1 : (BY == 4 ? 7 : (BY == 8 ? 4 : 1));
+    return sizeof(T) == 8 ? 1 : (BY == 4 ? (std::is_same<S, float>::value ? 8 : 7) : (BY == 8 ? 4 : 1));
 }
 
 // Blocks per SM of the batched step: fewer than the single-instance step's,
@@ -1180,7 +1192,7 @@ inline cudaError_t allow_dynamic_smem(K kernel, size_t bytes, std::atomic<unsign
 
 // io: step_io() of this launch's parities, resolved on the host (PH = cur).
 template <typename S, typename T, typename A, int BY, int PH>
-__global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
+__global__ void __launch_bounds__(32 * BY, step_min_blocks<S, T, BY>())
     k_step(StepIO<S, T, A> io, Consts<T> c, Shift sh) {
     __shared__ TileSmem<T, BY> sm;
     extern __shared__ __align__(16) unsigned char dsm_stash[];     // NPOP x BY x 32 values

@@ -287,9 +287,10 @@ __global__ void __launch_bounds__(32 * OBS_BY) k_obs(DevState s, int cur, int lc
             }
         }
         T gex, gey, gphx, gphy;
-        grad_s<T, 34>(s_eps, ex, ey, gex, gey);
-        grad_s<T, 34>(s_phi, ex, ey, gphx, gphy);
-        const T lphi = lap_s<T, 34>(s_phi, ex, ey);
+        constexpr bool RED = reduced_stencils<S>();
+        grad_s<T, 34, RED>(s_eps, ex, ey, gex, gey);
+        grad_s<T, 34, RED>(s_phi, ex, ey, gphx, gphy);
+        const T lphi = lap_s<T, 34, RED>(s_phi, ex, ey);
         v_q = R(-(gex * gphx + gey * gphy + m.eps * lphi));
         v_psi = R(m.psi);
         v_H = R(m.H);
@@ -526,7 +527,7 @@ struct StepObs {
 // state it starts from.  io, rng, cur as for k_step; `ws` carries this
 // grid's block and group counts.
 template <typename S, typename T, typename A, int BY, int PH>
-__global__ void __launch_bounds__(32 * BY, step_min_blocks<T, BY>())
+__global__ void __launch_bounds__(32 * BY, step_min_blocks<S, T, BY>())
     k_step_obs(StepIO<S, T, A> io, Consts<T> c, Shift sh, ObsScratch ws, Scalars sc) {
     __shared__ TileSmem<T, BY> sm;
     __shared__ T s_fs[BY + 2][34], s_Tm[BY + 2][34];
