@@ -1155,12 +1155,12 @@ __device__ __forceinline__ void step_tile(const StepIO<S, T, A> &io, const Const
 }
 
 // Blocks per SM the single-precision step asks the register allocator for:
-// with 4-row tiles 8 blocks (32 warps, 64 registers) for single-precision
-// storage and 7 (28 warps, 72 registers) for half storage, whose rounding
-// and shifts slow down with fewer registers.
+// with 4-row tiles, 7 blocks (28 warps) hold a 512 x 256 lattice in one wave.
+// (8 blocks at 64 registers were 0.3 us faster at 1024 x 512 but slowed the
+// one-wave lattices: latency per block counts there.)
 template <typename S, typename T, int BY>
 constexpr int step_min_blocks() {
-    return sizeof(T) == 8 ? 1 : (BY == 4 ? (std::is_same<S, float>::value ? 8 : 7) : (BY == 8 ? 4 : 1));
+    return sizeof(T) == 8 ? 1 : (BY == 4 ? 7 : (BY == 8 ? 4 : 1));
 }
 
 // Blocks per SM of the batched step: fewer than the single-instance step's,
